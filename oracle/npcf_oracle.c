@@ -1,0 +1,828 @@
+/*
+ * npcf_oracle.c -- plain, slow, FP64 CPU evaluation of the isotropic NPCF
+ * estimator of Philcox & Slepian, "Efficient Computation of N-Point
+ * Correlation Functions in D Dimensions" (arXiv:2106.10278).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link
+ * or call this file; only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code with the CUDA library.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   - hyperspherical harmonics Y_l(r^) for D = 2, 3, 4         (eq. hypersph-def)
+ *   - Ferrers functions P^mu_nu for integer and half-odd nu,mu (DLMF 14.6.1,
+ *     14.9.3, 18.5.8, 14.5.11-12, 14.10.1)
+ *   - Wigner 3j symbols (Racah formula, DLMF 34.2.4), D=3 Clebsch-Gordan
+ *     coefficients                                             (eq. CG-examples)
+ *   - the zero-total-angular-momentum coupling coefficients    (eq. Coupling-C,
+ *                                                               eq. zero-ang-mom-states)
+ *   - the separable discrete estimator                         (eq. NPCF-estimator-discrete)
+ *   - the naive O(n^N) estimator projected on the same basis   (eq. NPCF-estimator-intro-discrete
+ *                                                               with eq. B-hypersph)
+ *   - the N=3 estimator through the addition theorem, with its analytic
+ *     gradient in positions and weights                        (Sec. "Derivation", eq. zeta-basis-decomp)
+ *
+ * Readings of the paper that this file takes where the text is silent or
+ * garbled (every one is also listed in the design notes):
+ *   R1 the self pair k=j and any pair with r=0 exactly are skipped (Y(0) is
+ *      undefined);
+ *   R2 degenerate tuples (two secondaries equal) are kept, as in the naive
+ *      sum over all N-tuplets;
+ *   R3 bins are half-open [e_b, e_{b+1}), decided by comparing the FP64 r^2
+ *      with the FP64 square of the edge;
+ *   R4 v_b is the volume of the shell, |S^{D-1}|/D (e_{b+1}^D - e_b^D);
+ *   R5 theta_1 = atan2(x_2, x_1) and cos(theta_K) = x_{K+1}/|x_{1..K+1}|;
+ *   R6 for D=4, N=3 the zero coupling is (-1)^(l-l_1)/sqrt(dim_l) on states
+ *      with l_1' = -l_1 and equal higher indices (the D=3 value, extended);
+ *   R7 periodic boxes use the minimum image; V_D is the box volume;
+ *   R8 N=3 keys have b1 <= b2 (or b1 < b2 on request), N=4 keys b1<b2<b3.
+ *
+ * Floating point: compile with -ffp-contract=off so that no multiply-add is
+ * fused; r^2 is formed as ((dx*dx + dy*dy) + dz*dz) + ... left to right.
+ */
+#define _GNU_SOURCE
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+#define OR_MAXD 4
+#define OR_MAXL 16
+#define OR_MAXB 64
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ */
+/* factorials and binomials (exact in double up to 170!, used far below) */
+static double fact(int k)
+{
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= (double)i;
+    return f;
+}
+
+static double binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0.0;
+    return fact(n) / (fact(k) * fact(n - k));
+}
+
+static double sgn_pow(int e) { return (e % 2 == 0) ? 1.0 : -1.0; } /* (-1)^e */
+
+/* ------------------------------------------------------------------ */
+/* Ferrers (on-the-cut associated Legendre) functions.                 */
+
+/* Legendre polynomial P_n(x) by its explicit sum (DLMF 18.5.8),
+ * differentiated mu times term by term. */
+static double legendre_deriv(int n, int mu, double x)
+{
+    double s = 0.0;
+    for (int k = 0; 2 * k <= n; ++k) {
+        int p = n - 2 * k;
+        if (p < mu) continue;
+        double c = sgn_pow(k) * binom(n, k) * binom(2 * n - 2 * k, n);
+        s += c * (fact(p) / fact(p - mu)) * pow(x, (double)(p - mu));
+    }
+    return s / pow(2.0, (double)n);
+}
+
+/* P^mu_n(x) for integers n >= 0, |mu| <= n (DLMF 14.6.1 for mu >= 0, with
+ * the (-1)^mu phase; DLMF 14.9.3 for mu < 0). */
+static double ferrers_int(int n, int mu, double x)
+{
+    if (mu >= 0) {
+        return sgn_pow(mu) * pow(1.0 - x * x, 0.5 * mu) * legendre_deriv(n, mu, x);
+    }
+    int m = -mu;
+    return sgn_pow(m) * fact(n - m) / fact(n + m) * ferrers_int(n, m, x);
+}
+
+/* P^{-(k+1/2)}_{nu}(cos th) for half-odd degree nu = L + 1/2 and integer
+ * k >= 0: the elementary forms DLMF 14.5.11 (mu = +1/2) and 14.5.12
+ * (mu = -1/2), then the order recurrence DLMF 14.10.1 run downwards. */
+static double ferrers_half(int L, int k, double th)
+{
+    double nu = L + 0.5;
+    double s = sin(th), x = cos(th);
+    double pre = sqrt(2.0 / (M_PI * s));
+    double p_up = pre * cos((nu + 0.5) * th);               /* mu = +1/2 */
+    double p_lo = pre * sin((nu + 0.5) * th) / (nu + 0.5);  /* mu = -1/2 */
+    if (k == 0) return p_lo;
+    double mu = -0.5;
+    for (int step = 1; step <= k; ++step) {
+        double m = mu - 1.0; /* new, lower order */
+        /* P^{m+2} + 2(m+1) x (1-x^2)^{-1/2} P^{m+1} + (nu-m)(nu+m+1) P^m = 0 */
+        double p_new = -(p_up + 2.0 * (m + 1.0) * x / s * p_lo) / ((nu - m) * (nu + m + 1.0));
+        p_up = p_lo;
+        p_lo = p_new;
+        mu = m;
+    }
+    return p_lo;
+}
+
+/* ------------------------------------------------------------------ */
+/* Hyperspherical harmonic states and values.                          */
+
+typedef struct { int l[OR_MAXD - 1]; } state_t; /* l[0] = l_1 (signed) ... l[D-2] = total */
+
+/* Enumerate states obeying the selection rules (eq. selection-rules):
+ * -l_2 <= l_1 <= l_2 <= ... <= l_{D-1} <= lmax; D=2 has l_1 in [-lmax, lmax]. */
+static int enum_states(int D, int lmax, state_t *out)
+{
+    int ns = 0;
+    if (D == 2) {
+        for (int l1 = -lmax; l1 <= lmax; ++l1) {
+            if (out) { memset(&out[ns], 0, sizeof(state_t)); out[ns].l[0] = l1; }
+            ++ns;
+        }
+    } else if (D == 3) {
+        for (int l2 = 0; l2 <= lmax; ++l2)
+            for (int l1 = -l2; l1 <= l2; ++l1) {
+                if (out) { memset(&out[ns], 0, sizeof(state_t)); out[ns].l[0] = l1; out[ns].l[1] = l2; }
+                ++ns;
+            }
+    } else if (D == 4) {
+        for (int l3 = 0; l3 <= lmax; ++l3)
+            for (int l2 = 0; l2 <= l3; ++l2)
+                for (int l1 = -l2; l1 <= l2; ++l1) {
+                    if (out) {
+                        memset(&out[ns], 0, sizeof(state_t));
+                        out[ns].l[0] = l1; out[ns].l[1] = l2; out[ns].l[2] = l3;
+                    }
+                    ++ns;
+                }
+    }
+    return ns;
+}
+
+/* Y_{l_1..l_{D-1}}(d/|d|) from eq. hypersph-def: the product of
+ * Theta_1 = e^{i l_1 th_1}/sqrt(2 pi) (the D=2 form printed with the
+ * paper's two- and three-dimensional harmonics) and, for 2 <= K <= D-1,
+ * Theta_K = sqrt((2 l_K + K - 1)/2 (l_K + l_{K-1} + K - 2)!/(l_K - l_{K-1})!)
+ *           sin^{1-K/2}(th_K) P^{-(l_{K-1}+K/2-1)}_{l_K+K/2-1}(cos th_K). */
+static cplx harmonic(int D, const state_t *s, const double *d)
+{
+    double th1 = atan2(d[1], d[0]);
+    cplx y = cexp(I * (double)s->l[0] * th1) / sqrt(2.0 * M_PI);
+    double rho2 = d[0] * d[0] + d[1] * d[1];
+    for (int K = 2; K <= D - 1; ++K) {
+        double rhoK2 = rho2 + d[K] * d[K];          /* |x_{1..K+1}|^2 */
+        double cth = d[K] / sqrt(rhoK2);
+        if (cth > 1.0) cth = 1.0;
+        if (cth < -1.0) cth = -1.0;
+        double th = acos(cth);
+        int lK = s->l[K - 1], lKm1 = s->l[K - 2];
+        double norm;
+        double val;
+        if (K % 2 == 0) {
+            /* integer degree and order: K/2 - 1 is an integer */
+            int h = K / 2 - 1;
+            norm = sqrt((2.0 * lK + K - 1) / 2.0 * fact(lK + lKm1 + K - 2) / fact(lK - lKm1));
+            val = pow(sin(th), 1.0 - 0.5 * K) * ferrers_int(lK + h, -(lKm1 + h), cth);
+        } else {
+            /* half-odd degree and order: K/2 - 1 = (K-3)/2 + 1/2 */
+            int h = (K - 3) / 2;
+            norm = sqrt((2.0 * lK + K - 1) / 2.0 * fact(lK + lKm1 + K - 2) / fact(lK - lKm1));
+            val = pow(sin(th), 1.0 - 0.5 * K) * ferrers_half(lK + h, lKm1 + h, th);
+        }
+        y *= norm * val;
+        rho2 = rhoK2;
+    }
+    return y;
+}
+
+/* ------------------------------------------------------------------ */
+/* Wigner 3j symbol by the Racah formula (DLMF 34.2.4).               */
+static double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3)
+{
+    if (m1 + m2 + m3 != 0) return 0.0;
+    if (j3 < abs(j1 - j2) || j3 > j1 + j2) return 0.0;
+    if (abs(m1) > j1 || abs(m2) > j2 || abs(m3) > j3) return 0.0;
+    double tri = fact(j1 + j2 - j3) * fact(j1 - j2 + j3) * fact(-j1 + j2 + j3) / fact(j1 + j2 + j3 + 1);
+    double pre = sqrt(tri * fact(j1 + m1) * fact(j1 - m1) * fact(j2 + m2) * fact(j2 - m2) *
+                      fact(j3 + m3) * fact(j3 - m3));
+    int kmin = 0;
+    if (j2 - j3 - m1 > kmin) kmin = j2 - j3 - m1;
+    if (j1 - j3 + m2 > kmin) kmin = j1 - j3 + m2;
+    int kmax = j1 + j2 - j3;
+    if (j1 - m1 < kmax) kmax = j1 - m1;
+    if (j2 + m2 < kmax) kmax = j2 + m2;
+    double s = 0.0;
+    for (int k = kmin; k <= kmax; ++k) {
+        s += sgn_pow(k) / (fact(k) * fact(j1 + j2 - j3 - k) * fact(j1 - m1 - k) * fact(j2 + m2 - k) *
+                           fact(j3 - j2 + m1 + k) * fact(j3 - j1 - m2 + k));
+    }
+    return sgn_pow(abs(j1 - j2 - m3)) * pre * s;
+}
+
+/* D=3 Clebsch-Gordan coefficient <l1 m1, l2 m2 | L M> as printed in
+ * eq. CG-examples: (-1)^(-l1+l2-M) sqrt(2L+1) (l1 l2 L; m1 m2 -M). */
+static double cg_d3(int l1, int m1, int l2, int m2, int L, int M)
+{
+    return sgn_pow(abs(-l1 + l2 - M)) * sqrt(2.0 * L + 1.0) * wigner3j(l1, l2, L, m1, m2, -M);
+}
+
+/* ------------------------------------------------------------------ */
+/* Output keys and coupling terms.                                     */
+
+typedef struct { int b[3]; int l[3]; } okey_t;  /* unused entries are -1 (bins) / 0 (ells) */
+
+typedef struct {
+    int nl;            /* entries of Lambda used: 1 for N=3, 3 for N=4 */
+    int l[3];
+} lam_t;
+
+/* Angular labels Lambda of the isotropic basis.
+ * N=3: Lambda = (l), l = 0..lmax (the final CG forces l^1 = l^2 = l).
+ * N=4, D=3: Lambda = (l1, l2, l3) with l^12 = l3 forced by the final CG,
+ *           every l <= lmax and (l1, l2, l3) obeying the triangle rule.
+ * N=4, D=2: the signed (l1, l2, l3) with l1 + l2 + l3 = 0, l1 >= 0. */
+static int enum_lambdas(int D, int N, int lmax, lam_t *out)
+{
+    int nl = 0;
+    if (N == 3) {
+        for (int l = 0; l <= lmax; ++l) {
+            if (out) { out[nl].nl = 1; out[nl].l[0] = l; out[nl].l[1] = 0; out[nl].l[2] = 0; }
+            ++nl;
+        }
+    } else if (N == 4 && D == 3) {
+        for (int l1 = 0; l1 <= lmax; ++l1)
+            for (int l2 = 0; l2 <= lmax; ++l2)
+                for (int l3 = 0; l3 <= lmax; ++l3) {
+                    if (l3 < abs(l1 - l2) || l3 > l1 + l2) continue;
+                    if (out) { out[nl].nl = 3; out[nl].l[0] = l1; out[nl].l[1] = l2; out[nl].l[2] = l3; }
+                    ++nl;
+                }
+    } else if (N == 4 && D == 2) {
+        for (int l1 = 0; l1 <= lmax; ++l1)
+            for (int l2 = -lmax; l2 <= lmax; ++l2) {
+                int l3 = -l1 - l2;
+                if (abs(l3) > lmax) continue;
+                if (out) { out[nl].nl = 3; out[nl].l[0] = l1; out[nl].l[1] = l2; out[nl].l[2] = l3; }
+                ++nl;
+            }
+    }
+    return nl;
+}
+
+static int supported(int D, int N, int lmax, int nbins)
+{
+    if (lmax < 0 || lmax > 12 || nbins < 1 || nbins > OR_MAXB) return 0;
+    if (N == 3) return D >= 2 && D <= 4;
+    if (N == 4) return D == 2 || D == 3;
+    return 0;
+}
+
+static int enum_keys(int D, int N, int lmax, int nbins, int bin_lt, okey_t *out)
+{
+    int nl = enum_lambdas(D, N, lmax, NULL);
+    lam_t *lam = (lam_t *)malloc(sizeof(lam_t) * (nl > 0 ? nl : 1));
+    enum_lambdas(D, N, lmax, lam);
+    int nk = 0;
+    if (N == 3) {
+        for (int b1 = 0; b1 < nbins; ++b1)
+            for (int b2 = b1 + (bin_lt ? 1 : 0); b2 < nbins; ++b2)
+                for (int il = 0; il < nl; ++il) {
+                    if (out) {
+                        okey_t *k = &out[nk];
+                        k->b[0] = b1; k->b[1] = b2; k->b[2] = -1;
+                        k->l[0] = lam[il].l[0]; k->l[1] = 0; k->l[2] = 0;
+                    }
+                    ++nk;
+                }
+    } else {
+        for (int b1 = 0; b1 < nbins; ++b1)
+            for (int b2 = b1 + 1; b2 < nbins; ++b2)
+                for (int b3 = b2 + 1; b3 < nbins; ++b3)
+                    for (int il = 0; il < nl; ++il) {
+                        if (out) {
+                            okey_t *k = &out[nk];
+                            k->b[0] = b1; k->b[1] = b2; k->b[2] = b3;
+                            k->l[0] = lam[il].l[0]; k->l[1] = lam[il].l[1]; k->l[2] = lam[il].l[2];
+                        }
+                        ++nk;
+                    }
+    }
+    free(lam);
+    return nk;
+}
+
+/* One term of P^0_Lambda = sum_terms C prod_i Y_{s_i}(r^i) (eq. N-1-particle-basis-wavefunction). */
+typedef struct { int s[3]; double c; } term_t;
+
+static int state_index(int D, int lmax, const state_t *st)
+{
+    /* position of st in the enumeration order of enum_states */
+    if (D == 2) return st->l[0] + lmax;
+    if (D == 3) return st->l[1] * st->l[1] + (st->l[0] + st->l[1]);
+    /* D == 4: states with l3' < l3 number sum_{l'<l3} (l'+1)^2 */
+    int base = 0;
+    for (int l = 0; l < st->l[2]; ++l) base += (l + 1) * (l + 1);
+    return base + st->l[1] * st->l[1] + (st->l[0] + st->l[1]);
+}
+
+/* Terms of the coupling coefficient C^{Lambda;0} (eq. Coupling-C with
+ * the CGs of eq. CG-examples), non-zero ones only. */
+static int lambda_terms(int D, int N, int lmax, const lam_t *lam, term_t *out)
+{
+    int nt = 0;
+    if (N == 3) {
+        int l = lam->l[0];
+        if (D == 2) {
+            /* <l^1 l^2 | 0> = delta(l^1 + l^2, 0); key l means (l, -l) */
+            if (out) {
+                state_t a = {{l, 0, 0}}, b = {{-l, 0, 0}};
+                out[nt].s[0] = state_index(D, lmax, &a);
+                out[nt].s[1] = state_index(D, lmax, &b);
+                out[nt].s[2] = -1;
+                out[nt].c = 1.0;
+            }
+            ++nt;
+        } else if (D == 3) {
+            for (int m1 = -l; m1 <= l; ++m1)
+                for (int m2 = -l; m2 <= l; ++m2) {
+                    double c = cg_d3(l, m1, l, m2, 0, 0);
+                    if (c == 0.0) continue;
+                    if (out) {
+                        state_t a = {{m1, l, 0}}, b = {{m2, l, 0}};
+                        out[nt].s[0] = state_index(D, lmax, &a);
+                        out[nt].s[1] = state_index(D, lmax, &b);
+                        out[nt].s[2] = -1;
+                        out[nt].c = c;
+                    }
+                    ++nt;
+                }
+        } else if (D == 4) {
+            /* reading R6 */
+            double dim = (double)(l + 1) * (double)(l + 1);
+            for (int l2 = 0; l2 <= l; ++l2)
+                for (int l1 = -l2; l1 <= l2; ++l1) {
+                    if (out) {
+                        state_t a = {{l1, l2, l}}, b = {{-l1, l2, l}};
+                        out[nt].s[0] = state_index(D, lmax, &a);
+                        out[nt].s[1] = state_index(D, lmax, &b);
+                        out[nt].s[2] = -1;
+                        out[nt].c = sgn_pow(abs(l - l1)) / sqrt(dim);
+                    }
+                    ++nt;
+                }
+        }
+    } else if (N == 4 && D == 2) {
+        /* <l^1 l^2 | L^12> <L^12 l^3 | 0> = delta(l^1 + l^2 + l^3, 0) */
+        if (out) {
+            state_t a = {{lam->l[0], 0, 0}}, b = {{lam->l[1], 0, 0}}, c = {{lam->l[2], 0, 0}};
+            out[nt].s[0] = state_index(D, lmax, &a);
+            out[nt].s[1] = state_index(D, lmax, &b);
+            out[nt].s[2] = state_index(D, lmax, &c);
+            out[nt].c = 1.0;
+        }
+        ++nt;
+    } else if (N == 4 && D == 3) {
+        int l1 = lam->l[0], l2 = lam->l[1], l3 = lam->l[2];
+        for (int m1 = -l1; m1 <= l1; ++m1)
+            for (int m2 = -l2; m2 <= l2; ++m2)
+                for (int m3 = -l3; m3 <= l3; ++m3) {
+                    /* sum over the intermediate [l^12] = M of the CG product */
+                    double c = 0.0;
+                    for (int M = -l3; M <= l3; ++M)
+                        c += cg_d3(l1, m1, l2, m2, l3, M) * cg_d3(l3, M, l3, m3, 0, 0);
+                    if (c == 0.0) continue;
+                    if (out) {
+                        state_t a = {{m1, l1, 0}}, b = {{m2, l2, 0}}, cc = {{m3, l3, 0}};
+                        out[nt].s[0] = state_index(D, lmax, &a);
+                        out[nt].s[1] = state_index(D, lmax, &b);
+                        out[nt].s[2] = state_index(D, lmax, &cc);
+                        out[nt].c = c;
+                    }
+                    ++nt;
+                }
+    }
+    return nt;
+}
+
+/* ------------------------------------------------------------------ */
+/* Geometry.                                                           */
+
+static double sphere_area(int D)
+{
+    /* |S^{D-1}| = 2 pi^{D/2} / Gamma(D/2) */
+    return 2.0 * pow(M_PI, 0.5 * D) / tgamma(0.5 * D);
+}
+
+/* separation y_k - y_j, minimum image when periodic (reading R7) */
+static void separation(int D, const double *yk, const double *yj, const double *box, int periodic, double *d)
+{
+    for (int a = 0; a < D; ++a) {
+        double v = yk[a] - yj[a];
+        if (periodic) {
+            double L = box[a];
+            if (v > 0.5 * L) v -= L;
+            else if (v < -0.5 * L) v += L;
+        }
+        d[a] = v;
+    }
+}
+
+static double norm2(int D, const double *d)
+{
+    double s = d[0] * d[0];
+    for (int a = 1; a < D; ++a) s = s + d[a] * d[a];
+    return s;
+}
+
+/* bin of a squared separation, -1 outside [e_0, e_nb) (reading R3) */
+static int bin_of(double r2, int nbins, const double *edges)
+{
+    if (r2 <= 0.0) return -1; /* reading R1 */
+    if (r2 < edges[0] * edges[0]) return -1;
+    for (int b = 0; b < nbins; ++b)
+        if (r2 < edges[b + 1] * edges[b + 1]) return b;
+    return -1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Public entry points (C ABI, called from Python through ctypes).     */
+
+int npcf_oracle_nstates(int D, int lmax) { return enum_states(D, lmax, NULL); }
+
+int npcf_oracle_states(int D, int lmax, int *l_out /* nstates x 3 */)
+{
+    int ns = enum_states(D, lmax, NULL);
+    state_t *st = (state_t *)malloc(sizeof(state_t) * ns);
+    enum_states(D, lmax, st);
+    for (int i = 0; i < ns; ++i)
+        for (int a = 0; a < 3; ++a) l_out[3 * i + a] = (a < D - 1) ? st[i].l[a] : 0;
+    free(st);
+    return ns;
+}
+
+/* Y for every state at every direction: out[(i*ns + s)*2 + {0,1}] */
+int npcf_oracle_harmonics(int D, int lmax, const double *dirs, int64_t nd, double *out)
+{
+    if (D < 2 || D > 4) return -1;
+    int ns = enum_states(D, lmax, NULL);
+    state_t *st = (state_t *)malloc(sizeof(state_t) * ns);
+    enum_states(D, lmax, st);
+    for (int64_t i = 0; i < nd; ++i)
+        for (int s = 0; s < ns; ++s) {
+            cplx y = harmonic(D, &st[s], dirs + i * D);
+            out[2 * (i * ns + s)] = creal(y);
+            out[2 * (i * ns + s) + 1] = cimag(y);
+        }
+    free(st);
+    return ns;
+}
+
+double npcf_oracle_wigner3j(int j1, int j2, int j3, int m1, int m2, int m3)
+{
+    return wigner3j(j1, j2, j3, m1, m2, m3);
+}
+
+double npcf_oracle_cg_d3(int l1, int m1, int l2, int m2, int L, int M) { return cg_d3(l1, m1, l2, m2, L, M); }
+
+double npcf_oracle_ferrers_int(int n, int mu, double x) { return ferrers_int(n, mu, x); }
+
+double npcf_oracle_ferrers_half(int L, int k, double th) { return ferrers_half(L, k, th); }
+
+int npcf_oracle_nkeys(int D, int N, int lmax, int nbins, int bin_lt)
+{
+    if (!supported(D, N, lmax, nbins)) return -1;
+    return enum_keys(D, N, lmax, nbins, bin_lt, NULL);
+}
+
+int npcf_oracle_keys(int D, int N, int lmax, int nbins, int bin_lt, int *keys /* nkeys x 6 */)
+{
+    if (!supported(D, N, lmax, nbins)) return -1;
+    int nk = enum_keys(D, N, lmax, nbins, bin_lt, NULL);
+    okey_t *k = (okey_t *)malloc(sizeof(okey_t) * (nk > 0 ? nk : 1));
+    enum_keys(D, N, lmax, nbins, bin_lt, k);
+    for (int i = 0; i < nk; ++i) {
+        for (int a = 0; a < 3; ++a) keys[6 * i + a] = k[i].b[a];
+        for (int a = 0; a < 3; ++a) keys[6 * i + 3 + a] = k[i].l[a];
+    }
+    free(k);
+    return nk;
+}
+
+/* Coupling terms of every Lambda, flattened: for lambda index il the terms
+ * are returned as (s1, s2, s3, c) rows.  Used by the tests to pin the
+ * coupling against independent formulas. */
+int npcf_oracle_coupling(int D, int N, int lmax, int il, int *s_out /* nt x 3 */, double *c_out)
+{
+    if (!supported(D, N, lmax, 1)) return -1;
+    int nl = enum_lambdas(D, N, lmax, NULL);
+    if (il < 0 || il >= nl) return -1;
+    lam_t *lam = (lam_t *)malloc(sizeof(lam_t) * nl);
+    enum_lambdas(D, N, lmax, lam);
+    int nt = lambda_terms(D, N, lmax, &lam[il], NULL);
+    if (s_out && c_out) {
+        term_t *t = (term_t *)malloc(sizeof(term_t) * (nt > 0 ? nt : 1));
+        lambda_terms(D, N, lmax, &lam[il], t);
+        for (int i = 0; i < nt; ++i) {
+            for (int a = 0; a < 3; ++a) s_out[3 * i + a] = t[i].s[a];
+            c_out[i] = t[i].c;
+        }
+        free(t);
+    }
+    free(lam);
+    return nt;
+}
+
+/* lambda index of a key's angular labels (keys are ordered bins-major) */
+static int key_lambda(const okey_t *k, const lam_t *lam, int nl)
+{
+    for (int i = 0; i < nl; ++i)
+        if (lam[i].l[0] == k->l[0] && lam[i].l[1] == k->l[1] && lam[i].l[2] == k->l[2]) return i;
+    return -1;
+}
+
+/*
+ * The estimator.  brute = 0: separable form, eq. NPCF-estimator-discrete:
+ *   zeta = (1/V) sum_j w_j sum_terms C prod_i a^{b_i}_{s_i}(y_j),
+ *   a^b_s(y_j) = (1/v_b) sum_k w_k Y*_s(y_k - y_j) Theta^b(|y_k - y_j|).
+ * brute = 1: the naive sum over all N-tuplets, eq. NPCF-estimator-intro-discrete,
+ *   with B = P^{0*}_Lambda prod Theta^{b_i}/v_{b_i} (eq. B-hypersph; the
+ *   coefficient is the projection on the conjugate basis, eq. zeta-basis-coeff).
+ * Primaries are j in [pb, pe); secondaries are all particles.
+ * out: 2*nkeys doubles (re, im), overwritten.
+ */
+int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const double *edges,
+                         const double *box, int periodic, const double *pos, const double *w, int64_t n,
+                         int64_t pb, int64_t pe, int brute, double *out)
+{
+    if (!supported(D, N, lmax, nbins)) return -1;
+    if (pb < 0 || pe > n || pb > pe) return -2;
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b + 1] > edges[b]) || edges[b] < 0.0) return -3;
+
+    int ns = enum_states(D, lmax, NULL);
+    state_t *st = (state_t *)malloc(sizeof(state_t) * ns);
+    enum_states(D, lmax, st);
+
+    int nl = enum_lambdas(D, N, lmax, NULL);
+    lam_t *lam = (lam_t *)malloc(sizeof(lam_t) * nl);
+    enum_lambdas(D, N, lmax, lam);
+    int *tstart = (int *)malloc(sizeof(int) * (nl + 1));
+    tstart[0] = 0;
+    for (int i = 0; i < nl; ++i) tstart[i + 1] = tstart[i] + lambda_terms(D, N, lmax, &lam[i], NULL);
+    term_t *terms = (term_t *)malloc(sizeof(term_t) * (tstart[nl] > 0 ? tstart[nl] : 1));
+    for (int i = 0; i < nl; ++i) lambda_terms(D, N, lmax, &lam[i], terms + tstart[i]);
+
+    int nk = enum_keys(D, N, lmax, nbins, bin_lt, NULL);
+    okey_t *keys = (okey_t *)malloc(sizeof(okey_t) * nk);
+    enum_keys(D, N, lmax, nbins, bin_lt, keys);
+    int *klam = (int *)malloc(sizeof(int) * nk);
+    for (int i = 0; i < nk; ++i) klam[i] = key_lambda(&keys[i], lam, nl);
+
+    double vb[OR_MAXB];
+    for (int b = 0; b < nbins; ++b)
+        vb[b] = sphere_area(D) / D * (pow(edges[b + 1], (double)D) - pow(edges[b], (double)D));
+    double V = 1.0;
+    for (int a = 0; a < D; ++a) V *= box[a];
+
+    cplx *zeta = (cplx *)calloc(nk, sizeof(cplx));
+    cplx *a = (cplx *)malloc(sizeof(cplx) * nbins * ns);
+    /* neighbour lists for the naive sum */
+    int64_t *nb_idx = NULL;
+    int *nb_bin = NULL;
+    cplx *nb_y = NULL;
+    if (brute) {
+        nb_idx = (int64_t *)malloc(sizeof(int64_t) * n);
+        nb_bin = (int *)malloc(sizeof(int) * n);
+        nb_y = (cplx *)malloc(sizeof(cplx) * n * ns);
+    }
+
+    double d[OR_MAXD];
+    for (int64_t j = pb; j < pe; ++j) {
+        const double *yj = pos + j * D;
+        if (!brute) {
+            for (int i = 0; i < nbins * ns; ++i) a[i] = 0.0;
+            for (int64_t k = 0; k < n; ++k) {
+                if (k == j) continue;
+                separation(D, pos + k * D, yj, box, periodic, d);
+                int b = bin_of(norm2(D, d), nbins, edges);
+                if (b < 0) continue;
+                for (int s = 0; s < ns; ++s) a[b * ns + s] += w[k] * conj(harmonic(D, &st[s], d));
+            }
+            for (int b = 0; b < nbins; ++b)
+                for (int s = 0; s < ns; ++s) a[b * ns + s] /= vb[b];
+            for (int i = 0; i < nk; ++i) {
+                const okey_t *kk = &keys[i];
+                cplx acc = 0.0;
+                for (int t = tstart[klam[i]]; t < tstart[klam[i] + 1]; ++t) {
+                    cplx p = terms[t].c * a[kk->b[0] * ns + terms[t].s[0]] * a[kk->b[1] * ns + terms[t].s[1]];
+                    if (N == 4) p *= a[kk->b[2] * ns + terms[t].s[2]];
+                    acc += p;
+                }
+                zeta[i] += w[j] * acc;
+            }
+        } else {
+            int64_t nn = 0;
+            for (int64_t k = 0; k < n; ++k) {
+                if (k == j) continue;
+                separation(D, pos + k * D, yj, box, periodic, d);
+                int b = bin_of(norm2(D, d), nbins, edges);
+                if (b < 0) continue;
+                nb_idx[nn] = k;
+                nb_bin[nn] = b;
+                for (int s = 0; s < ns; ++s) nb_y[nn * ns + s] = harmonic(D, &st[s], d);
+                ++nn;
+            }
+            for (int i = 0; i < nk; ++i) {
+                const okey_t *kk = &keys[i];
+                cplx acc = 0.0;
+                for (int64_t p1 = 0; p1 < nn; ++p1) {
+                    if (nb_bin[p1] != kk->b[0]) continue;
+                    for (int64_t p2 = 0; p2 < nn; ++p2) {
+                        if (nb_bin[p2] != kk->b[1]) continue;
+                        if (N == 3) {
+                            cplx P = 0.0;
+                            for (int t = tstart[klam[i]]; t < tstart[klam[i] + 1]; ++t)
+                                P += terms[t].c * nb_y[p1 * ns + terms[t].s[0]] * nb_y[p2 * ns + terms[t].s[1]];
+                            double wt = w[nb_idx[p1]] * w[nb_idx[p2]] / (vb[kk->b[0]] * vb[kk->b[1]]);
+                            acc += wt * conj(P);
+                        } else {
+                            for (int64_t p3 = 0; p3 < nn; ++p3) {
+                                if (nb_bin[p3] != kk->b[2]) continue;
+                                cplx P = 0.0;
+                                for (int t = tstart[klam[i]]; t < tstart[klam[i] + 1]; ++t)
+                                    P += terms[t].c * nb_y[p1 * ns + terms[t].s[0]] * nb_y[p2 * ns + terms[t].s[1]] *
+                                         nb_y[p3 * ns + terms[t].s[2]];
+                                double wt = w[nb_idx[p1]] * w[nb_idx[p2]] * w[nb_idx[p3]] /
+                                            (vb[kk->b[0]] * vb[kk->b[1]] * vb[kk->b[2]]);
+                                acc += wt * conj(P);
+                            }
+                        }
+                    }
+                }
+                zeta[i] += w[j] * acc;
+            }
+        }
+    }
+    for (int i = 0; i < nk; ++i) {
+        out[2 * i] = creal(zeta[i]) / V;
+        out[2 * i + 1] = cimag(zeta[i]) / V;
+    }
+    free(zeta); free(a); free(keys); free(klam); free(terms); free(tstart); free(lam); free(st);
+    free(nb_idx); free(nb_bin); free(nb_y);
+    return nk;
+}
+
+/* ------------------------------------------------------------------ */
+/* N = 3 through the addition theorem.                                 */
+/*
+ * For N=3 the isotropic basis function is, by eq. zero-ang-mom-states with
+ * the zero coupling of reading R6 (which for D=3 is the CG of eq. CG-examples,
+ * (-1)^(l-m)/sqrt(2l+1)), proportional to the sum over the intermediate
+ * labels of Y_l(r1) Y*_l(r2).  The addition theorem for hyperspherical
+ * harmonics turns that sum into a Gegenbauer polynomial of r1.r2:
+ *     sum_[l] Y_l(r1) Y*_l(r2) = dim_l/|S^{D-1}| C^{(lam)}_l(t)/C^{(lam)}_l(1),
+ * lam = D/2 - 1, t = r1.r2, dim_l from the state count quoted after
+ * eq. single-particle-eigenfun.  Hence (D >= 3)
+ *   zeta_l(b1,b2) = (1/V) sum_j w_j sum_{k in b1, k' in b2} w_k w_k'
+ *                   (-1)^l sqrt(dim_l)/|S^{D-1}| G_l(t_jkk') / (v_b1 v_b2),
+ * with G_l = C_l/C_l(1).  This route uses no harmonic and no coupling table,
+ * so it pins the separable estimator of N=3; its derivative in positions and
+ * weights (bins held fixed) is the gradient oracle for the adjoint.
+ */
+
+/* C^{(lam)}_n(x) by its explicit sum (DLMF 18.5.10) and its derivative */
+static double gegenbauer(int n, double lam, double x, double *deriv)
+{
+    double s = 0.0, ds = 0.0;
+    for (int k = 0; 2 * k <= n; ++k) {
+        int p = n - 2 * k;
+        /* (lam)_{n-k} / (k! (n-2k)!) * 2^p */
+        double poch = 1.0;
+        for (int i = 0; i < n - k; ++i) poch *= (lam + i);
+        double c = sgn_pow(k) * poch / (fact(k) * fact(p)) * pow(2.0, (double)p);
+        s += c * pow(x, (double)p);
+        if (p > 0) ds += c * p * pow(x, (double)(p - 1));
+    }
+    if (deriv) *deriv = ds;
+    return s;
+}
+
+static double gegenbauer_at_one(int n, double lam)
+{
+    /* C^{(lam)}_n(1) = (2 lam)_n / n! */
+    double poch = 1.0;
+    for (int i = 0; i < n; ++i) poch *= (2.0 * lam + i);
+    return poch / fact(n);
+}
+
+static double dim_l(int D, int l)
+{
+    if (D == 2) return 1.0;
+    return binom(l + D - 3, D - 3) * (2.0 * l + D - 2) / (double)(D - 2);
+}
+
+/*
+ * zeta (2*nkeys, imaginary parts zero) for N=3, D in {3,4}; if grad_coeffs is
+ * non-NULL also the gradient of L = sum_c grad_coeffs[2c] * Re zeta_c with
+ * respect to every position (grad_pos, n x D) and weight (grad_w, n).
+ */
+int npcf_oracle_n3_closed(int D, int lmax, int nbins, int bin_lt, const double *edges, const double *box,
+                          int periodic, const double *pos, const double *w, int64_t n, int64_t pb, int64_t pe,
+                          const double *grad_coeffs, double *out, double *grad_pos, double *grad_w)
+{
+    if (D < 3 || D > 4 || !supported(D, 3, lmax, nbins)) return -1;
+    if (pb < 0 || pe > n || pb > pe) return -2;
+    int nk = enum_keys(D, 3, lmax, nbins, bin_lt, NULL);
+    /* key index of (b1, b2, l) in enum_keys order */
+    int *kidx = (int *)malloc(sizeof(int) * nbins * nbins);
+    {
+        int c = 0;
+        for (int b1 = 0; b1 < nbins; ++b1)
+            for (int b2 = 0; b2 < nbins; ++b2) kidx[b1 * nbins + b2] = -1;
+        for (int b1 = 0; b1 < nbins; ++b1)
+            for (int b2 = b1 + (bin_lt ? 1 : 0); b2 < nbins; ++b2) {
+                kidx[b1 * nbins + b2] = c;
+                c += lmax + 1;
+            }
+    }
+    double vb[OR_MAXB];
+    for (int b = 0; b < nbins; ++b)
+        vb[b] = sphere_area(D) / D * (pow(edges[b + 1], (double)D) - pow(edges[b], (double)D));
+    double V = 1.0;
+    for (int a = 0; a < D; ++a) V *= box[a];
+    double lam = 0.5 * D - 1.0;
+    double S = sphere_area(D);
+    double pref[OR_MAXL + 1];
+    for (int l = 0; l <= lmax; ++l) pref[l] = sgn_pow(l) * sqrt(dim_l(D, l)) / S / gegenbauer_at_one(l, lam);
+
+    double *zeta = (double *)calloc(nk, sizeof(double));
+    int64_t *nb_idx = (int64_t *)malloc(sizeof(int64_t) * n);
+    int *nb_bin = (int *)malloc(sizeof(int) * n);
+    double *nb_u = (double *)malloc(sizeof(double) * n * D);  /* unit vectors */
+    double *nb_r = (double *)malloc(sizeof(double) * n);
+    if (grad_pos) memset(grad_pos, 0, sizeof(double) * n * D);
+    if (grad_w) memset(grad_w, 0, sizeof(double) * n);
+
+    double d[OR_MAXD];
+    for (int64_t j = pb; j < pe; ++j) {
+        int64_t nn = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            if (k == j) continue;
+            separation(D, pos + k * D, pos + j * D, box, periodic, d);
+            double r2 = norm2(D, d);
+            int b = bin_of(r2, nbins, edges);
+            if (b < 0) continue;
+            double r = sqrt(r2);
+            nb_idx[nn] = k;
+            nb_bin[nn] = b;
+            nb_r[nn] = r;
+            for (int a = 0; a < D; ++a) nb_u[nn * D + a] = d[a] / r;
+            ++nn;
+        }
+        for (int64_t p = 0; p < nn; ++p)
+            for (int64_t q = 0; q < nn; ++q) {
+                int b1 = nb_bin[p], b2 = nb_bin[q];
+                int kb = kidx[b1 * nbins + b2];
+                if (kb < 0) continue; /* the key stores (b1 <= b2) ordered pairs only */
+                double t = 0.0;
+                for (int a = 0; a < D; ++a) t += nb_u[p * D + a] * nb_u[q * D + a];
+                double wp = w[nb_idx[p]], wq = w[nb_idx[q]];
+                double scale = 1.0 / (vb[b1] * vb[b2] * V);
+                double dLdt = 0.0, L_no_w = 0.0;
+                for (int l = 0; l <= lmax; ++l) {
+                    double dg;
+                    double g = pref[l] * gegenbauer(l, lam, t, &dg);
+                    dg *= pref[l];
+                    zeta[kb + l] += w[j] * wp * wq * g * scale;
+                    if (grad_coeffs) {
+                        double G = grad_coeffs[2 * (kb + l)];
+                        dLdt += G * dg;
+                        L_no_w += G * g;
+                    }
+                }
+                if (!grad_coeffs) continue;
+                if (grad_w) {
+                    grad_w[j] += wp * wq * L_no_w * scale;
+                    grad_w[nb_idx[p]] += w[j] * wq * L_no_w * scale;
+                    grad_w[nb_idx[q]] += w[j] * wp * L_no_w * scale;
+                }
+                if (grad_pos) {
+                    double f = w[j] * wp * wq * scale * dLdt;
+                    for (int a = 0; a < D; ++a) {
+                        /* dt/dd_p = (u_q - t u_p)/|d_p|, d_p = y_p - y_j */
+                        double gp = f * (nb_u[q * D + a] - t * nb_u[p * D + a]) / nb_r[p];
+                        double gq = f * (nb_u[p * D + a] - t * nb_u[q * D + a]) / nb_r[q];
+                        grad_pos[nb_idx[p] * D + a] += gp;
+                        grad_pos[nb_idx[q] * D + a] += gq;
+                        grad_pos[j * D + a] -= gp + gq;
+                    }
+                }
+            }
+    }
+    for (int i = 0; i < nk; ++i) {
+        out[2 * i] = zeta[i];
+        out[2 * i + 1] = 0.0;
+    }
+    free(zeta); free(kidx); free(nb_idx); free(nb_bin); free(nb_u); free(nb_r);
+    return nk;
+}

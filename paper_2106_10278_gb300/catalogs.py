@@ -1,0 +1,156 @@
+"""Seeded synthetic particle catalogues and the named workloads.
+
+This module only draws inputs (positions, weights, bin edges); it holds none of
+the estimator's arithmetic, so both the CUDA path and the FP64 oracle may use
+it.  Every position it returns is exactly representable in FP32 and lies in
+[0, L) on every axis, so an FP32 device copy and an FP64 host copy describe the
+same points.
+
+Workloads (all periodic boxes, linear radial bins):
+
+=========  =====================================================================
+name       recipe
+=========  =====================================================================
+d3n3_fp64  D=3, N=3, lmax=5, FP64. n=2000 uniform in a cube of side 250,
+           w=1, 10 bins over [0, 100].
+d2         D=2, N=3 and N=4, lmax=10. n=200k in the unit square: 100k uniform
+           plus 100k in 400 Gaussian blobs (centres uniform, members
+           multinomial, sigma=0.005, wrapped), w ~ N(1, 0.1), 16 bins over
+           [0.002, 0.05].
+d3n4       D=3, N=4, lmax=5, data minus randoms: ~1M Poisson draws from a
+           lognormal field on a 256^3 grid (P(k) ~ k^-1.5, Gaussian variance 1,
+           rho = exp(G - 1/2)) in a box of side 1000, w=+1, plus 1M uniform
+           randoms with w=-1; 10 bins over [20, 160].
+d4n3       D=4, N=3, lmax=4. n=100k in the unit 4-cube: 50k uniform plus 50k
+           in 200 Gaussian blobs (sigma=0.01, wrapped), w ~ N(1, 0.1), 8 bins
+           over [0.01, 0.12].
+=========  =====================================================================
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _fp32_in_box(x: np.ndarray, L: np.ndarray) -> np.ndarray:
+    """Wrap into [0, L), round to FP32, and re-wrap values that rounded up to L."""
+    x = np.mod(x, L)
+    x32 = x.astype(np.float32).astype(np.float64)
+    L32 = np.asarray(L, dtype=np.float64)
+    x32 = np.where(x32 >= L32, 0.0, x32)
+    return x32
+
+
+def uniform(n: int, D: int, L, seed: int) -> np.ndarray:
+    """n points uniform in the periodic box [0, L)^D."""
+    L = np.broadcast_to(np.asarray(L, dtype=np.float64), (D,))
+    return _fp32_in_box(_rng(seed).random((n, D)) * L, L)
+
+
+def gaussian_blobs(n: int, D: int, L, n_centres: int, sigma: float, seed: int) -> np.ndarray:
+    """n points in Gaussian blobs: centres uniform, membership multinomial, wrapped."""
+    L = np.broadcast_to(np.asarray(L, dtype=np.float64), (D,))
+    g = _rng(seed)
+    centres = g.random((n_centres, D)) * L
+    counts = g.multinomial(n, np.full(n_centres, 1.0 / n_centres))
+    members = np.repeat(np.arange(n_centres), counts)
+    x = centres[members] + g.normal(0.0, sigma, (n, D))
+    return _fp32_in_box(x, L)
+
+
+def lognormal_poisson(n_mean: float, L: float, seed: int, grid: int = 256, slope: float = -1.5) -> np.ndarray:
+    """Poisson draws from a lognormal density on a grid^3 mesh of a periodic cube.
+
+    G is a Gaussian field with power spectrum P(k) ~ k^slope (k != 0), scaled to
+    unit variance; the density is rho = exp(G - 1/2); each cell holds a Poisson
+    number of points with mean n_mean * rho / sum(rho), placed uniformly in it.
+    """
+    g = _rng(seed)
+    white = g.standard_normal((grid, grid, grid))
+    fk = np.fft.rfftn(white)
+    kx = np.fft.fftfreq(grid)[:, None, None]
+    ky = np.fft.fftfreq(grid)[None, :, None]
+    kz = np.fft.rfftfreq(grid)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    amp = k2 ** (slope / 4.0)  # sqrt(P(k)) with P ~ k^slope
+    amp[0, 0, 0] = 0.0
+    G = np.fft.irfftn(fk * amp, s=(grid, grid, grid))
+    G /= G.std()
+    rho = np.exp(G - 0.5)
+    lam = n_mean * rho / rho.sum()
+    counts = g.poisson(lam).ravel()
+    cells = np.repeat(np.arange(grid ** 3), counts)
+    ix, iy, iz = np.unravel_index(cells, (grid, grid, grid))
+    cell = L / grid
+    base = np.stack([ix, iy, iz], axis=1).astype(np.float64) * cell
+    x = base + g.random((cells.size, 3)) * cell
+    return _fp32_in_box(x, np.full(3, float(L)))
+
+
+def normal_weights(n: int, mean: float, sd: float, seed: int) -> np.ndarray:
+    return _rng(seed).normal(mean, sd, n).astype(np.float32).astype(np.float64)
+
+
+def linear_edges(lo: float, hi: float, nbins: int) -> np.ndarray:
+    return np.linspace(lo, hi, nbins + 1)
+
+
+@dataclass
+class Workload:
+    name: str
+    D: int
+    N: int
+    lmax: int
+    edges: np.ndarray
+    box: np.ndarray
+    pos: np.ndarray
+    w: np.ndarray
+    precision: str = "fp32"
+    periodic: bool = True
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+
+def workload(name: str, seed: int | None = None, scale: float = 1.0) -> Workload:
+    """Build a named workload.  ``scale`` < 1 shrinks the particle count (and,
+    for the lognormal box, the volume) at fixed density, for tests."""
+    if name == "d3n3_fp64":
+        s = 0 if seed is None else seed
+        n = max(8, int(round(2000 * scale)))
+        pos = uniform(n, 3, 250.0, s)
+        return Workload(name, 3, 3, 5, linear_edges(0.0, 100.0, 10), np.full(3, 250.0), pos, np.ones(n), "fp64")
+    if name in ("d2", "d2n3", "d2n4"):
+        s = 1 if seed is None else seed
+        n_half = max(4, int(round(100_000 * scale)))
+        nc = max(1, int(round(400 * scale)))
+        pos = np.concatenate([uniform(n_half, 2, 1.0, s), gaussian_blobs(n_half, 2, 1.0, nc, 0.005, s + 500)])
+        w = normal_weights(2 * n_half, 1.0, 0.1, s + 900)
+        N = 4 if name == "d2n4" else 3
+        return Workload(name, 2, N, 10, linear_edges(0.002, 0.05, 16), np.full(2, 1.0), pos, w)
+    if name == "d3n4":
+        s = 2 if seed is None else seed
+        L = 1000.0 * scale ** (1.0 / 3.0)
+        grid = max(16, int(round(256 * scale ** (1.0 / 3.0))))
+        data = lognormal_poisson(1e6 * scale, L, s, grid=grid)
+        nr = max(4, int(round(1e6 * scale)))
+        rand = uniform(nr, 3, L, s + 500)
+        pos = np.concatenate([data, rand])
+        w = np.concatenate([np.ones(data.shape[0]), -np.ones(nr)])
+        return Workload(name, 3, 4, 5, linear_edges(20.0, 160.0, 10), np.full(3, L), pos, w)
+    if name == "d4n3":
+        s = 4 if seed is None else seed
+        n_half = max(4, int(round(50_000 * scale)))
+        nc = max(1, int(round(200 * scale)))
+        pos = np.concatenate([uniform(n_half, 4, 1.0, s), gaussian_blobs(n_half, 4, 1.0, nc, 0.01, s + 500)])
+        w = normal_weights(2 * n_half, 1.0, 0.1, s + 900)
+        return Workload(name, 4, 3, 4, linear_edges(0.01, 0.12, 8), np.full(4, 1.0), pos, w)
+    raise KeyError(name)
