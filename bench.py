@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the separable isotropic NPCF estimator on GB300.
+
+One step = one full evaluation (cell list, pair kernel, coupling kernel, FP64
+reduction) of the D=3 isotropic 4PCF on the data-minus-randoms workload:
+~1M Poisson draws from a lognormal field (256^3 grid, P(k) ~ k^-1.5) plus 1M
+uniform randoms with weight -1, periodic box of side 1000, 10 radial bins
+over [20, 160], lmax = 5 (13,320 complex coefficients).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own catalogue (seed + rank):
+independent problems, no data-path collective ("scaling": "weak").
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs/s and NPCF coeffs/s, 3D iso 4PCF n=1M, mixed vs FP32 at stated rel err"
+WORKLOAD = ("d3n4: D=3 isotropic 4PCF, ~1M lognormal-Poisson data (w=+1) + 1M uniform randoms (w=-1), "
+            "periodic box 1000, 10 linear bins over [20,160], lmax=5")
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="d3n4")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ counting helpers
+def pair_flops_per_pair(D: int, lmax: int) -> int:
+    """Algorithmic FP32 operations of one pair (FMA = 2): separation and r^2,
+    the direction, the harmonic recurrence and the accumulation, counted from
+    the recurrence of the pair kernel (see the design notes)."""
+    sep = 3 * D  # D subtractions, D multiply-adds for r^2 (2 each) -> 3D
+    direction = 2 + D  # rsqrt, r, D scalings
+    if D == 3:
+        powers = 6 * lmax  # complex multiply by (x - iy): 2 FMA + 2 MUL
+        first = 1 + 2 * lmax  # z * P_m (real for m = 0, complex after)
+        rec = 0
+        for m in range(lmax + 1):
+            for _ in range(m + 2, lmax + 1):
+                rec += 3 if m == 0 else 5  # A*z, then one FMA per real component
+        acc = (lmax + 1) ** 2
+        return sep + direction + powers + first + rec + acc
+    if D == 2:
+        return sep + direction + 6 * lmax + (2 * lmax + 1)
+    nq = sum((l + 1) ** 2 for l in range(lmax + 1))
+    return sep + direction + 6 * lmax + 5 * lmax * lmax + 2 * nq
+
+
+def coupling_terms_per_primary(D: int, N: int, lmax: int, nbins: int) -> int:
+    """Non-zero (Lambda, m1, m2) coupling terms summed over the bin tuples of one primary."""
+    if N == 3:
+        per = sum(2 * l + 1 for l in range(lmax + 1)) if D == 3 else (lmax + 1)
+        return per * nbins * (nbins + 1) // 2
+    ntrip = math.comb(nbins, 3)
+    if D == 2:
+        return ntrip * sum(1 for a in range(lmax + 1) for b in range(-lmax, lmax + 1) if abs(a + b) <= lmax)
+    t = 0
+    for l1 in range(lmax + 1):
+        for l2 in range(lmax + 1):
+            for l3 in range(abs(l1 - l2), min(l1 + l2, lmax) + 1):
+                for m1 in range(-l1, l1 + 1):
+                    for m2 in range(-l2, l2 + 1):
+                        if abs(m1 + m2) <= l3:
+                            t += 1
+    return ntrip * t
+
+
+def count_pairs_numpy(pos, edges, box, primaries):
+    """Ordered pairs (j, k != j, r in [e0, e_nb), minimum image) of the given primaries."""
+    lo, hi = edges[0] ** 2, edges[-1] ** 2
+    tot = 0
+    for j in range(*primaries):
+        d = pos - pos[j]
+        d -= box * np.round(d / box)
+        r2 = np.einsum("ij,ij->i", d, d)
+        tot += int(np.count_nonzero((r2 >= lo) & (r2 < hi) & (r2 > 0)))
+    return tot
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="npcf_clocks_", suffix=".csv")
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"unavailable": "nvidia-smi not runnable"}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"unavailable": "no samples"}
+        sm = [r[0] for r in rows]
+        mx = max(r[1] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _traffic_from_profiles(workload: str):
+    """Per-launch DRAM bytes of the pair kernel from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", f"k_pairs_{workload}.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null") else float(v)
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------- arms
+def _cpu_baseline(wl, target_s):
+    """The FP64 oracle (single thread, as it stands) on a bounded sample of primaries."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, 1))
+    t1 = time.perf_counter() - t0
+    nprim = int(max(1, min(256, round(target_s / max(t1, 1e-3)))))
+    t0 = time.perf_counter()
+    oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, nprim))
+    dt = time.perf_counter() - t0
+    pairs = count_pairs_numpy(wl.pos, wl.edges, wl.box, (0, nprim))
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"primaries [0,{nprim}) of the {wl.n}-particle workload, all secondaries, "
+                      f"{pairs} pairs in {dt:.2f} s (FP64 C oracle, single thread)"}
+
+
+def run_reference(args, rank, world):
+    from paper_2106_10278_gb300 import catalogs
+
+    if rank != 0:
+        return
+    wl = catalogs.workload(args.workload)
+    import oracle
+
+    oracle.build()
+    # size one step at ~ (a few minutes / steps) of CPU time
+    t0 = time.perf_counter()
+    oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, 1))
+    t1 = time.perf_counter() - t0
+    per_step = max(1, int(round(min(20.0, 150.0 / max(args.steps + args.warmup, 1)) / max(t1, 1e-3))))
+    for k in range(args.warmup):
+        oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(k, k + 1))
+    total_pairs, total_t = 0, 0.0
+    for k in range(args.steps):
+        a = (k * per_step) % max(wl.n - per_step, 1)
+        t0 = time.perf_counter()
+        oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(a, a + per_step))
+        total_t += time.perf_counter() - t0
+        total_pairs += count_pairs_numpy(wl.pos, wl.edges, wl.box, (a, a + per_step))
+    v = total_pairs / total_t
+    sample = f"{per_step} primaries per step of the {wl.n}-particle workload, all secondaries"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": wl.n},
+        "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2106_10278_gb300 import build as pbuild
+    from paper_2106_10278_gb300 import catalogs
+    from paper_2106_10278_gb300.npcf import Plan
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    base_seed = {"d3n4": 2, "d2n3": 1, "d2n4": 1, "d4n3": 4, "d3n3_fp64": 0}[args.workload]
+    wl = catalogs.workload(args.workload, seed=base_seed + 1000 * rank)
+    prec = "fp64" if wl.precision == "fp64" else "fp32"
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    plan = Plan(wl.D, wl.N, wl.lmax, wl.edges, wl.box, precision=prec, sync_check=False, timing=True)
+    pos = torch.tensor(wl.pos, dtype=tdt, device=dev)
+    w = torch.tensor(wl.w, dtype=tdt, device=dev)
+    out = torch.empty(2 * plan.ncoeff, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        plan.compute(pos, w, out=out)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    pairs_per_step = st["pairs"]
+    nprim = st["primaries"]
+
+    clocks = ClockSampler()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, pair_ms, couple_ms, cells_ms, launches = [], [], [], [], 0
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between timed steps (outside the events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.compute(pos, w, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pr = plan.profile()
+        pair_ms.append(pr["pairs_ms"])
+        couple_ms.append(pr["couple_ms"])
+        cells_ms.append(pr["cells_ms"])
+        launches += pr["launches"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total, float(pairs_per_step * args.steps)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_max, all_pairs = float(mx[0]), float(tt[1])
+    else:
+        t_max, all_pairs = t_total, float(pairs_per_step * args.steps)
+    value = all_pairs / t_max
+    terms = coupling_terms_per_primary(wl.D, wl.N, wl.lmax, len(wl.edges) - 1)
+    coeffs_per_s = world * nprim * terms * args.steps / t_max
+
+    # roofline of the dominant kernel (the pair kernel: FP32 ALU bound)
+    fpp = pair_flops_per_pair(wl.D, wl.lmax)
+    pk_s = float(np.mean(pair_ms)) / 1e3
+    achieved = fpp * pairs_per_step / pk_s / 1e12
+    sm_clock = 2070.0
+    peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12
+    traffic = _traffic_from_profiles(args.workload)
+    roofline = {"bound": "alu", "kernel": "k_pairs", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, FP32 CUDA cores)",
+                "flops_per_pair": fpp, "pairs_per_launch": pairs_per_step,
+                "pair_kernel_ms": float(np.mean(pair_ms))}
+
+    # end to end through the public host-buffer entry point (pinned inputs)
+    hp = torch.tensor(wl.pos, dtype=tdt).pin_memory()
+    hw = torch.tensor(wl.w, dtype=tdt).pin_memory()
+    plan.compute_host(hp.numpy(), hw.numpy())  # warm
+    e2e_t = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.compute_host(hp.numpy(), hw.numpy())
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": world * pairs_per_step / float(np.mean(e2e_t)), "unit": "pairs/s",
+           "h2d_bytes_per_step": int(hp.numel() * hp.element_size() + hw.numel() * hw.element_size()),
+           "d2h_bytes_per_step": int(2 * plan.ncoeff * 8)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "d3n4" else args.workload, "n": wl.n,
+                   "primaries": nprim, "pairs_per_step": pairs_per_step, "ncoeff": plan.ncoeff,
+                   "l2": "256 MB buffer written before every timed step (outside the events)"},
+        "coeffs_per_s": coeffs_per_s, "coupling_terms_per_primary": terms,
+        "stages_ms": {"cells": float(np.mean(cells_ms)), "pairs": float(np.mean(pair_ms)),
+                      "couple": float(np.mean(couple_ms))},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

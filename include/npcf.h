@@ -1,0 +1,152 @@
+/*
+ * npcf.h -- C ABI of libnpcf, a GB300 (sm_103a) implementation of the
+ * separable isotropic N-point correlation function estimator of
+ * Philcox & Slepian, arXiv:2106.10278.
+ *
+ * What one call computes (eq. NPCF-estimator-discrete, Sec. "Application to
+ * Discrete Data"): for every primary particle j, for every secondary k with
+ * |y_k - y_j| in radial bin b,
+ *     a^b_l(y_j) = (1/v_b) sum_k w_k Y*_l(unit(y_k - y_j)),
+ * with Y_l the D-dimensional hyperspherical harmonics (eq. hypersph-def), and
+ *     zeta^{0,b}_Lambda = (1/V_D) sum_j w_j sum_[l] C^{Lambda;0} prod_i a^{b_i}_{l^i}(y_j),
+ * with C the zero-total-angular-momentum coupling (eq. Coupling-C,
+ * eq. zero-ang-mom-states).  Supported: N=3 for D in {2,3,4}; N=4 for
+ * D in {2,3}.  Euclidean space (k = 0 in eq. metric).
+ *
+ * Conventions (the readings of the paper this library takes):
+ *   - bins are half-open [e_b, e_{b+1}); pairs with r = 0 are skipped;
+ *   - v_b = |S^{D-1}|/D (e_{b+1}^D - e_b^D); V_D = product of the box sides;
+ *   - periodic boxes use the minimum image (requires r_max < min(box)/2);
+ *     non-periodic runs require every position inside [0, box) and use the
+ *     box volume for V_D;
+ *   - tuples with two equal secondaries are kept (as in the naive N-tuplet
+ *     sum of eq. NPCF-estimator-intro-discrete);
+ *   - N=3 keys: b1 <= b2 (NPCF_BINS_LE) or b1 < b2 (NPCF_BINS_LT), l = 0..lmax;
+ *     N=4 keys: b1 < b2 < b3 and, for D=3, (l1, l2, l3) <= lmax obeying the
+ *     triangle rule (both parities); for D=2, signed (l1, l2, l3) with
+ *     l1 + l2 + l3 = 0, 0 <= l1 <= lmax, |l2|, |l3| <= lmax.
+ *
+ * Ownership: the caller owns every data buffer; the plan owns its tables and
+ * device workspace.  All pointers named "device" must be device memory of the
+ * current CUDA device; "host" pointers are ordinary host memory.
+ * Errors: every entry point returns an npcf_status; npcf_last_error() gives a
+ * thread-local message for the last failure.  No C++ exception crosses the ABI.
+ */
+#ifndef NPCF_H
+#define NPCF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NPCF_API __attribute__((visibility("default")))
+#else
+#define NPCF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct npcf_plan_s* npcf_plan_t; /* opaque; owned by the library */
+typedef void* npcf_stream_t;             /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    NPCF_OK = 0,
+    NPCF_ERR_ARG = -1,            /* invalid argument or size (detected on the host) */
+    NPCF_ERR_UNSUPPORTED = -2,    /* (D, N, lmax, nbins) or an option this build does not provide */
+    NPCF_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+    NPCF_ERR_WORKSPACE = -4,      /* device allocation failed */
+    NPCF_ERR_DEVICE_TIMEOUT = -5, /* a bounded device wait ran out */
+    NPCF_ERR_NONFINITE = -6,      /* a position or weight was NaN/Inf, or a position left the box */
+} npcf_status;
+
+enum { NPCF_FP64 = 0, NPCF_FP32 = 1 };          /* npcf_opts.precision */
+enum { NPCF_BINS_LE = 0, NPCF_BINS_LT = 1 };    /* npcf_opts.bin_order (N=3 only) */
+
+typedef struct {
+    int precision;  /* NPCF_FP32 (positions/weights float, pair and coupling arithmetic FP32,
+                       cross-primary sums FP64) or NPCF_FP64 (double throughout) */
+    int periodic;   /* 1: minimum image in the box; 0: open boundaries */
+    int bin_order;  /* NPCF_BINS_LE (default) or NPCF_BINS_LT, N=3 only */
+    int sync_check; /* 1 (default): npcf_compute waits for the stream and reports
+                       device-detected input errors; 0: fully asynchronous, query
+                       them later with npcf_device_status */
+    int timing;     /* 1: record CUDA events between the stages of every compute
+                       (read with npcf_last_profile); 0 (default): none */
+} npcf_opts;
+
+/* Default options: FP32, periodic, b1 <= b2, sync_check = 1, timing = 0. */
+NPCF_API void npcf_default_opts(npcf_opts* opts);
+
+/*
+ * Build a plan (host call; allocates the coupling tables on the current device).
+ *   D, N, lmax : dimension (2..4), order (3 or 4), maximum total angular momentum.
+ *   bin_edges  : host, nbins+1 ascending edges, bin_edges[0] >= 0; r_max = bin_edges[nbins].
+ *   box        : host, D side lengths (> 0).  Required in both modes (gives V_D).
+ *   opts       : host, may be NULL for the defaults.
+ * Errors: NPCF_ERR_ARG for bad sizes/edges/box, NPCF_ERR_UNSUPPORTED for
+ * combinations outside the list above (or nbins > 32), NPCF_ERR_CUDA.
+ */
+NPCF_API npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const double* bin_edges, int nbins,
+                             const double* box, const npcf_opts* opts);
+
+/* Number of output coefficients (each one complex: 2 doubles). */
+NPCF_API npcf_status npcf_num_coeffs(npcf_plan_t plan, int64_t* ncoeff);
+
+/* Labels of coefficient i: bins (N-1 entries, host) and ells (1 for N=3, 3 for N=4, host). */
+NPCF_API npcf_status npcf_coeff_index(npcf_plan_t plan, int64_t i, int* bins, int* ells);
+
+/*
+ * Compute the coefficients.
+ *   positions : device, n x D row-major, float (NPCF_FP32) or double (NPCF_FP64).
+ *   weights   : device, n, same type.
+ *   coeffs    : device, 2*ncoeff doubles (re, im), overwritten.
+ *   [primary_begin, primary_end): the primaries summed over (indices into the
+ *               input arrays); every particle is a secondary.  0, n = all.
+ *   stream    : the CUDA stream every kernel is launched on.
+ * Asynchronous on `stream` when opts.sync_check == 0.  Errors: NPCF_ERR_ARG
+ * (bad n or range), NPCF_ERR_NONFINITE (sync_check only), NPCF_ERR_WORKSPACE,
+ * NPCF_ERR_CUDA.  A plan must not be used by two calls at the same time.
+ */
+NPCF_API npcf_status npcf_compute(npcf_plan_t plan, const void* positions, const void* weights, int64_t n, double* coeffs,
+                         int64_t primary_begin, int64_t primary_end, npcf_stream_t stream);
+
+/*
+ * Same as npcf_compute with host buffers: positions/weights are host arrays,
+ * coeffs a host array of 2*ncoeff doubles.  Copies in, computes and copies out
+ * on `stream`, then waits for it.
+ */
+NPCF_API npcf_status npcf_compute_host(npcf_plan_t plan, const void* positions, const void* weights, int64_t n,
+                              double* coeffs, int64_t primary_begin, int64_t primary_end, npcf_stream_t stream);
+
+/* Device-side input errors flagged by the last asynchronous npcf_compute (waits for its stream). */
+NPCF_API npcf_status npcf_device_status(npcf_plan_t plan);
+
+/*
+ * Per-launch statistics of the last npcf_compute (host, after the stream has
+ * finished): ordered pairs accumulated, primaries processed, candidate
+ * secondaries examined.  Any pointer may be NULL.
+ */
+NPCF_API npcf_status npcf_last_stats(npcf_plan_t plan, int64_t* pairs, int64_t* primaries, int64_t* candidates);
+
+/*
+ * Stage timings and kernel count of the last npcf_compute (host, waits for its
+ * stream).  stage_ms (may be NULL) receives 4 values measured with CUDA events
+ * on the compute stream when opts.timing = 1 (else -1): cell list + work items,
+ * pair kernel, coupling kernel, final reduction.  launches (may be NULL)
+ * receives the number of kernels the call launched.
+ */
+NPCF_API npcf_status npcf_last_profile(npcf_plan_t plan, double* stage_ms, int* launches);
+
+/* Thread-local description of the most recent error on this thread. */
+NPCF_API const char* npcf_last_error(void);
+
+/* Release the plan and its device memory (waits for nothing; the caller must
+ * make sure no launch that uses the plan is still running). */
+NPCF_API void npcf_plan_destroy(npcf_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NPCF_H */

@@ -1,0 +1,132 @@
+// npcf_internal.h -- structures shared by the host plan code and the CUDA
+// translation units of libnpcf.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace npcf {
+
+constexpr int kMaxBins = 32;   // lanes own bins in the pair kernel: at most one warp's worth
+constexpr int kMaxD = 4;
+constexpr int kTab = 4096;     // radial lookup-table entries
+constexpr int kStageCap = 64;  // staged pairs per (warp, bin) in the pair kernel
+
+// Number of real components of a^b per bin for dimension D and lmax, in the
+// order the pair kernel writes them (see pair_layout in npcf_device.cuh).
+inline int num_real_components(int D, int lmax)
+{
+    if (D == 2) return 2 * lmax + 1;
+    if (D == 3) return (lmax + 1) * (lmax + 1);
+    int s = 0;  // D == 4: sum_{l3 <= lmax} (l3 + 1)^2
+    for (int l = 0; l <= lmax; ++l) s += (l + 1) * (l + 1);
+    return s;
+}
+
+// ---------------------------------------------------------------- cell list
+struct CellParams {
+    int D;
+    int64_t n;
+    int nc[4];          // cells per axis
+    int ncells;
+    double box[4];
+    double inv_side[4]; // nc[d] / box[d]
+    int periodic;
+    const void* pos;    // n x D (float or double)
+    const void* w;      // n
+    int* cid;           // n
+    int* cell_count;    // ncells (+1 scratch)
+    int* cell_start;    // ncells + 1
+    int* cell_fill;     // ncells
+    int* perm;          // n: slot -> original index
+    void* rec;          // n records (see Rec in npcf_device.cuh)
+    int* err;           // bit 0: non-finite value, bit 1: position outside the box
+};
+
+// --------------------------------------------------------------- pair kernel
+struct PairParams {
+    int D, nbins, lmax, nq;
+    int periodic;
+    int nc[4];
+    int stride[4];         // cell index = sum c[d] * stride[d]
+    double box[4];
+    float boxf[4];
+    float sidef[4];
+    double side[4];
+    float rmax2f, rmin2f;  // squared outer / inner radius (FP32, widened by the tolerance)
+    float tol;             // absolute half-width of the near-edge window (FP32 path)
+    float edgef[kMaxBins + 1];
+    double edge2[kMaxBins + 1];  // FP64 squares, the exact bin decision
+    float tab_lo, tab_inv;       // radial table: bucket k covers [tab_lo + k/tab_inv, ...)
+    signed char lane_bin[32];
+    signed char lane_rank[32];
+    signed char bin_nlanes[kMaxBins];
+    signed char bin_first[kMaxBins];
+    int warps;                   // primaries per item (= warps per CTA)
+    int nstencil;
+    const int* stencil;          // packed offsets, 8 bits per axis (signed)
+    const unsigned char* tab;    // kTab entries
+    const void* rec;             // sorted records
+    const int* cell_start;
+    const int4* items;           // (cell, slot_lo, count, primary_base)
+    const int* nitems;
+    int* ticket;
+    const void* qnorm;           // nq normalisation constants (T)
+    const void* inv_vb;          // nbins (T)
+    void* a_out;                 // nprim x nbins x nq (T)
+    void* w_out;                 // nprim (T)
+    unsigned long long* stats;   // [0] pairs, [1] candidates
+};
+
+// ----------------------------------------------------------- coupling kernel
+struct CoupleParams {
+    int D, N, nbins, lmax, nq, nlam;
+    const void* a;             // nprim x nbins x nq (T)
+    const void* wprim;         // nprim (T)
+    const int* nprim;
+    int chunk;                 // primaries per chunk (FP32 shared accumulation span)
+    int ncoeff;
+    double* partial;           // gridDim.x rows x 2*ncoeff
+    const int2* pairs;         // (b1, b2) pairs of the items
+    const int* pair_key;       // first key of each pair's outputs
+    const int4* kblocks;       // (pair_lo, pair_hi, key_lo, key_hi) per blockIdx.y
+    int nkb;
+    int max_block_keys;        // largest key_hi - key_lo
+    const int2* lam2;          // D=2, N=4: (l1, l2) per Lambda index
+    const signed char* lam_odd;// D=3, N=4: 1 if l1+l2+l3 is odd (coefficient imaginary)
+    const void* pref;          // N=3: per-l factor of the zero coupling (T)
+};
+
+// ------------------------------------------------------------- launchers
+// Each returns cudaSuccess or the launch error, and adds the kernels it
+// launched to launch_counter() (per host thread).
+inline int& launch_counter()
+{
+    static thread_local int n = 0;
+    return n;
+}
+cudaError_t launch_cell_ids(const CellParams& p, int fp64, cudaStream_t s);
+cudaError_t launch_cell_scatter(const CellParams& p, int fp64, cudaStream_t s);
+cudaError_t launch_exclusive_scan(const int* in, int* out, int n, int* scratch, cudaStream_t s);
+struct ItemBuffers {
+    int* cell_lo;      // ncells
+    int* cell_prims;   // ncells
+    int* prim_start;   // ncells
+    int* cell_items;   // ncells
+    int* item_start;   // ncells
+    int* scan_scratch; // 2 * 4096
+    int4* items;       // up to n items
+    int* nitems;       // 1
+    int* nprim;        // 1
+    int* ticket;       // 1
+};
+cudaError_t launch_make_items(const ItemBuffers& b, const int* cell_start, const int* perm, int ncells, int64_t pb,
+                              int64_t pe, int warps, cudaStream_t s);
+cudaError_t launch_pairs(const PairParams& p, int fp64, int grid, int smem, cudaStream_t s);
+int pair_kernel_smem(int D, int fp64, int nbins, int warps, int nq);
+int pair_kernel_compiled_lmax(int D, int fp64, int lmax);
+cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
+int couple_smem(const CoupleParams& p, int fp64);
+cudaError_t launch_reduce(const double* partial, int rows, int ncols, double scale, double* out, cudaStream_t s);
+
+}  // namespace npcf

@@ -1,0 +1,850 @@
+// npcf_plan.cu -- host side of libnpcf: plans (keys, coupling and
+// normalisation tables, lane map), the cell grid, the device workspace, the
+// launch sequence and the C ABI declared in include/npcf.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "npcf.h"
+#include "npcf_device.cuh"
+#include "npcf_internal.h"
+#include "npcf_pairs.cuh"
+
+namespace npcf {
+int pair_compiled_lmax_d2(int fp64, int lmax);
+int pair_compiled_lmax_d3(int fp64, int lmax);
+int pair_compiled_lmax_d4(int fp64, int lmax);
+int pair_threads_d2(int fp64, int L);
+int pair_threads_d3(int fp64, int L);
+int pair_threads_d4(int fp64, int L);
+cudaError_t launch_pairs_d2(const PairParams& p, int fp64, int L, int grid, int smem, cudaStream_t s);
+cudaError_t launch_pairs_d3(const PairParams& p, int fp64, int L, int grid, int smem, cudaStream_t s);
+cudaError_t launch_pairs_d4(const PairParams& p, int fp64, int L, int grid, int smem, cudaStream_t s);
+int couple_max_lmax_d3n4();
+}  // namespace npcf
+
+using namespace npcf;
+
+namespace {
+
+thread_local std::string g_err;
+
+npcf_status fail(npcf_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) return fail(NPCF_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+// A grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t b)
+    {
+        if (b <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t nb = b + b / 8 + 256;
+        cudaError_t e = cudaMalloc(&p, nb);
+        if (e == cudaSuccess) bytes = nb;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename U> U* as() const { return static_cast<U*>(p); }
+};
+
+double sphere_area(int D) { return 2.0 * std::pow(M_PI, 0.5 * D) / std::tgamma(0.5 * D); }
+
+}  // namespace
+
+struct npcf_plan_s {
+    int D = 3, N = 3, lmax = 0, nbins = 0;
+    npcf_opts opts{};
+    int fp64 = 0;
+    std::vector<double> edges;
+    double box[4] = {1, 1, 1, 1};
+    double V = 1.0;
+    // keys
+    int nlam = 0;
+    std::vector<int> lam;       // nlam x 3
+    int64_t ncoeff = 0;
+    std::vector<int> key_bins;  // ncoeff x 3
+    std::vector<int> key_lam;   // ncoeff
+    // coupling structure
+    std::vector<int2> pairs;
+    std::vector<int> pair_key;
+    std::vector<int4> kblocks;
+    int max_block_keys = 0;
+    // pair kernel configuration
+    int Lc = 0;        // compiled lmax of the pair kernel
+    int nq = 0;        // components written per bin (plan lmax)
+    int nq_c = 0;      // components of the compiled kernel
+    int threads = 0, warps = 0, pair_smem = 0;
+    PairParams pp{};
+    // device tables
+    DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil;
+    // workspace
+    DevBuf w_cid, w_perm, w_rec, w_cells, w_items, w_a, w_wprim, w_partial, w_small, w_hpos, w_hw, w_hout;
+    // cached cell grid
+    int grid_c = -1;
+    int nc[4] = {1, 1, 1, 1};
+    int ncells = 0;
+    int nstencil = 0;
+    int64_t grid_n = -1;
+    // device facts
+    int device = -1, nsm = 0, smem_optin = 0;
+    // stats of the last run (host copies)
+    unsigned long long* h_stats = nullptr;  // pinned, 2 entries
+    int* h_small = nullptr;                 // pinned, 4 entries
+    int64_t last_nprim = 0;
+    cudaStream_t last_stream = nullptr;
+    // stage timing (opts.timing)
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int last_launches = 0;
+    int timed = 0;
+};
+
+namespace {
+
+enum SmallIdx { S_ERR = 0, S_TICKET = 1, S_NITEMS = 2, S_NPRIM = 3 };  // ints; stats follow at byte 16
+
+// ----------------------------------------------------------------- keys
+void build_keys(npcf_plan_s* P)
+{
+    const int nb = P->nbins, L = P->lmax;
+    P->lam.clear();
+    if (P->N == 3) {
+        for (int l = 0; l <= L; ++l) P->lam.insert(P->lam.end(), {l, 0, 0});
+    } else if (P->D == 3) {
+        for (int a = 0; a <= L; ++a)
+            for (int b = 0; b <= L; ++b)
+                for (int c = 0; c <= L; ++c)
+                    if (c >= std::abs(a - b) && c <= a + b) P->lam.insert(P->lam.end(), {a, b, c});
+    } else {
+        for (int a = 0; a <= L; ++a)
+            for (int b = -L; b <= L; ++b) {
+                const int c = -a - b;
+                if (std::abs(c) <= L) P->lam.insert(P->lam.end(), {a, b, c});
+            }
+    }
+    P->nlam = (int)P->lam.size() / 3;
+    P->key_bins.clear();
+    P->key_lam.clear();
+    P->pairs.clear();
+    P->pair_key.clear();
+    if (P->N == 3) {
+        const int lt = P->opts.bin_order == NPCF_BINS_LT ? 1 : 0;
+        for (int b1 = 0; b1 < nb; ++b1)
+            for (int b2 = b1 + lt; b2 < nb; ++b2) {
+                P->pairs.push_back(make_int2(b1, b2));
+                P->pair_key.push_back((int)P->key_lam.size());
+                for (int il = 0; il < P->nlam; ++il) {
+                    P->key_bins.insert(P->key_bins.end(), {b1, b2, -1});
+                    P->key_lam.push_back(il);
+                }
+            }
+    } else {
+        for (int b1 = 0; b1 < nb; ++b1)
+            for (int b2 = b1 + 1; b2 < nb; ++b2) {
+                if (b2 + 1 < nb) {
+                    P->pairs.push_back(make_int2(b1, b2));
+                    P->pair_key.push_back((int)P->key_lam.size());
+                }
+                for (int b3 = b2 + 1; b3 < nb; ++b3)
+                    for (int il = 0; il < P->nlam; ++il) {
+                        P->key_bins.insert(P->key_bins.end(), {b1, b2, b3});
+                        P->key_lam.push_back(il);
+                    }
+            }
+    }
+    P->ncoeff = (int64_t)P->key_lam.size();
+}
+
+// Split the pair list into blocks whose keys fit the shared accumulators.
+void build_key_blocks(npcf_plan_s* P, int max_keys)
+{
+    P->kblocks.clear();
+    const int np = (int)P->pairs.size();
+    int lo = 0;
+    P->max_block_keys = 0;
+    while (lo < np) {
+        int hi = lo + 1;
+        auto key_end = [&](int h) { return h < np ? P->pair_key[h] : (int)P->ncoeff; };
+        while (hi < np && key_end(hi + 1) - P->pair_key[lo] <= max_keys) ++hi;
+        const int k0 = P->pair_key[lo], k1 = key_end(hi);
+        P->kblocks.push_back(make_int4(lo, hi, k0, k1));
+        P->max_block_keys = std::max(P->max_block_keys, k1 - k0);
+        lo = hi;
+    }
+}
+
+// ------------------------------------------------------- normalisation
+// Per real component of the a-array, the constant that turns the scaled
+// recurrence sums of the pair kernel into sum_k w_k Y*(r^).
+std::vector<double> component_norms(int D, int lmax)
+{
+    std::vector<double> q(num_q(D, lmax), 0.0);
+    if (D == 2) {
+        for (auto& v : q) v = 1.0 / std::sqrt(2.0 * M_PI);
+    } else if (D == 3) {
+        for (int l = 0; l <= lmax; ++l)
+            for (int m = 0; m <= l; ++m) {
+                const double N = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * cx::fact(l - m) / cx::fact(l + m));
+                const double F = N * cx::leg_scale(l, m);
+                q[q_index_d3(l, m)] = F;
+                if (m > 0) q[q_index_d3(l, m) + 1] = F;
+            }
+    } else {
+        for (int l3 = 0; l3 <= lmax; ++l3)
+            for (int l2 = 0; l2 <= l3; ++l2) {
+                const int n = l3 - l2, lam = l2 + 1;
+                // norm of C^{(lam)}_n with weight (1-x^2)^{lam-1/2}
+                const double h = M_PI * std::pow(2.0, 1.0 - 2.0 * lam) * std::tgamma(n + 2.0 * lam) /
+                                 (cx::fact(n) * (n + lam) * std::tgamma((double)lam) * std::tgamma((double)lam));
+                const double c = 1.0 / std::sqrt(h);
+                for (int l1 = 0; l1 <= l2; ++l1) {
+                    const double N3 =
+                        std::sqrt((2.0 * l2 + 1.0) / (4.0 * M_PI) * cx::fact(l2 - l1) / cx::fact(l2 + l1));
+                    const double F = N3 * cx::leg_scale(l2, l1) * c * cx::geg_scale(n, lam);
+                    q[q_index_d4(l3, l2, l1)] = F;
+                    if (l1 > 0) q[q_index_d4(l3, l2, l1) + 1] = F;
+                }
+            }
+    }
+    return q;
+}
+
+template <typename T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& v)
+{
+    cudaError_t e = b.reserve(std::max<size_t>(sizeof(T) * v.size(), 16));
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+std::vector<T> cast_vec(const std::vector<double>& v)
+{
+    return std::vector<T>(v.begin(), v.end());
+}
+
+// ------------------------------------------------------------ cell grid
+struct GridChoice {
+    int c = 0;
+    int nc[4] = {1, 1, 1, 1};
+    int ncells = 0;
+    std::vector<int> stencil;
+};
+
+std::vector<int> make_stencil(int D, int c, const double* side, double reach)
+{
+    std::vector<int> out;
+    int o[4] = {0, 0, 0, 0};
+    const int span = 2 * c + 1;
+    int total = 1;
+    for (int d = 0; d < D; ++d) total *= span;
+    for (int idx = 0; idx < total; ++idx) {
+        int r = idx;
+        double m2 = 0.0;
+        int packed = 0;
+        for (int d = 0; d < D; ++d) {
+            o[d] = r % span - c;
+            r /= span;
+            const double g = std::max(std::abs(o[d]) - 1, 0) * side[d];
+            m2 += g * g;
+            packed |= (o[d] & 0xff) << (8 * d);
+        }
+        if (m2 < reach * reach) out.push_back(packed);
+    }
+    return out;
+}
+
+GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
+{
+    GridChoice best;
+    double best_cost = 1e300;
+    const double rmax = P->edges[P->nbins];
+    const double reach = rmax * (1.0 + 1e-6) + 1e-12;
+    for (int c = 1; c <= 4; ++c) {
+        GridChoice g;
+        g.c = c;
+        bool ok = true;
+        double side[4];
+        int64_t ncells = 1;
+        for (int d = 0; d < P->D; ++d) {
+            int k = (int)std::floor(P->box[d] * c / rmax);
+            if (k < 1) k = 1;
+            if (P->opts.periodic && k < 2 * c + 1) ok = false;
+            if (k > 4096) k = 4096;
+            g.nc[d] = k;
+            side[d] = P->box[d] / k;
+            ncells *= k;
+        }
+        if (!ok || ncells >= (1 << 24)) continue;
+        g.ncells = (int)ncells;
+        const double npc = (double)std::max<int64_t>(n, 1) / (double)ncells;
+        if (c > 1 && npc < 4.0) continue;
+        g.stencil = make_stencil(P->D, c, side, reach);
+        const double cost = g.stencil.size() * (npc + 24.0);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = g;
+        }
+    }
+    return best;
+}
+
+// ------------------------------------------------------------ lane map
+void lane_map(npcf_plan_s* P)
+{
+    const int nb = P->nbins, D = P->D;
+    std::vector<double> share(nb);
+    double tot = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        share[b] = std::pow(P->edges[b + 1], D) - std::pow(P->edges[b], D);
+        tot += share[b];
+    }
+    std::vector<int> lanes(nb, 1);
+    for (int k = nb; k < 32; ++k) {
+        int best = 0;
+        double bv = -1.0;
+        for (int b = 0; b < nb; ++b) {
+            const double v = share[b] / tot / lanes[b];
+            if (v > bv) {
+                bv = v;
+                best = b;
+            }
+        }
+        lanes[best]++;
+    }
+    int l = 0;
+    for (int b = 0; b < nb; ++b) {
+        P->pp.bin_first[b] = (signed char)l;
+        P->pp.bin_nlanes[b] = (signed char)lanes[b];
+        for (int r = 0; r < lanes[b]; ++r, ++l) {
+            P->pp.lane_bin[l] = (signed char)b;
+            P->pp.lane_rank[l] = (signed char)r;
+        }
+    }
+}
+
+int pair_compiled_lmax(int D, int fp64, int lmax)
+{
+    if (D == 2) return pair_compiled_lmax_d2(fp64, lmax);
+    if (D == 3) return pair_compiled_lmax_d3(fp64, lmax);
+    return pair_compiled_lmax_d4(fp64, lmax);
+}
+
+int pair_threads(int D, int fp64, int L)
+{
+    if (D == 2) return pair_threads_d2(fp64, L);
+    if (D == 3) return pair_threads_d3(fp64, L);
+    return pair_threads_d4(fp64, L);
+}
+
+int rec_bytes(int D, int fp64) { return (fp64 ? 8 : 4) * 4 * (D <= 3 ? 1 : 2); }
+
+npcf_status ensure_device(npcf_plan_s* P)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (P->device == dev) return NPCF_OK;
+    if (P->device >= 0) return fail(NPCF_ERR_ARG, "plan was created on device %d, current device is %d", P->device, dev);
+    P->device = dev;
+    CUDA_TRY(cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&P->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    void* pinned = nullptr;
+    CUDA_TRY(cudaMallocHost(&pinned, 64));
+    std::memset(pinned, 0, 64);
+    P->h_small = static_cast<int*>(pinned);
+    P->h_stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(pinned) + 16);
+    return NPCF_OK;
+}
+
+npcf_status setup_tables(npcf_plan_s* P)
+{
+    const int D = P->D, nb = P->nbins;
+    // pair kernel
+    P->Lc = pair_compiled_lmax(D, P->fp64, P->lmax);
+    if (P->Lc < 0) return fail(NPCF_ERR_UNSUPPORTED, "lmax=%d is not compiled for D=%d (%s)", P->lmax, D,
+                                P->fp64 ? "FP64" : "FP32");
+    P->nq = num_q(D, P->lmax);
+    P->nq_c = num_q(D, P->Lc);
+    P->threads = pair_threads(D, P->fp64, P->Lc);
+    const int rb = rec_bytes(D, P->fp64), tb = P->fp64 ? 8 : 4;
+    int warps = P->threads / 32;
+    while (warps > 1 && pair_fixed_bytes(rb, warps * 32) + warps * pair_warp_bytes(rb, tb, nb, P->nq_c) >
+                            P->smem_optin)
+        --warps;
+    P->warps = warps;
+    P->threads = warps * 32;
+    P->pair_smem = pair_fixed_bytes(rb, P->threads) + warps * pair_warp_bytes(rb, tb, nb, P->nq_c);
+    if (P->pair_smem > P->smem_optin)
+        return fail(NPCF_ERR_UNSUPPORTED, "pair kernel needs %d bytes of shared memory", P->pair_smem);
+
+    PairParams& pp = P->pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.D = D;
+    pp.nbins = nb;
+    pp.lmax = P->lmax;
+    pp.nq = P->nq;
+    pp.periodic = P->opts.periodic;
+    pp.warps = warps;
+    double maxL = 0.0;
+    for (int d = 0; d < D; ++d) maxL = std::max(maxL, P->box[d]);
+    const double rmax = P->edges[nb], rmin = P->edges[0];
+    const double tol = 4.0 * (std::sqrt((double)D) * maxL * std::ldexp(1.0, -23) + rmax * std::ldexp(1.0, -21));
+    pp.tol = (float)tol;
+    pp.rmax2f = (float)((rmax + 2 * tol) * (rmax + 2 * tol));
+    const double rl = std::max(rmin - 2 * tol, 0.0);
+    pp.rmin2f = (float)(rl * rl);
+    for (int b = 0; b <= nb; ++b) {
+        pp.edgef[b] = (float)P->edges[b];
+        pp.edge2[b] = P->edges[b] * P->edges[b];
+    }
+    pp.tab_lo = (float)rmin;
+    pp.tab_inv = (float)(kTab / (rmax - rmin));
+    std::vector<unsigned char> tab(kTab);
+    for (int k = 0; k < kTab; ++k) {
+        const double r = rmin + k * (rmax - rmin) / kTab;
+        int b = 0;
+        while (b < nb && r >= P->edges[b + 1]) ++b;
+        tab[k] = (unsigned char)b;
+    }
+    lane_map(P);
+    CUDA_TRY(upload(P->d_tab, tab));
+    std::vector<double> qn = component_norms(D, P->lmax);
+    std::vector<double> ivb(nb);
+    for (int b = 0; b < nb; ++b)
+        ivb[b] = 1.0 / (sphere_area(D) / D * (std::pow(P->edges[b + 1], D) - std::pow(P->edges[b], D)));
+    if (P->fp64) {
+        CUDA_TRY(upload(P->d_qnorm, qn));
+        CUDA_TRY(upload(P->d_invvb, ivb));
+    } else {
+        CUDA_TRY(upload(P->d_qnorm, cast_vec<float>(qn)));
+        CUDA_TRY(upload(P->d_invvb, cast_vec<float>(ivb)));
+    }
+    pp.tab = P->d_tab.as<unsigned char>();
+    pp.qnorm = P->d_qnorm.p;
+    pp.inv_vb = P->d_invvb.p;
+
+    // coupling tables
+    std::vector<double> pref(P->lmax + 1, 1.0);
+    for (int l = 0; l <= P->lmax; ++l) {
+        if (D == 3) pref[l] = cx::neg1_pow(l) / std::sqrt(2.0 * l + 1.0);
+        if (D == 4) pref[l] = cx::neg1_pow(l) / (double)(l + 1);
+    }
+    if (P->fp64) CUDA_TRY(upload(P->d_pref, pref));
+    else CUDA_TRY(upload(P->d_pref, cast_vec<float>(pref)));
+    std::vector<int2> lam2;
+    std::vector<signed char> lamodd;
+    for (int i = 0; i < P->nlam; ++i) {
+        lam2.push_back(make_int2(P->lam[3 * i], P->lam[3 * i + 1]));
+        lamodd.push_back((signed char)((P->lam[3 * i] + P->lam[3 * i + 1] + P->lam[3 * i + 2]) & 1));
+    }
+    CUDA_TRY(upload(P->d_lam2, lam2));
+    CUDA_TRY(upload(P->d_lamodd, lamodd));
+    // key blocks: accumulators get what shared memory the per-primary copy leaves
+    CoupleParams cp{};
+    cp.D = D;
+    cp.N = P->N;
+    cp.nbins = nb;
+    cp.lmax = P->lmax;
+    cp.nq = P->nq;
+    cp.max_block_keys = 0;
+    const int base = couple_smem(cp, P->fp64);
+    const int comps = (P->N == 3 && D != 2) || (P->N == 4 && D == 3) ? 1 : 2;
+    const int budget = std::min(P->smem_optin, 160 * 1024) - base;
+    build_key_blocks(P, std::max(1, budget / (comps * tb)));
+    CUDA_TRY(upload(P->d_pairs, P->pairs));
+    CUDA_TRY(upload(P->d_pair_key, P->pair_key));
+    CUDA_TRY(upload(P->d_kblocks, P->kblocks));
+    return NPCF_OK;
+}
+
+npcf_status prepare_grid(npcf_plan_s* P, int64_t n)
+{
+    if (P->grid_n == n && P->grid_c > 0) return NPCF_OK;
+    GridChoice g = choose_grid(P, n);
+    if (g.c == 0)
+        return fail(NPCF_ERR_UNSUPPORTED, "no cell grid fits r_max=%g in the box (need r_max < box/2.25)",
+                    P->edges[P->nbins]);
+    P->grid_c = g.c;
+    for (int d = 0; d < 4; ++d) P->nc[d] = g.nc[d];
+    P->ncells = g.ncells;
+    P->nstencil = (int)g.stencil.size();
+    CUDA_TRY(upload(P->d_stencil, g.stencil));
+    P->grid_n = n;
+    return NPCF_OK;
+}
+
+npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int rows)
+{
+    const int rb = rec_bytes(P->D, P->fp64), tb = P->fp64 ? 8 : 4;
+    const size_t nc = (size_t)P->ncells;
+    auto R = [&](DevBuf& b, size_t bytes) -> npcf_status {
+        if (b.reserve(bytes) != cudaSuccess)
+            return fail(NPCF_ERR_WORKSPACE, "device allocation of %zu bytes failed", bytes);
+        return NPCF_OK;
+    };
+    npcf_status st;
+    if ((st = R(P->w_cid, sizeof(int) * (n + 1))) != NPCF_OK) return st;
+    if ((st = R(P->w_perm, sizeof(int) * (n + 1))) != NPCF_OK) return st;
+    if ((st = R(P->w_rec, (size_t)rb * (n + 1))) != NPCF_OK) return st;
+    // cells: count(nc+1) start(nc+1) fill(nc) lo prims pstart items istart (nc each) scan(8192)
+    if ((st = R(P->w_cells, sizeof(int) * (8 * nc + 16 + 8192))) != NPCF_OK) return st;
+    if ((st = R(P->w_items, sizeof(int4) * (n + nc + 1))) != NPCF_OK) return st;
+    if ((st = R(P->w_a, (size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins * P->nq)) != NPCF_OK) return st;
+    if ((st = R(P->w_wprim, (size_t)tb * std::max<int64_t>(nprim_max, 1))) != NPCF_OK) return st;
+    if ((st = R(P->w_partial, sizeof(double) * rows * 2 * P->ncoeff)) != NPCF_OK) return st;
+    if ((st = R(P->w_small, 64)) != NPCF_OK) return st;
+    return NPCF_OK;
+}
+
+npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, double* coeffs, int64_t pb, int64_t pe,
+                cudaStream_t s)
+{
+    npcf_status st;
+    if ((st = ensure_device(P)) != NPCF_OK) return st;
+    if ((st = prepare_grid(P, n)) != NPCF_OK) return st;
+    const int64_t nprim_max = pe - pb;
+    const int chunk = 128;
+    const int nkb = (int)P->kblocks.size();
+    int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
+    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim_max + chunk - 1) / chunk));
+    if ((st = reserve_workspace(P, n, nprim_max, rows)) != NPCF_OK) return st;
+
+    const int nc = P->ncells;
+    int* cells = P->w_cells.as<int>();
+    int* cell_count = cells;                // nc + 1
+    int* cell_start = cells + (nc + 1);     // nc + 1
+    int* cell_fill = cells + 2 * (nc + 1);  // nc
+    ItemBuffers ib;
+    ib.cell_lo = cell_fill + nc;
+    ib.cell_prims = ib.cell_lo + nc;
+    ib.prim_start = ib.cell_prims + nc;
+    ib.cell_items = ib.prim_start + nc;
+    ib.item_start = ib.cell_items + nc;
+    ib.scan_scratch = ib.item_start + nc;
+    int* small = P->w_small.as<int>();
+    ib.items = P->w_items.as<int4>();
+    ib.nitems = small + S_NITEMS;
+    ib.nprim = small + S_NPRIM;
+    ib.ticket = small + S_TICKET;
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(small + 4);
+
+    launch_counter() = 0;
+    P->timed = 0;
+    if (P->opts.timing) {
+        for (auto& e : P->ev)
+            if (!e) CUDA_TRY(cudaEventCreate(&e));
+        CUDA_TRY(cudaEventRecord(P->ev[0], s));
+    }
+    CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(int) * (3 * (size_t)nc + 2), s));
+    CUDA_TRY(cudaMemsetAsync(small, 0, 64, s));
+
+    CellParams cp{};
+    cp.D = P->D;
+    cp.n = n;
+    cp.ncells = nc;
+    cp.periodic = P->opts.periodic;
+    for (int d = 0; d < 4; ++d) {
+        cp.nc[d] = P->nc[d];
+        cp.box[d] = P->box[d];
+        cp.inv_side[d] = P->nc[d] / P->box[d];
+    }
+    cp.pos = pos;
+    cp.w = w;
+    cp.cid = P->w_cid.as<int>();
+    cp.cell_count = cell_count;
+    cp.cell_start = cell_start;
+    cp.cell_fill = cell_fill;
+    cp.perm = P->w_perm.as<int>();
+    cp.rec = P->w_rec.p;
+    cp.err = small + S_ERR;
+    CUDA_TRY(launch_cell_ids(cp, P->fp64, s));
+    CUDA_TRY(launch_exclusive_scan(cell_count, cell_start, nc + 1, ib.scan_scratch, s));
+    CUDA_TRY(launch_cell_scatter(cp, P->fp64, s));
+    CUDA_TRY(launch_make_items(ib, cell_start, cp.perm, nc, pb, pe, P->warps, s));
+
+    if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[1], s));
+    PairParams pp = P->pp;
+    int stride = 1;
+    for (int d = 0; d < P->D; ++d) {
+        pp.nc[d] = P->nc[d];
+        pp.stride[d] = stride;
+        stride *= P->nc[d];
+        pp.box[d] = P->box[d];
+        pp.boxf[d] = (float)P->box[d];
+        pp.side[d] = P->box[d] / P->nc[d];
+        pp.sidef[d] = (float)pp.side[d];
+    }
+    pp.nstencil = P->nstencil;
+    pp.stencil = P->d_stencil.as<int>();
+    pp.rec = P->w_rec.p;
+    pp.cell_start = cell_start;
+    pp.items = ib.items;
+    pp.nitems = ib.nitems;
+    pp.ticket = ib.ticket;
+    pp.a_out = P->w_a.p;
+    pp.w_out = P->w_wprim.p;
+    pp.stats = stats;
+    const int grid = P->nsm;
+    cudaError_t e;
+    if (P->D == 2) e = launch_pairs_d2(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
+    else if (P->D == 3) e = launch_pairs_d3(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
+    else e = launch_pairs_d4(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "pair kernel launch: %s", cudaGetErrorString(e));
+    if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[2], s));
+
+    CoupleParams kp{};
+    kp.D = P->D;
+    kp.N = P->N;
+    kp.nbins = P->nbins;
+    kp.lmax = P->lmax;
+    kp.nq = P->nq;
+    kp.nlam = P->nlam;
+    kp.a = P->w_a.p;
+    kp.wprim = P->w_wprim.p;
+    kp.nprim = ib.nprim;
+    kp.chunk = chunk;
+    kp.ncoeff = (int)P->ncoeff;
+    kp.partial = P->w_partial.as<double>();
+    kp.pairs = P->d_pairs.as<int2>();
+    kp.pair_key = P->d_pair_key.as<int>();
+    kp.kblocks = P->d_kblocks.as<int4>();
+    kp.nkb = nkb;
+    kp.max_block_keys = P->max_block_keys;
+    kp.lam2 = P->d_lam2.as<int2>();
+    kp.lam_odd = P->d_lamodd.as<signed char>();
+    kp.pref = P->d_pref.p;
+    CUDA_TRY(cudaMemsetAsync(kp.partial, 0, sizeof(double) * rows * 2 * P->ncoeff, s));
+    const int csm = couple_smem(kp, P->fp64);
+    e = launch_couple(kp, P->fp64, rows, csm, s);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
+    if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[3], s));
+    CUDA_TRY(launch_reduce(kp.partial, rows, (int)(2 * P->ncoeff), 1.0 / P->V, coeffs, s));
+    if (P->opts.timing) {
+        CUDA_TRY(cudaEventRecord(P->ev[4], s));
+        P->timed = 1;
+    }
+    P->last_launches = launch_counter();
+    CUDA_TRY(cudaMemcpyAsync(P->h_small, small, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 16, cudaMemcpyDeviceToHost, s));
+    P->last_stream = s;
+    P->last_nprim = nprim_max;
+    return NPCF_OK;
+}
+
+npcf_status check_flags(npcf_plan_s* P)
+{
+    if (P->h_small[S_ERR] & 1) return fail(NPCF_ERR_NONFINITE, "a position or weight is NaN or infinite");
+    if (P->h_small[S_ERR] & 2) return fail(NPCF_ERR_NONFINITE, "a position lies outside [0, box)");
+    return NPCF_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void npcf_default_opts(npcf_opts* o)
+{
+    if (!o) return;
+    o->precision = NPCF_FP32;
+    o->periodic = 1;
+    o->bin_order = NPCF_BINS_LE;
+    o->sync_check = 1;
+    o->timing = 0;
+}
+
+npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const double* edges, int nbins,
+                             const double* box, const npcf_opts* opts)
+{
+    if (!out) return fail(NPCF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (D < 2 || D > 4) return fail(NPCF_ERR_UNSUPPORTED, "D=%d not supported (2..4)", D);
+    if (N != 3 && N != 4) return fail(NPCF_ERR_UNSUPPORTED, "N=%d not supported (3 or 4)", N);
+    if (N == 4 && D == 4) return fail(NPCF_ERR_UNSUPPORTED, "N=4 needs the SO(4) coupling, not provided");
+    if (lmax < 0) return fail(NPCF_ERR_ARG, "lmax must be >= 0");
+    if (N == 4 && D == 3 && lmax > couple_max_lmax_d3n4())
+        return fail(NPCF_ERR_UNSUPPORTED, "N=4, D=3 supports lmax <= %d", couple_max_lmax_d3n4());
+    if (nbins < 1 || nbins > kMaxBins) return fail(NPCF_ERR_UNSUPPORTED, "nbins must be in [1, %d]", kMaxBins);
+    if (N == 4 && nbins < 3) return fail(NPCF_ERR_ARG, "N=4 needs at least 3 bins");
+    if (!edges || !box) return fail(NPCF_ERR_ARG, "bin_edges and box are required");
+    if (!(edges[0] >= 0.0) || !std::isfinite(edges[0])) return fail(NPCF_ERR_ARG, "bin_edges[0] must be >= 0");
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b + 1] > edges[b]) || !std::isfinite(edges[b + 1]))
+            return fail(NPCF_ERR_ARG, "bin_edges must be finite and strictly increasing");
+    npcf_opts o;
+    npcf_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != NPCF_FP32 && o.precision != NPCF_FP64) return fail(NPCF_ERR_ARG, "bad precision");
+    if (o.bin_order != NPCF_BINS_LE && o.bin_order != NPCF_BINS_LT) return fail(NPCF_ERR_ARG, "bad bin_order");
+    for (int d = 0; d < D; ++d) {
+        if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(NPCF_ERR_ARG, "box sides must be > 0");
+        if (o.periodic && !(edges[nbins] < 0.5 * box[d]))
+            return fail(NPCF_ERR_ARG, "periodic boxes need r_max < box/2 (axis %d)", d);
+    }
+    npcf_plan_s* P = new (std::nothrow) npcf_plan_s;
+    if (!P) return fail(NPCF_ERR_WORKSPACE, "out of host memory");
+    P->D = D;
+    P->N = N;
+    P->lmax = lmax;
+    P->nbins = nbins;
+    P->opts = o;
+    P->fp64 = o.precision == NPCF_FP64;
+    P->edges.assign(edges, edges + nbins + 1);
+    P->V = 1.0;
+    for (int d = 0; d < D; ++d) {
+        P->box[d] = box[d];
+        P->V *= box[d];
+    }
+    build_keys(P);
+    npcf_status st = ensure_device(P);
+    if (st == NPCF_OK) st = setup_tables(P);
+    if (st != NPCF_OK) {
+        npcf_plan_destroy(P);
+        return st;
+    }
+    *out = P;
+    return NPCF_OK;
+}
+
+npcf_status npcf_num_coeffs(npcf_plan_t P, int64_t* n)
+{
+    if (!P || !n) return fail(NPCF_ERR_ARG, "NULL argument");
+    *n = P->ncoeff;
+    return NPCF_OK;
+}
+
+npcf_status npcf_coeff_index(npcf_plan_t P, int64_t i, int* bins, int* ells)
+{
+    if (!P || !bins || !ells) return fail(NPCF_ERR_ARG, "NULL argument");
+    if (i < 0 || i >= P->ncoeff) return fail(NPCF_ERR_ARG, "index %lld out of range", (long long)i);
+    for (int k = 0; k < P->N - 1; ++k) bins[k] = P->key_bins[3 * i + k];
+    const int il = P->key_lam[i];
+    const int ne = P->N == 3 ? 1 : 3;
+    for (int k = 0; k < ne; ++k) ells[k] = P->lam[3 * il + k];
+    return NPCF_OK;
+}
+
+npcf_status npcf_compute(npcf_plan_t P, const void* pos, const void* w, int64_t n, double* coeffs, int64_t pb,
+                         int64_t pe, npcf_stream_t stream)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (n < 0 || n > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)n);
+    if (!coeffs) return fail(NPCF_ERR_ARG, "coeffs is NULL");
+    if (n > 0 && (!pos || !w)) return fail(NPCF_ERR_ARG, "positions/weights are NULL");
+    if (pb == 0 && pe == 0) pe = n;
+    if (pb < 0 || pe > n || pb > pe) return fail(NPCF_ERR_ARG, "primary range [%lld, %lld) outside [0, %lld)",
+                                                 (long long)pb, (long long)pe, (long long)n);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    npcf_status st = run(P, pos, w, n, coeffs, pb, pe, s);
+    if (st != NPCF_OK) return st;
+    if (P->opts.sync_check) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return check_flags(P);
+    }
+    return NPCF_OK;
+}
+
+npcf_status npcf_compute_host(npcf_plan_t P, const void* pos, const void* w, int64_t n, double* coeffs,
+                              int64_t pb, int64_t pe, npcf_stream_t stream)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (n < 0 || !coeffs || (n > 0 && (!pos || !w))) return fail(NPCF_ERR_ARG, "bad arguments");
+    npcf_status st = ensure_device(P);
+    if (st != NPCF_OK) return st;
+    const size_t tb = P->fp64 ? 8 : 4;
+    if (P->w_hpos.reserve(tb * P->D * std::max<int64_t>(n, 1)) != cudaSuccess ||
+        P->w_hw.reserve(tb * std::max<int64_t>(n, 1)) != cudaSuccess ||
+        P->w_hout.reserve(sizeof(double) * 2 * P->ncoeff + 16) != cudaSuccess)
+        return fail(NPCF_ERR_WORKSPACE, "device staging allocation failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n > 0) {
+        CUDA_TRY(cudaMemcpyAsync(P->w_hpos.p, pos, tb * P->D * n, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(P->w_hw.p, w, tb * n, cudaMemcpyHostToDevice, s));
+    }
+    if (pb == 0 && pe == 0) pe = n;
+    if (pb < 0 || pe > n || pb > pe) return fail(NPCF_ERR_ARG, "bad primary range");
+    st = run(P, P->w_hpos.p, P->w_hw.p, n, P->w_hout.as<double>(), pb, pe, s);
+    if (st != NPCF_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(coeffs, P->w_hout.p, sizeof(double) * 2 * P->ncoeff, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return check_flags(P);
+}
+
+npcf_status npcf_device_status(npcf_plan_t P)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    return check_flags(P);
+}
+
+npcf_status npcf_last_stats(npcf_plan_t P, int64_t* pairs, int64_t* primaries, int64_t* candidates)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    if (pairs) *pairs = (int64_t)P->h_stats[0];
+    if (candidates) *candidates = (int64_t)P->h_stats[1];
+    if (primaries) *primaries = (int64_t)P->h_small[S_NPRIM];
+    return NPCF_OK;
+}
+
+npcf_status npcf_last_profile(npcf_plan_t P, double* stage_ms, int* launches)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    if (launches) *launches = P->last_launches;
+    if (stage_ms) {
+        for (int i = 0; i < 4; ++i) {
+            float ms = -1.0f;
+            if (P->timed) CUDA_TRY(cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]));
+            stage_ms[i] = ms;
+        }
+    }
+    return NPCF_OK;
+}
+
+const char* npcf_last_error(void) { return g_err.c_str(); }
+
+void npcf_plan_destroy(npcf_plan_t P)
+{
+    if (!P) return;
+    DevBuf* bufs[] = {&P->d_tab,   &P->d_qnorm, &P->d_invvb, &P->d_pairs, &P->d_pair_key, &P->d_kblocks,
+                      &P->d_lam2,  &P->d_lamodd, &P->d_pref, &P->d_stencil, &P->w_cid,    &P->w_perm,
+                      &P->w_rec,   &P->w_cells, &P->w_items, &P->w_a,     &P->w_wprim,   &P->w_partial,
+                      &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout};
+    for (DevBuf* b : bufs) b->release();
+    if (P->h_small) cudaFreeHost(P->h_small);
+    for (auto& e : P->ev)
+        if (e) cudaEventDestroy(e);
+    delete P;
+}
+
+}  // extern "C"

@@ -1,0 +1,208 @@
+"""Thin ctypes binding of libnpcf (include/npcf.h).
+
+Every step of the estimator runs in the CUDA library; this module only checks
+arguments, passes pointers and sizes through the C ABI and wraps results in
+torch tensors (PyTorch is used for device memory and streams only).  It fails
+loudly when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnpcf.so")
+
+NPCF_OK = 0
+NPCF_FP64, NPCF_FP32 = 0, 1
+NPCF_BINS_LE, NPCF_BINS_LT = 0, 1
+STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPCF_ERR_CUDA",
+          -4: "NPCF_ERR_WORKSPACE", -5: "NPCF_ERR_DEVICE_TIMEOUT", -6: "NPCF_ERR_NONFINITE"}
+
+# every entry point declared in include/npcf.h
+EXPORTS = ("npcf_default_opts", "npcf_plan_create", "npcf_num_coeffs", "npcf_coeff_index", "npcf_compute",
+           "npcf_compute_host", "npcf_device_status", "npcf_last_stats", "npcf_last_profile", "npcf_last_error",
+           "npcf_plan_destroy")
+
+
+class NpcfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("periodic", ctypes.c_int), ("bin_order", ctypes.c_int),
+                ("sync_check", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnpcf.so (raises if it is missing: build it with paper_2106_10278_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libnpcf is not built ({path} missing); run python -m paper_2106_10278_gb300.build")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i32, i64 = ctypes.c_int, ctypes.c_int64
+        lib.npcf_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        lib.npcf_default_opts.restype = None
+        lib.npcf_plan_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, ctypes.POINTER(ctypes.c_double), i32,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Opts)]
+        lib.npcf_plan_create.restype = i32
+        lib.npcf_num_coeffs.argtypes = [P, ctypes.POINTER(i64)]
+        lib.npcf_num_coeffs.restype = i32
+        lib.npcf_coeff_index.argtypes = [P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.npcf_coeff_index.restype = i32
+        lib.npcf_compute.argtypes = [P, P, P, i64, P, i64, i64, P]
+        lib.npcf_compute.restype = i32
+        lib.npcf_compute_host.argtypes = [P, P, P, i64, P, i64, i64, P]
+        lib.npcf_compute_host.restype = i32
+        lib.npcf_device_status.argtypes = [P]
+        lib.npcf_device_status.restype = i32
+        lib.npcf_last_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.npcf_last_stats.restype = i32
+        lib.npcf_last_profile.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        lib.npcf_last_profile.restype = i32
+        lib.npcf_last_error.argtypes = []
+        lib.npcf_last_error.restype = ctypes.c_char_p
+        lib.npcf_plan_destroy.argtypes = [P]
+        lib.npcf_plan_destroy.restype = None
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != NPCF_OK:
+        msg = load_library().npcf_last_error().decode(errors="replace")
+        raise NpcfError(status, msg)
+
+
+class Plan:
+    """A plan for one (D, N, lmax, bins, box) estimator configuration.
+
+    precision: "fp32" (positions/weights float32; FP32 pair and coupling
+    arithmetic, FP64 sums over primaries) or "fp64" (double throughout).
+    """
+
+    def __init__(self, D, N, lmax, edges, box, *, precision="fp32", periodic=True, bin_lt=False, sync_check=True,
+                 timing=False):
+        lib = load_library()
+        self.D, self.N, self.lmax = int(D), int(N), int(lmax)
+        self.edges = np.ascontiguousarray(edges, dtype=np.float64)
+        self.box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (self.D,)))
+        self.nbins = len(self.edges) - 1
+        self.precision = precision
+        o = Opts()
+        lib.npcf_default_opts(ctypes.byref(o))
+        o.precision = NPCF_FP64 if precision == "fp64" else NPCF_FP32
+        o.periodic = int(bool(periodic))
+        o.bin_order = NPCF_BINS_LT if bin_lt else NPCF_BINS_LE
+        o.sync_check = int(bool(sync_check))
+        o.timing = int(bool(timing))
+        h = ctypes.c_void_p()
+        _check(lib.npcf_plan_create(ctypes.byref(h), self.D, self.N, self.lmax,
+                                    self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.nbins,
+                                    self.box.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(o)))
+        self._h = h
+        n = ctypes.c_int64()
+        _check(lib.npcf_num_coeffs(self._h, ctypes.byref(n)))
+        self.ncoeff = int(n.value)
+        self._keys = None
+
+    # ------------------------------------------------------------------
+    def keys(self) -> np.ndarray:
+        """(ncoeff, 6) int array: b1, b2, b3 (-1 if unused), l1, l2, l3 (0 if unused)."""
+        if self._keys is None:
+            lib = load_library()
+            k = np.zeros((self.ncoeff, 6), dtype=np.int32)
+            k[:, 2] = -1
+            bins = (ctypes.c_int * 3)()
+            ells = (ctypes.c_int * 3)()
+            for i in range(self.ncoeff):
+                _check(lib.npcf_coeff_index(self._h, i, bins, ells))
+                for a in range(self.N - 1):
+                    k[i, a] = bins[a]
+                for a in range(1 if self.N == 3 else 3):
+                    k[i, 3 + a] = ells[a]
+            self._keys = k
+        return self._keys
+
+    def _dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def compute(self, pos, w, primaries=None, out=None, stream=None):
+        """Coefficients on the device for device tensors pos (n, D) and w (n).
+
+        Returns a complex128 tensor of ncoeff entries (a view of `out`, a float64
+        tensor of 2*ncoeff, allocated if not given)."""
+        import torch
+        lib = load_library()
+        dt = self._dtype()
+        if not (pos.is_cuda and w.is_cuda):
+            raise ValueError("pos and w must be CUDA tensors (use compute_host for host arrays)")
+        if pos.dtype != dt or w.dtype != dt:
+            raise TypeError(f"pos and w must be {dt} for a {self.precision} plan")
+        if pos.dim() != 2 or pos.shape[1] != self.D or w.shape != (pos.shape[0],):
+            raise ValueError("pos must be (n, D) and w (n,)")
+        pos = pos.contiguous()
+        w = w.contiguous()
+        n = pos.shape[0]
+        if out is None:
+            out = torch.empty(2 * self.ncoeff, dtype=torch.float64, device=pos.device)
+        pb, pe = (0, n) if primaries is None else (int(primaries[0]), int(primaries[1]))
+        s = stream if stream is not None else torch.cuda.current_stream(pos.device)
+        with torch.cuda.device(pos.device):
+            _check(lib.npcf_compute(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(w.data_ptr()), n,
+                                    ctypes.c_void_p(out.data_ptr()), pb, pe, ctypes.c_void_p(s.cuda_stream)))
+        return torch.view_as_complex(out.view(-1, 2))
+
+    def compute_host(self, pos, w, primaries=None, stream=None) -> np.ndarray:
+        """Coefficients for host arrays (copied in and out by the library)."""
+        lib = load_library()
+        dt = np.float64 if self.precision == "fp64" else np.float32
+        pos = np.ascontiguousarray(pos, dtype=dt)
+        w = np.ascontiguousarray(w, dtype=dt)
+        n = pos.shape[0]
+        out = np.zeros(2 * self.ncoeff)
+        pb, pe = (0, n) if primaries is None else (int(primaries[0]), int(primaries[1]))
+        sptr = ctypes.c_void_p(None if stream is None else stream.cuda_stream)
+        _check(lib.npcf_compute_host(self._h, pos.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
+                                     n, out.ctypes.data_as(ctypes.c_void_p), pb, pe, sptr))
+        return out[0::2] + 1j * out[1::2]
+
+    def stats(self) -> dict:
+        """Pairs accumulated, primaries and candidate secondaries of the last call."""
+        lib = load_library()
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.npcf_last_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"pairs": a.value, "primaries": b.value, "candidates": c.value}
+
+    def profile(self) -> dict:
+        """Stage times (ms, CUDA events; -1 unless timing=True) and kernel launches of the last call."""
+        lib = load_library()
+        ms = (ctypes.c_double * 4)()
+        nl = ctypes.c_int()
+        _check(lib.npcf_last_profile(self._h, ms, ctypes.byref(nl)))
+        return {"cells_ms": ms[0], "pairs_ms": ms[1], "couple_ms": ms[2], "reduce_ms": ms[3], "launches": nl.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().npcf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
