@@ -252,6 +252,7 @@ def run_ours(args, rank, world):
     st = plan.stats()
     pairs_per_step = st["pairs"]
     nprim = st["primaries"]
+    cand_per_step = st["candidates"]
 
     clocks = ClockSampler()
     if world > 1:
@@ -324,7 +325,8 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == "d3n4" else args.workload, "n": wl.n,
-                   "primaries": nprim, "pairs_per_step": pairs_per_step, "ncoeff": plan.ncoeff,
+                   "primaries": nprim, "pairs_per_step": pairs_per_step, "candidates_per_step": cand_per_step,
+                   "ncoeff": plan.ncoeff,
                    "l2": "256 MB buffer written before every timed step (outside the events)"},
         "coeffs_per_s": coeffs_per_s, "coupling_terms_per_primary": terms,
         "stages_ms": {"cells": float(np.mean(cells_ms)), "pairs": float(np.mean(pair_ms)),

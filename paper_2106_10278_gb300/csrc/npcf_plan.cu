@@ -285,8 +285,10 @@ std::vector<int> make_stencil(int D, int c, const double* side, double reach)
 
 GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
 {
-    GridChoice best;
-    double best_cost = 1e300;
+    // Preferred: the cheapest grid with >= 4 particles per cell on average;
+    // otherwise (very sparse inputs) the cheapest valid grid of any density.
+    GridChoice best, any;
+    double best_cost = 1e300, any_cost = 1e300;
     const double rmax = P->edges[P->nbins];
     const double reach = rmax * (1.0 + 1e-6) + 1e-12;
     for (int c = 1; c <= 4; ++c) {
@@ -307,15 +309,18 @@ GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
         if (!ok || ncells >= (1 << 24)) continue;
         g.ncells = (int)ncells;
         const double npc = (double)std::max<int64_t>(n, 1) / (double)ncells;
-        if (c > 1 && npc < 4.0) continue;
         g.stencil = make_stencil(P->D, c, side, reach);
         const double cost = g.stencil.size() * (npc + 24.0);
-        if (cost < best_cost) {
+        if (cost < any_cost) {
+            any_cost = cost;
+            any = g;
+        }
+        if (npc >= 4.0 && cost < best_cost) {
             best_cost = cost;
             best = g;
         }
     }
-    return best;
+    return best.c > 0 ? best : any;
 }
 
 // ------------------------------------------------------------ lane map
