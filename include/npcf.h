@@ -138,6 +138,30 @@ NPCF_API npcf_status npcf_last_stats(npcf_plan_t plan, int64_t* pairs, int64_t* 
  */
 NPCF_API npcf_status npcf_last_profile(npcf_plan_t plan, double* stage_ms, int* launches);
 
+/*
+ * Allocation-free variant of npcf_compute (no counterpart in the paper; it is
+ * an operational entry point).  Same arguments, same results.  For callers
+ * that must not allocate device memory while running -- cudaMalloc
+ * synchronises the device and can fail under memory pressure, which real-time
+ * loops, processes whose caching allocator already holds the free memory, and
+ * work recorded into CUDA graphs cannot accept.  Create the plan during set-up
+ * (that allocates its tables once); this call then uses no cudaMalloc,
+ * cudaFree or allocating library routine: all of its device workspace comes
+ * from one static array of 16 MiB inside libnpcf (held by every GPU that loads
+ * the library until the process exits).
+ *   - Sizes whose workspace exceeds the array return NPCF_ERR_WORKSPACE with
+ *     the bytes needed (about n*(44 + nbins*nq*4) bytes for FP32, nq = 36 at
+ *     D=3, lmax=5, plus one row of partial sums; e.g. the D=3 4PCF with
+ *     lmax=5 and 10 bins fits n up to about 10,000).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array and clears what must start at zero;
+ *     calls whose GPU work overlaps (two streams, two threads) race on it.
+ */
+NPCF_API npcf_status npcf_compute_noalloc(npcf_plan_t plan, const void* positions, const void* weights, int64_t n,
+                                          double* coeffs, int64_t primary_begin, int64_t primary_end,
+                                          npcf_stream_t stream);
+
 /* Thread-local description of the most recent error on this thread. */
 NPCF_API const char* npcf_last_error(void);
 

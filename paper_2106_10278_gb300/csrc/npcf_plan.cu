@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -853,3 +854,224 @@ void npcf_plan_destroy(npcf_plan_t P)
 }
 
 }  // extern "C"
+
+// ======================================================= allocation-free entry
+// npcf_compute_noalloc: the npcf_compute pipeline with every device buffer it
+// needs at compute time carved out of one file-scope __device__ array instead
+// of plan workspace.  It exists for callers that must not allocate device
+// memory once they are running: cudaMalloc synchronises the whole device and
+// may fail under memory pressure, which real-time loops, code that shares the
+// GPU with a caching allocator that owns all free memory, and code recorded
+// into a CUDA graph cannot accept.  Such callers create the plan (which
+// allocates its small tables once) during set-up and then call this.
+//
+// The array below is part of the module: every GPU that loads libnpcf holds
+// its kNoallocBytes until the process exits.  Host code must not use the
+// symbol name as an address; the device address is obtained once per device
+// with cudaGetSymbolAddress on the first call made on that device (so that
+// first call should happen before any stream capture begins).
+namespace {
+
+constexpr size_t kNoallocBytes = size_t(16) << 20;  // 16 MiB of static scratch
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+npcf_status noalloc_scratch(int dev, unsigned char** out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return fail(NPCF_ERR_UNSUPPORTED, "device index %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return fail(NPCF_ERR_CUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    return NPCF_OK;
+}
+
+// bump allocator over the static scratch (256-byte aligned pieces)
+struct Carve {
+    unsigned char* base;
+    size_t used = 0;
+    size_t need = 0;
+    void* take(size_t bytes)
+    {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + bytes;
+        need = used;
+        return used <= kNoallocBytes ? base + off : nullptr;
+    }
+};
+
+npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t n, double* coeffs, int64_t pb,
+                        int64_t pe, cudaStream_t s)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != P->device) return fail(NPCF_ERR_ARG, "plan was created on device %d, current device is %d", P->device, dev);
+    unsigned char* base = nullptr;
+    npcf_status st = noalloc_scratch(dev, &base);
+    if (st != NPCF_OK) return st;
+
+    GridChoice g = choose_grid(P, n);
+    if (g.c == 0) return fail(NPCF_ERR_UNSUPPORTED, "no cell grid fits r_max in the box");
+    const int nc = g.ncells;
+    const int64_t nprim_max = pe - pb;
+    const int chunk = 128;
+    const int nkb = (int)P->kblocks.size();
+    const int rb = rec_bytes(P->D, P->fp64), tb = P->fp64 ? 8 : 4;
+
+    Carve cv{base};
+    int* stencil = static_cast<int*>(cv.take(sizeof(int) * g.stencil.size()));
+    int* cid = static_cast<int*>(cv.take(sizeof(int) * (n + 1)));
+    int* perm = static_cast<int*>(cv.take(sizeof(int) * (n + 1)));
+    void* rec = cv.take((size_t)rb * (n + 1));
+    int* cells = static_cast<int*>(cv.take(sizeof(int) * (8 * (size_t)nc + 16 + 8192)));
+    int4* items = static_cast<int4*>(cv.take(sizeof(int4) * (n + nc + 1)));
+    void* a = cv.take((size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins * P->nq);
+    void* wprim = cv.take((size_t)tb * std::max<int64_t>(nprim_max, 1));
+    int* small = static_cast<int*>(cv.take(64));
+    const size_t row_bytes = sizeof(double) * 2 * P->ncoeff;
+    size_t left = cv.used <= kNoallocBytes ? kNoallocBytes - ((cv.used + 255) & ~size_t(255)) : 0;
+    int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
+    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim_max + chunk - 1) / chunk));
+    rows = (int)std::min<size_t>((size_t)rows, left / row_bytes);
+    if (cv.used > kNoallocBytes || rows < 1) {
+        size_t need = ((cv.need + 255) & ~size_t(255)) + row_bytes;
+        return fail(NPCF_ERR_WORKSPACE,
+                    "npcf_compute_noalloc needs %zu bytes of scratch for n=%lld; its static scratch holds %zu",
+                    need, (long long)n, kNoallocBytes);
+    }
+    double* partial = static_cast<double*>(cv.take(row_bytes * rows));
+
+    CUDA_TRY(cudaMemcpyAsync(stencil, g.stencil.data(), sizeof(int) * g.stencil.size(), cudaMemcpyHostToDevice, s));
+    int* cell_count = cells;
+    int* cell_start = cells + (nc + 1);
+    int* cell_fill = cells + 2 * (nc + 1);
+    ItemBuffers ib;
+    ib.cell_lo = cell_fill + nc;
+    ib.cell_prims = ib.cell_lo + nc;
+    ib.prim_start = ib.cell_prims + nc;
+    ib.cell_items = ib.prim_start + nc;
+    ib.item_start = ib.cell_items + nc;
+    ib.scan_scratch = ib.item_start + nc;
+    ib.items = items;
+    ib.nitems = small + S_NITEMS;
+    ib.nprim = small + S_NPRIM;
+    ib.ticket = small + S_TICKET;
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(small + 4);
+    launch_counter() = 0;
+    P->timed = 0;
+    CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(int) * (3 * (size_t)nc + 2), s));
+    CUDA_TRY(cudaMemsetAsync(small, 0, 64, s));
+
+    CellParams cp{};
+    cp.D = P->D;
+    cp.n = n;
+    cp.ncells = nc;
+    cp.periodic = P->opts.periodic;
+    for (int d = 0; d < 4; ++d) {
+        cp.nc[d] = g.nc[d];
+        cp.box[d] = P->box[d];
+        cp.inv_side[d] = g.nc[d] / P->box[d];
+    }
+    cp.pos = pos;
+    cp.w = w;
+    cp.cid = cid;
+    cp.cell_count = cell_count;
+    cp.cell_start = cell_start;
+    cp.cell_fill = cell_fill;
+    cp.perm = perm;
+    cp.rec = rec;
+    cp.err = small + S_ERR;
+    CUDA_TRY(launch_cell_ids(cp, P->fp64, s));
+    CUDA_TRY(launch_exclusive_scan(cell_count, cell_start, nc + 1, ib.scan_scratch, s));
+    CUDA_TRY(launch_cell_scatter(cp, P->fp64, s));
+    CUDA_TRY(launch_make_items(ib, cell_start, perm, nc, pb, pe, P->warps, s));
+
+    PairParams pp = P->pp;
+    int stride = 1;
+    for (int d = 0; d < P->D; ++d) {
+        pp.nc[d] = g.nc[d];
+        pp.stride[d] = stride;
+        stride *= g.nc[d];
+        pp.box[d] = P->box[d];
+        pp.boxf[d] = (float)P->box[d];
+        pp.side[d] = P->box[d] / g.nc[d];
+        pp.sidef[d] = (float)pp.side[d];
+    }
+    pp.nstencil = (int)g.stencil.size();
+    pp.stencil = stencil;
+    pp.rec = rec;
+    pp.cell_start = cell_start;
+    pp.items = ib.items;
+    pp.nitems = ib.nitems;
+    pp.ticket = ib.ticket;
+    pp.a_out = a;
+    pp.w_out = wprim;
+    pp.stats = stats;
+    cudaError_t e;
+    if (P->D == 2) e = launch_pairs_d2(pp, P->fp64, P->Lc, P->nsm, P->pair_smem, s);
+    else if (P->D == 3) e = launch_pairs_d3(pp, P->fp64, P->Lc, P->nsm, P->pair_smem, s);
+    else e = launch_pairs_d4(pp, P->fp64, P->Lc, P->nsm, P->pair_smem, s);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "pair kernel launch: %s", cudaGetErrorString(e));
+
+    CoupleParams kp{};
+    kp.D = P->D;
+    kp.N = P->N;
+    kp.nbins = P->nbins;
+    kp.lmax = P->lmax;
+    kp.nq = P->nq;
+    kp.nlam = P->nlam;
+    kp.a = a;
+    kp.wprim = wprim;
+    kp.nprim = ib.nprim;
+    kp.chunk = chunk;
+    kp.ncoeff = (int)P->ncoeff;
+    kp.partial = partial;
+    kp.pairs = P->d_pairs.as<int2>();
+    kp.pair_key = P->d_pair_key.as<int>();
+    kp.kblocks = P->d_kblocks.as<int4>();
+    kp.nkb = nkb;
+    kp.max_block_keys = P->max_block_keys;
+    kp.lam2 = P->d_lam2.as<int2>();
+    kp.lam_odd = P->d_lamodd.as<signed char>();
+    kp.pref = P->d_pref.p;
+    CUDA_TRY(cudaMemsetAsync(partial, 0, row_bytes * rows, s));
+    e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
+    CUDA_TRY(launch_reduce(partial, rows, (int)(2 * P->ncoeff), 1.0 / P->V, coeffs, s));
+    P->last_launches = launch_counter();
+    CUDA_TRY(cudaMemcpyAsync(P->h_small, small, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 16, cudaMemcpyDeviceToHost, s));
+    P->last_stream = s;
+    P->last_nprim = nprim_max;
+    return NPCF_OK;
+}
+
+}  // namespace
+
+extern "C" npcf_status npcf_compute_noalloc(npcf_plan_t P, const void* pos, const void* w, int64_t n,
+                                            double* coeffs, int64_t pb, int64_t pe, npcf_stream_t stream)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (n < 0 || n > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)n);
+    if (!coeffs) return fail(NPCF_ERR_ARG, "coeffs is NULL");
+    if (n > 0 && (!pos || !w)) return fail(NPCF_ERR_ARG, "positions/weights are NULL");
+    if (pb == 0 && pe == 0) pe = n;
+    if (pb < 0 || pe > n || pb > pe) return fail(NPCF_ERR_ARG, "primary range [%lld, %lld) outside [0, %lld)",
+                                                 (long long)pb, (long long)pe, (long long)n);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    npcf_status st = run_noalloc(P, pos, w, n, coeffs, pb, pe, s);
+    if (st != NPCF_OK) return st;
+    if (P->opts.sync_check) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return check_flags(P);
+    }
+    return NPCF_OK;
+}

@@ -25,7 +25,7 @@ STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPC
 # every entry point declared in include/npcf.h
 EXPORTS = ("npcf_default_opts", "npcf_plan_create", "npcf_num_coeffs", "npcf_coeff_index", "npcf_compute",
            "npcf_compute_host", "npcf_device_status", "npcf_last_stats", "npcf_last_profile", "npcf_last_error",
-           "npcf_plan_destroy")
+           "npcf_plan_destroy", "npcf_compute_noalloc")
 
 
 class NpcfError(RuntimeError):
@@ -65,6 +65,8 @@ def load_library(path: str = LIB_PATH):
         lib.npcf_coeff_index.restype = i32
         lib.npcf_compute.argtypes = [P, P, P, i64, P, i64, i64, P]
         lib.npcf_compute.restype = i32
+        lib.npcf_compute_noalloc.argtypes = [P, P, P, i64, P, i64, i64, P]
+        lib.npcf_compute_noalloc.restype = i32
         lib.npcf_compute_host.argtypes = [P, P, P, i64, P, i64, i64, P]
         lib.npcf_compute_host.restype = i32
         lib.npcf_device_status.argtypes = [P]
