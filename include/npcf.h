@@ -162,6 +162,15 @@ NPCF_API npcf_status npcf_compute_noalloc(npcf_plan_t plan, const void* position
                                           double* coeffs, int64_t primary_begin, int64_t primary_end,
                                           npcf_stream_t stream);
 
+/*
+ * Work counters of the pair kernel in the last call (host, waits for its
+ * stream), for profiling: [0] pairs, [1] candidate secondaries examined,
+ * [2] consumption rounds, [3] lanes that found work in those rounds,
+ * [4] 32-candidate chunks scanned, [5] rounds forced by full queues.
+ * Writes min(n, 6) entries (the rest zero).
+ */
+NPCF_API npcf_status npcf_last_counters(npcf_plan_t plan, int64_t* counters, int n);
+
 /* Thread-local description of the most recent error on this thread. */
 NPCF_API const char* npcf_last_error(void);
 

@@ -63,6 +63,8 @@ struct PairParams {
     signed char bin_nlanes[kMaxBins];
     signed char bin_first[kMaxBins];
     int warps;                   // primaries per item (= warps per CTA)
+    int busy_round;              // run a consumption round when this many lanes have work
+    int tot_round;               // ... or when this many pairs are staged in total
     int nstencil;
     const int* stencil;          // packed offsets, 8 bits per axis (signed)
     const unsigned char* tab;    // kTab entries
@@ -75,7 +77,7 @@ struct PairParams {
     const void* inv_vb;          // nbins (T)
     void* a_out;                 // nprim x nbins x nq (T)
     void* w_out;                 // nprim (T)
-    unsigned long long* stats;   // [0] pairs, [1] candidates
+    unsigned long long* stats;   // [0] pairs, [1] candidates, [2] rounds, [3] busy lanes, [4] chunks, [5] forced rounds
 };
 
 // ----------------------------------------------------------- coupling kernel

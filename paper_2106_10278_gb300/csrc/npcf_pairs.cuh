@@ -32,18 +32,31 @@ struct PairCfg {
     static constexpr int kThreads = (sizeof(T) == 4) ? (NQ <= 64 ? 512 : 256) : (NQ <= 40 ? 256 : 128);
 };
 
-// shared-memory bytes of one CTA (must match the carve-up in k_pairs)
+constexpr int kPool = 320;      // staged pairs per warp (shared by all bins)
+constexpr int kQCap = 128;      // entries of one bin's index queue
+
+// Shared-memory carve-up of one CTA (host and device must agree):
+//   2 candidate tiles of `threads` records | radial table + edges + lane map (kTab + 576)
+//   | per warp: [qcnt[32] ints | ftop + pad | fstack[kPool] u16 | binq[nbins][kQCap] u16 | pool]
+// where the pool region also holds the final cross-lane reduction scratch.
+__host__ __device__ inline int pair_pool_bytes(int rec_bytes, int t_bytes, int nq_compiled)
+{
+    const int pool = kPool * rec_bytes;
+    const int scratch = 32 * (nq_compiled + 1) * t_bytes;
+    return pool > scratch ? pool : scratch;
+}
+
 __host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int nbins, int nq_compiled)
 {
-    int stage = nbins * kStageCap * rec_bytes;
-    int scratch = 32 * (nq_compiled + 1) * t_bytes;
-    int body = stage > scratch ? stage : scratch;
-    return ((128 + body) + 15) / 16 * 16;
+    const int head = 128 + 16 + kPool * 2 + nbins * kQCap * 2;
+    return ((head + 15) / 16) * 16 + ((pair_pool_bytes(rec_bytes, t_bytes, nq_compiled) + 15) / 16) * 16;
 }
+
+constexpr int kMaxJobs = 1024;  // neighbour cells of one item (the host keeps stencils this small)
 
 __host__ __device__ inline int pair_fixed_bytes(int rec_bytes, int threads)
 {
-    return threads * rec_bytes + kTab + 576;
+    return 2 * threads * rec_bytes + kTab + 576 + (3 * kMaxJobs + 4 + 72) * 4;
 }
 
 template <int D, int LMAX, typename T>
@@ -57,6 +70,83 @@ __device__ __forceinline__ void accum_pair(T* acc, const Rec<D, T>& e)
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Exclusive block-wide scan of two ints per thread (deterministic), totals
+// returned to every thread.  `ws` holds 2 * 32 ints of shared scratch.
+__device__ __forceinline__ void block_scan2(int a, int b, int* ea, int* eb, int* ta, int* tb, int* ws)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int xa = __shfl_up_sync(0xffffffffu, ia, o);
+        const int xb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += xa;
+            ib += xb;
+        }
+    }
+    if (lane == 31) {
+        ws[warp] = ia;
+        ws[32 + warp] = ib;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int va = lane < nw ? ws[lane] : 0, vb = lane < nw ? ws[32 + lane] : 0;
+        int sa = va, sb = vb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int xa = __shfl_up_sync(0xffffffffu, sa, o);
+            const int xb = __shfl_up_sync(0xffffffffu, sb, o);
+            if (lane >= o) {
+                sa += xa;
+                sb += xb;
+            }
+        }
+        ws[lane] = sa - va;  // exclusive warp offsets
+        ws[32 + lane] = sb - vb;
+        if (lane == 31) {
+            ws[64] = sa;
+            ws[65] = sb;
+        }
+    }
+    __syncthreads();
+    *ea = ws[warp] + ia - a;
+    *eb = ws[32 + warp] + ib - b;
+    *ta = ws[64];
+    *tb = ws[65];
+    __syncthreads();
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void prefetch_records(Rec<D, T>* dst, const Rec<D, T>* rec, const int* job_a,
+                                                 const int* job_pre, int njobs, int T0, int tn)
+{
+    constexpr int kChunks = sizeof(Rec<D, T>) / 16;
+    if ((int)threadIdx.x < tn) {
+        const int v = T0 + threadIdx.x;
+        int lo = 0, hi = njobs;  // job j with job_pre[j] <= v < job_pre[j+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (job_pre[mid] <= v) lo = mid;
+            else hi = mid;
+        }
+        const Rec<D, T>* src = rec + job_a[lo] + (v - job_pre[lo]);
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c)
+            cp_async16(reinterpret_cast<char*>(dst + threadIdx.x) + 16 * c, reinterpret_cast<const char*>(src) + 16 * c);
+    }
+    cp_async_commit();
+}
+
 template <int D, int LMAX, typename T>
 __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(const PairParams p)
 {
@@ -68,18 +158,26 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     extern __shared__ __align__(16) unsigned char smem[];
     const int nthreads = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int nbins = p.nbins;
-    R* tile = reinterpret_cast<R*>(smem);
-    unsigned char* tab = smem + nthreads * sizeof(R);
-    float* s_edge = reinterpret_cast<float*>(tab + kTab);        // nbins + 1
-    double* s_edge2 = reinterpret_cast<double*>(tab + kTab + 192); // nbins + 1
+    R* tiles = reinterpret_cast<R*>(smem);  // [2][nthreads]
+    unsigned char* tab = smem + 2 * nthreads * sizeof(R);
+    float* s_edge = reinterpret_cast<float*>(tab + kTab);          // nbins + 1
+    double* s_edge2 = reinterpret_cast<double*>(tab + kTab + 192);  // nbins + 1
     signed char* s_first = reinterpret_cast<signed char*>(tab + kTab + 192 + 272);
     signed char* s_nl = s_first + 32;
+    int* job_a = reinterpret_cast<int*>(tab + kTab + 576);  // kMaxJobs: first slot of the cell
+    int* job_pk = job_a + kMaxJobs;                          // kMaxJobs: packed stencil offset
+    int* job_pre = job_pk + kMaxJobs;                        // kMaxJobs + 1: record prefix
+    int* ws = job_pre + kMaxJobs + 4;                        // 68 ints of scan scratch
     unsigned char* wbase = smem + pair_fixed_bytes(sizeof(R), nthreads) +
                            warp * pair_warp_bytes(sizeof(R), sizeof(T), nbins, NQ);
-    int* cnt = reinterpret_cast<int*>(wbase);
-    R* stage = reinterpret_cast<R*>(wbase + 128);
-    T* scratch = reinterpret_cast<T*>(wbase + 128);
+    int* qcnt = reinterpret_cast<int*>(wbase);
+    int* ftop = reinterpret_cast<int*>(wbase + 128);
+    unsigned short* fstack = reinterpret_cast<unsigned short*>(wbase + 144);
+    unsigned short* binq = fstack + kPool;
+    R* pool = reinterpret_cast<R*>(wbase + ((128 + 16 + kPool * 2 + nbins * kQCap * 2 + 15) / 16) * 16);
+    T* scratch = reinterpret_cast<T*>(pool);
 
     for (int i = threadIdx.x; i < kTab / 4; i += nthreads)
         reinterpret_cast<int*>(tab)[i] = reinterpret_cast<const int*>(p.tab)[i];
@@ -94,6 +192,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     const int mybin = p.lane_bin[lane];
     const int myrank = p.lane_rank[lane];
     const int mynl = p.bin_nlanes[mybin];
+    const int lane_nl = lane < nbins ? p.bin_nlanes[lane] : 0;
     const T* qnorm = static_cast<const T*>(p.qnorm);
     const T* inv_vb = static_cast<const T*>(p.inv_vb);
     const R* rec = static_cast<const R*>(p.rec);
@@ -113,10 +212,50 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         const int pidx = it.w + warp;
 
         int cc[D];
-        {
 #pragma unroll
-            for (int d = 0; d < D; ++d) cc[d] = (it.x / p.stride[d]) % p.nc[d];
+        for (int d = 0; d < D; ++d) cc[d] = (it.x / p.stride[d]) % p.nc[d];
+
+        // the item's neighbour cells: valid (periodic or inside the grid) and non-empty,
+        // in stencil order, with the prefix of their record counts
+        int njobs = 0, V = 0;
+        for (int base = 0; base < p.nstencil; base += nthreads) {
+            const int sidx = base + threadIdx.x;
+            int keep = 0, len = 0, a = 0, pk = 0;
+            if (sidx < p.nstencil) {
+                pk = p.stencil[sidx];
+                int cell = 0;
+                bool ok = true;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    int c = cc[d] + (int)(signed char)((pk >> (8 * d)) & 0xff);
+                    if (c < 0) {
+                        ok = ok && p.periodic;
+                        c += p.nc[d];
+                    } else if (c >= p.nc[d]) {
+                        ok = ok && p.periodic;
+                        c -= p.nc[d];
+                    }
+                    cell += c * p.stride[d];
+                }
+                if (ok) {
+                    a = p.cell_start[cell];
+                    len = p.cell_start[cell + 1] - a;
+                    keep = len > 0;
+                }
+            }
+            int pos, off, tcount, tlen;
+            block_scan2(keep, keep ? len : 0, &pos, &off, &tcount, &tlen, ws);
+            if (keep) {
+                job_a[njobs + pos] = a;
+                job_pk[njobs + pos] = pk;
+                job_pre[njobs + pos] = V + off;
+            }
+            njobs += tcount;
+            V += tlen;
         }
+        if (threadIdx.x == 0) job_pre[njobs] = V;
+        __syncthreads();
+
         const R pj = rec[jslot];
         T xj[D];
 #pragma unroll
@@ -126,99 +265,140 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         T acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = T(0);
-        if (lane < nbins) cnt[lane] = 0;
+        if (lane < nbins) qcnt[lane] = 0;
+        for (int i = lane; i < kPool; i += 32) fstack[i] = (unsigned short)i;
+        if (lane == 0) *ftop = kPool;
         __syncwarp();
         unsigned npairs = 0;
         unsigned long long ncand = 0;
+        unsigned nrounds = 0, nbusy = 0, nchunks = 0, nforced = 0;
 
-        // one consumption round: every lane pops one pair of its own bin
+        // one consumption round: every lane pops one staged pair of its own bin
         auto round = [&]() {
-            const int q = cnt[mybin];
-            if (myrank < q) {
-                const R e = stage[mybin * kStageCap + (q - 1 - myrank)];
+            const int q = qcnt[mybin];
+            const bool has = myrank < q;
+            ++nrounds;
+            nbusy += has ? 1u : 0u;
+            int idx = 0;
+            if (has) {
+                idx = binq[mybin * kQCap + (q - 1 - myrank)];
+                const R e = pool[idx];
                 accum_pair<D, LMAX, T>(acc, e);
             }
+            const unsigned fm = __ballot_sync(full, has);
+            const int ft = *ftop;
             __syncwarp();
-            if (myrank == 0) cnt[mybin] = q > mynl ? q - mynl : 0;
+            if (has) fstack[ft + __popc(fm & lt_mask)] = (unsigned short)idx;
+            if (lane == 0) *ftop = ft + __popc(fm);
+            if (myrank == 0) qcnt[mybin] = q > mynl ? q - mynl : 0;
             __syncwarp();
         };
-
-        for (int s = 0; s < p.nstencil; ++s) {
-            const int packed = p.stencil[s];
-            int ncell = 0;
-            bool cell_ok = true;
-            T xjs[D];
-            double shd[D];
-            T dmin2 = T(0), dmax2 = T(0);
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int o = (int)(signed char)((packed >> (8 * d)) & 0xff);
-                int c = cc[d] + o;
-                const T lo = T((double)c * p.side[d]);
-                const T hi = T((double)(c + 1) * p.side[d]);
-                double sh = 0.0;
-                if (c < 0) {
-                    cell_ok = cell_ok && p.periodic;
-                    c += p.nc[d];
-                    sh = -p.box[d];
-                } else if (c >= p.nc[d]) {
-                    cell_ok = cell_ok && p.periodic;
-                    c -= p.nc[d];
-                    sh = p.box[d];
-                }
-                ncell += c * p.stride[d];
-                shd[d] = sh;
-                xjs[d] = T((double)xj[d] - sh);
-                const T a = fmax(fmax(lo - xj[d], xj[d] - hi), T(0));
-                dmin2 = fma(a, a, dmin2);
-                const T b = fmax(fabs(xj[d] - lo), fabs(xj[d] - hi));
-                dmax2 = fma(b, b, dmax2);
+        auto consume = [&](bool drain) {
+            for (;;) {
+                const int qv = lane < nbins ? qcnt[lane] : 0;
+                const int busy = __reduce_add_sync(full, qv < lane_nl ? qv : lane_nl);
+                const int tot = __reduce_add_sync(full, qv);
+                if (tot == 0) break;
+                const bool over = __any_sync(full, qv > kQCap - 32) || tot > kPool - 32;
+                const bool want = busy >= p.busy_round || tot >= p.tot_round;
+                if (!drain && !want && !over) break;
+                if (!drain && !want) ++nforced;
+                round();
             }
-            if (!cell_ok) continue;  // CTA-uniform
-            const bool skip = !active || dmin2 >= T(p.rmax2f) || dmax2 < T(p.rmin2f);
-            const int start = p.cell_start[ncell], end = p.cell_start[ncell + 1];
-            for (int t0 = start; t0 < end; t0 += nthreads) {
-                const int tn = min(nthreads, end - t0);
-                __syncthreads();
-                if (threadIdx.x < tn) tile[threadIdx.x] = rec[t0 + threadIdx.x];
-                __syncthreads();
-                if (skip) continue;
-                ncand += tn;
-                for (int c0 = 0; c0 < tn; c0 += 32) {
+        };
+
+        int buf = 0;
+        if (V > 0) prefetch_records<D, T>(tiles, rec, job_a, job_pre, njobs, 0, min(nthreads, V));
+        for (int T0 = 0; T0 < V; T0 += nthreads) {
+            const int tn = min(nthreads, V - T0);
+            if (T0 + nthreads < V) {
+                prefetch_records<D, T>(tiles + (buf ^ 1) * nthreads, rec, job_a, job_pre, njobs, T0 + nthreads,
+                                       min(nthreads, V - T0 - nthreads));
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const R* tile = tiles + buf * nthreads;
+            // the cells (segments) this tile covers
+            int j;
+            {
+                int lo = 0, hi = njobs;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (job_pre[mid] <= T0) lo = mid;
+                    else hi = mid;
+                }
+                j = lo;
+            }
+            for (; j < njobs && job_pre[j] < T0 + tn; ++j) {
+                if (!active) continue;
+                const int seg_lo = max(job_pre[j], T0) - T0;
+                const int seg_hi = min(job_pre[j + 1], T0 + tn) - T0;
+                const int packed = job_pk[j];
+                // geometry of this cell for this warp's primary, in T (FP32 on the FP32 path;
+                // the exact FP64 image shift is rebuilt only for ambiguous pairs)
+                T xjs[D];
+                T dmin2 = T(0), dmax2 = T(0);
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
+                    T side, box;
+                    if constexpr (kFP32) {
+                        side = p.sidef[d];
+                        box = p.boxf[d];
+                    } else {
+                        side = p.side[d];
+                        box = p.box[d];
+                    }
+                    const T lo = T(c) * side;
+                    const T hi = lo + side;
+                    const T sh = c < 0 ? -box : (c >= p.nc[d] ? box : T(0));
+                    xjs[d] = xj[d] - sh;
+                    const T a = fmax(fmax(lo - xj[d], xj[d] - hi), T(0));
+                    dmin2 = fma(a, a, dmin2);
+                    const T b = fmax(fabs(xj[d] - lo), fabs(xj[d] - hi));
+                    dmax2 = fma(b, b, dmax2);
+                }
+                if (dmin2 >= T(p.rmax2f) || dmax2 < T(p.rmin2f)) continue;
+                ncand += seg_hi - seg_lo;
+                for (int c0 = seg_lo; c0 < seg_hi; c0 += 32) {
                     const int k = c0 + lane;
-                    const bool valid = k < tn;
-                    R pk = tile[valid ? k : 0];
+                    const bool valid = k < seg_hi;
+                    R pk = tile[valid ? k : seg_lo];
                     T dx[D];
                     T r2 = T(0);
 #pragma unroll
                     for (int d = 0; d < D; ++d) {
                         if constexpr (kFP32) dx[d] = pk.x(d) - xjs[d];
-                        else dx[d] = (pk.x(d) - xj[d]) + T(shd[d]);
+                        else dx[d] = (pk.x(d) - xj[d]) + (xj[d] - xjs[d]);
                         r2 = fma(dx[d], dx[d], r2);
                     }
                     int bin = -1;
-                    T rinv = T(0);
                     if (valid && r2 > T(0) && r2 < T(p.rmax2f) && r2 >= T(p.rmin2f)) {
-                        rinv = rsqrt_t(r2);
-                        const float r = (float)(r2 * rinv);
-                        int b;
-                        if (r < s_edge[0]) {
-                            b = -1;
-                        } else {
-                            int kk = (int)((r - p.tab_lo) * p.tab_inv);
-                            kk = kk < 0 ? 0 : (kk >= kTab ? kTab - 1 : kk);
-                            b = tab[kk];
-                            while (b < nbins && r >= s_edge[b + 1]) ++b;
+                        // radial table over r^2: bits 0-5 the bin (63: none), bit 6 set when an
+                        // edge lies within the FP32 error window of the bucket
+                        int kk = (int)(((float)r2 - p.tab_lo) * p.tab_inv);
+                        kk = kk < 0 ? 0 : (kk >= kTab ? kTab - 1 : kk);
+                        const int code = tab[kk];
+                        int b = (code & 63) == 63 ? -1 : (code & 63);
+                        bool exact = !kFP32;
+                        if (kFP32 && (code & 64)) {
+                            // an edge is close: decide in FP32 unless within its error window
+                            const float r = (float)r2 * rsqrtf((float)r2);
+                            int bb = 0;
+                            while (bb <= nbins && r >= s_edge[bb]) ++bb;
+                            b = (bb >= 1 && bb <= nbins) ? bb - 1 : -1;
+                            exact = (bb >= 1 && r - s_edge[bb - 1] < tol) || (bb <= nbins && s_edge[bb] - r < tol);
                         }
-                        const int blo = b < 0 ? 0 : b;
-                        const int bhi = b + 1 > nbins ? nbins : (b + 1 < 0 ? 0 : b + 1);
-                        const bool near = !kFP32 || fabsf(r - s_edge[blo]) < tol || fabsf(r - s_edge[bhi]) < tol;
-                        if (near) {
+                        if (exact) {
                             // exact decision from the original coordinates, as the definition makes it
                             double sd = 0.0;
 #pragma unroll
                             for (int d = 0; d < D; ++d) {
-                                const double dd = __dadd_rn(__dadd_rn((double)pk.x(d), -(double)xj[d]), shd[d]);
+                                const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
+                                const double shd = c < 0 ? -p.box[d] : (c >= p.nc[d] ? p.box[d] : 0.0);
+                                const double dd = __dadd_rn(__dadd_rn((double)pk.x(d), -(double)xj[d]), shd);
                                 sd = (d == 0) ? __dmul_rn(dd, dd) : __dadd_rn(sd, __dmul_rn(dd, dd));
                             }
                             b = -1;
@@ -229,51 +409,57 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                                         break;
                                     }
                             }
-                        } else if (b >= nbins) {
-                            b = -1;
                         }
                         bin = b;
                     }
-                    // append to the per-bin queues (warp-aggregated)
+                    // stage the pair: a pool slot from the free stack, its index on the bin queue
                     const bool take = bin >= 0;
-                    const unsigned peers = __match_any_sync(full, take ? bin : 64 + lane);
-                    const int rank = __popc(peers & ((1u << lane) - 1u));
-                    const int base = take ? cnt[bin] : 0;
+                    const unsigned tm = __ballot_sync(full, take);
+                    // lanes staging into the same bin: AND of the ballots of the bin's bits
+                    unsigned peers = tm;
+#pragma unroll
+                    for (int kb = 0; kb < 5; ++kb) {
+                        const unsigned bk = __ballot_sync(full, (bin >> kb) & 1);
+                        peers &= ((bin >> kb) & 1) ? bk : ~bk;
+                    }
+                    const int rank = __popc(peers & lt_mask);
+                    const int base = take ? qcnt[bin] : 0;
+                    const int ft = *ftop;
                     __syncwarp();
                     if (take) {
+                        const int slot = fstack[ft - 1 - __popc(tm & lt_mask)];
                         R e;
                         T* f = reinterpret_cast<T*>(e.v);
+                        const T rinv = rsqrt_t(r2);
 #pragma unroll
                         for (int d = 0; d < D; ++d) f[d] = dx[d] * rinv;
                         f[D] = pk.w();
-                        stage[bin * kStageCap + base + rank] = e;
-                        if (rank == 0) cnt[bin] = base + __popc(peers);
+                        pool[slot] = e;
+                        binq[bin * kQCap + base + rank] = (unsigned short)slot;
+                        if (rank == 0) qcnt[bin] = base + __popc(peers);
                         ++npairs;
                     }
+                    if (lane == 0) *ftop = ft - __popc(tm);
                     __syncwarp();
-                    // consume while enough is queued or a queue nears capacity
-                    for (;;) {
-                        const int qv = lane < nbins ? cnt[lane] : 0;
-                        const int tot = __reduce_add_sync(full, qv);
-                        const bool over = __any_sync(full, qv > kStageCap - 32);
-                        if (tot < 64 && !over) break;
-                        round();
-                    }
+                    ++nchunks;
+                    consume(false);
                 }
             }
+            __syncthreads();  // every warp is done with this tile before it is refilled
+            buf ^= 1;
         }
-        // drain
-        for (;;) {
-            const int qv = lane < nbins ? cnt[lane] : 0;
-            if (__reduce_add_sync(full, qv) == 0) break;
-            round();
-        }
+        consume(true);
         // statistics
         {
-            unsigned tot = __reduce_add_sync(full, npairs);
+            const unsigned tot = __reduce_add_sync(full, npairs);
+            const unsigned busy = __reduce_add_sync(full, nbusy);
             if (lane == 0 && active) {
                 atomicAdd(&p.stats[0], (unsigned long long)tot);
                 atomicAdd(&p.stats[1], ncand);
+                atomicAdd(&p.stats[2], (unsigned long long)nrounds);
+                atomicAdd(&p.stats[3], (unsigned long long)busy);
+                atomicAdd(&p.stats[4], (unsigned long long)nchunks);
+                atomicAdd(&p.stats[5], (unsigned long long)nforced);
             }
         }
         // reduce the lanes of each bin and write a^b (normalised)

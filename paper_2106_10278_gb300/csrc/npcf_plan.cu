@@ -7,9 +7,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -119,7 +121,7 @@ struct npcf_plan_s {
     // device facts
     int device = -1, nsm = 0, smem_optin = 0;
     // stats of the last run (host copies)
-    unsigned long long* h_stats = nullptr;  // pinned, 2 entries
+    unsigned long long* h_stats = nullptr;  // pinned, 6 entries
     int* h_small = nullptr;                 // pinned, 4 entries
     int64_t last_nprim = 0;
     cudaStream_t last_stream = nullptr;
@@ -281,6 +283,14 @@ std::vector<int> make_stencil(int D, int c, const double* side, double reach)
         }
         if (m2 < reach * reach) out.push_back(packed);
     }
+    // Visit the neighbour cells in a fixed pseudo-random order: consecutive
+    // cells then lie at unrelated distances, so the pairs a warp stages spread
+    // over all radial bins instead of arriving in bursts of 3-4 bins.
+    const char* order = std::getenv("NPCF_STENCIL_ORDER");
+    if (!(order && std::strcmp(order, "natural") == 0)) {
+        std::mt19937 rng(0x5eed1234u);
+        std::shuffle(out.begin(), out.end(), rng);
+    }
     return out;
 }
 
@@ -311,6 +321,7 @@ GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
         g.ncells = (int)ncells;
         const double npc = (double)std::max<int64_t>(n, 1) / (double)ncells;
         g.stencil = make_stencil(P->D, c, side, reach);
+        if ((int)g.stencil.size() > kMaxJobs) continue;  // the pair kernel lists an item's cells in smem
         const double cost = g.stencil.size() * (npc + 24.0);
         if (cost < any_cost) {
             any_cost = cost;
@@ -384,8 +395,8 @@ npcf_status ensure_device(npcf_plan_s* P)
     CUDA_TRY(cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&P->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     void* pinned = nullptr;
-    CUDA_TRY(cudaMallocHost(&pinned, 64));
-    std::memset(pinned, 0, 64);
+    CUDA_TRY(cudaMallocHost(&pinned, 128));
+    std::memset(pinned, 0, 128);
     P->h_small = static_cast<int*>(pinned);
     P->h_stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(pinned) + 16);
     return NPCF_OK;
@@ -420,6 +431,16 @@ npcf_status setup_tables(npcf_plan_s* P)
     pp.nq = P->nq;
     pp.periodic = P->opts.periodic;
     pp.warps = warps;
+    // consumption policy of the pair kernel's bin queues; NPCF_PAIR_POLICY="busy,total" overrides
+    pp.busy_round = 28;
+    pp.tot_round = 1 << 30;
+    if (const char* pol = std::getenv("NPCF_PAIR_POLICY")) {
+        int b = 0, t = 0;
+        if (std::sscanf(pol, "%d,%d", &b, &t) == 2 && b > 0 && t > 0) {
+            pp.busy_round = b;
+            pp.tot_round = t;
+        }
+    }
     double maxL = 0.0;
     for (int d = 0; d < D; ++d) maxL = std::max(maxL, P->box[d]);
     const double rmax = P->edges[nb], rmin = P->edges[0];
@@ -432,14 +453,28 @@ npcf_status setup_tables(npcf_plan_s* P)
         pp.edgef[b] = (float)P->edges[b];
         pp.edge2[b] = P->edges[b] * P->edges[b];
     }
-    pp.tab_lo = (float)rmin;
-    pp.tab_inv = (float)(kTab / (rmax - rmin));
+    // radial table over r^2 (so the common path needs no square root): bucket k
+    // covers [lo2 + k*w, lo2 + (k+1)*w); the entry is the bin of the whole bucket
+    // (63 = outside the bins) and bit 64 marks buckets that an edge, widened by
+    // the FP32 error window, touches (those pairs are decided exactly in FP64)
+    const double lo2 = std::max(rmin - 2 * tol, 0.0) * std::max(rmin - 2 * tol, 0.0);
+    const double hi2 = (rmax + 2 * tol) * (rmax + 2 * tol);
+    const double wb = (hi2 - lo2) / kTab;
+    pp.tab_lo = (float)lo2;
+    pp.tab_inv = (float)(1.0 / wb);
     std::vector<unsigned char> tab(kTab);
     for (int k = 0; k < kTab; ++k) {
-        const double r = rmin + k * (rmax - rmin) / kTab;
-        int b = 0;
-        while (b < nb && r >= P->edges[b + 1]) ++b;
-        tab[k] = (unsigned char)b;
+        // widen the bucket by the FP32 error of r^2 and of the bucket index itself
+        const double a2 = lo2 + (k - 1) * wb, b2 = lo2 + (k + 2) * wb;
+        const double ra = std::sqrt(std::max(a2, 0.0)) - tol, rb = std::sqrt(b2) + tol;
+        const double rc = std::sqrt(lo2 + (k + 0.5) * wb);
+        int b = -1;
+        for (int e = 0; e < nb; ++e)
+            if (rc >= P->edges[e] && rc < P->edges[e + 1]) b = e;
+        bool near = false;
+        for (int e = 0; e <= nb; ++e)
+            if (P->edges[e] >= ra && P->edges[e] <= rb) near = true;
+        tab[k] = (unsigned char)((b < 0 ? 63 : b) | (near ? 64 : 0));
     }
     lane_map(P);
     CUDA_TRY(upload(P->d_tab, tab));
@@ -527,7 +562,7 @@ npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int 
     if ((st = R(P->w_a, (size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins * P->nq)) != NPCF_OK) return st;
     if ((st = R(P->w_wprim, (size_t)tb * std::max<int64_t>(nprim_max, 1))) != NPCF_OK) return st;
     if ((st = R(P->w_partial, sizeof(double) * rows * 2 * P->ncoeff)) != NPCF_OK) return st;
-    if ((st = R(P->w_small, 64)) != NPCF_OK) return st;
+    if ((st = R(P->w_small, 128)) != NPCF_OK) return st;
     return NPCF_OK;
 }
 
@@ -571,7 +606,7 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
         CUDA_TRY(cudaEventRecord(P->ev[0], s));
     }
     CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(int) * (3 * (size_t)nc + 2), s));
-    CUDA_TRY(cudaMemsetAsync(small, 0, 64, s));
+    CUDA_TRY(cudaMemsetAsync(small, 0, 128, s));
 
     CellParams cp{};
     cp.D = P->D;
@@ -660,7 +695,7 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     }
     P->last_launches = launch_counter();
     CUDA_TRY(cudaMemcpyAsync(P->h_small, small, 16, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 48, cudaMemcpyDeviceToHost, s));
     P->last_stream = s;
     P->last_nprim = nprim_max;
     return NPCF_OK;
@@ -837,6 +872,14 @@ npcf_status npcf_last_profile(npcf_plan_t P, double* stage_ms, int* launches)
     return NPCF_OK;
 }
 
+npcf_status npcf_last_counters(npcf_plan_t P, int64_t* counters, int n)
+{
+    if (!P || (!counters && n > 0)) return fail(NPCF_ERR_ARG, "NULL argument");
+    CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    for (int i = 0; i < n; ++i) counters[i] = i < 6 ? (int64_t)P->h_stats[i] : 0;
+    return NPCF_OK;
+}
+
 const char* npcf_last_error(void) { return g_err.c_str(); }
 
 void npcf_plan_destroy(npcf_plan_t P)
@@ -935,7 +978,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     int4* items = static_cast<int4*>(cv.take(sizeof(int4) * (n + nc + 1)));
     void* a = cv.take((size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins * P->nq);
     void* wprim = cv.take((size_t)tb * std::max<int64_t>(nprim_max, 1));
-    int* small = static_cast<int*>(cv.take(64));
+    int* small = static_cast<int*>(cv.take(128));
     const size_t row_bytes = sizeof(double) * 2 * P->ncoeff;
     size_t left = cv.used <= kNoallocBytes ? kNoallocBytes - ((cv.used + 255) & ~size_t(255)) : 0;
     int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
@@ -968,7 +1011,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     launch_counter() = 0;
     P->timed = 0;
     CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(int) * (3 * (size_t)nc + 2), s));
-    CUDA_TRY(cudaMemsetAsync(small, 0, 64, s));
+    CUDA_TRY(cudaMemsetAsync(small, 0, 128, s));
 
     CellParams cp{};
     cp.D = P->D;
@@ -1048,7 +1091,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     CUDA_TRY(launch_reduce(partial, rows, (int)(2 * P->ncoeff), 1.0 / P->V, coeffs, s));
     P->last_launches = launch_counter();
     CUDA_TRY(cudaMemcpyAsync(P->h_small, small, 16, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 48, cudaMemcpyDeviceToHost, s));
     P->last_stream = s;
     P->last_nprim = nprim_max;
     return NPCF_OK;

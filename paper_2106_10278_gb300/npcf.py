@@ -14,7 +14,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libnpcf.so")
+LIB_PATH = os.environ.get("NPCF_LIBRARY") or os.path.join(_HERE, "_build", "libnpcf.so")
 
 NPCF_OK = 0
 NPCF_FP64, NPCF_FP32 = 0, 1
@@ -25,7 +25,7 @@ STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPC
 # every entry point declared in include/npcf.h
 EXPORTS = ("npcf_default_opts", "npcf_plan_create", "npcf_num_coeffs", "npcf_coeff_index", "npcf_compute",
            "npcf_compute_host", "npcf_device_status", "npcf_last_stats", "npcf_last_profile", "npcf_last_error",
-           "npcf_plan_destroy", "npcf_compute_noalloc")
+           "npcf_plan_destroy", "npcf_compute_noalloc", "npcf_last_counters")
 
 
 class NpcfError(RuntimeError):
@@ -75,6 +75,8 @@ def load_library(path: str = LIB_PATH):
         lib.npcf_last_stats.restype = i32
         lib.npcf_last_profile.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
         lib.npcf_last_profile.restype = i32
+        lib.npcf_last_counters.argtypes = [P, ctypes.POINTER(i64), i32]
+        lib.npcf_last_counters.restype = i32
         lib.npcf_last_error.argtypes = []
         lib.npcf_last_error.restype = ctypes.c_char_p
         lib.npcf_plan_destroy.argtypes = [P]
@@ -197,6 +199,14 @@ class Plan:
         nl = ctypes.c_int()
         _check(lib.npcf_last_profile(self._h, ms, ctypes.byref(nl)))
         return {"cells_ms": ms[0], "pairs_ms": ms[1], "couple_ms": ms[2], "reduce_ms": ms[3], "launches": nl.value}
+
+    def counters(self) -> dict:
+        """Pair-kernel work counters of the last call (profiling)."""
+        lib = load_library()
+        c = (ctypes.c_int64 * 6)()
+        _check(lib.npcf_last_counters(self._h, c, 6))
+        names = ("pairs", "candidates", "rounds", "busy_lanes", "chunks", "forced_rounds")
+        return dict(zip(names, (int(x) for x in c)))
 
     def close(self):
         if getattr(self, "_h", None):
