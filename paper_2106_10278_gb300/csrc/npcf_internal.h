@@ -94,6 +94,8 @@ struct CoupleParams {
     const int4* kblocks;       // (pair_lo, pair_hi, key_lo, key_hi) per blockIdx.y
     int nkb;
     int max_block_keys;        // largest key_hi - key_lo
+    int max_block_pairs;       // largest pair_hi - pair_lo
+    const int* task_pairs;     // D=3, N=4: the pairs of each block ordered by (b2, b1)
     const int2* lam2;          // D=2, N=4: (l1, l2) per Lambda index
     const signed char* lam_odd;// D=3, N=4: 1 if l1+l2+l3 is odd (coefficient imaginary)
     const void* pref;          // N=3: per-l factor of the zero coupling (T)

@@ -102,6 +102,8 @@ struct npcf_plan_s {
     std::vector<int> pair_key;
     std::vector<int4> kblocks;
     int max_block_keys = 0;
+    int max_block_pairs = 0;
+    std::vector<int> task_pairs;
     // pair kernel configuration
     int Lc = 0;        // compiled lmax of the pair kernel
     int nq = 0;        // components written per bin (plan lmax)
@@ -109,7 +111,7 @@ struct npcf_plan_s {
     int threads = 0, warps = 0, pair_smem = 0;
     PairParams pp{};
     // device tables
-    DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil;
+    DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil, d_task;
     // workspace
     DevBuf w_cid, w_perm, w_rec, w_cells, w_items, w_a, w_wprim, w_partial, w_small, w_hpos, w_hw, w_hout;
     // cached cell grid
@@ -194,6 +196,7 @@ void build_key_blocks(npcf_plan_s* P, int max_keys)
     const int np = (int)P->pairs.size();
     int lo = 0;
     P->max_block_keys = 0;
+    P->max_block_pairs = 0;
     while (lo < np) {
         int hi = lo + 1;
         auto key_end = [&](int h) { return h < np ? P->pair_key[h] : (int)P->ncoeff; };
@@ -201,7 +204,19 @@ void build_key_blocks(npcf_plan_s* P, int max_keys)
         const int k0 = P->pair_key[lo], k1 = key_end(hi);
         P->kblocks.push_back(make_int4(lo, hi, k0, k1));
         P->max_block_keys = std::max(P->max_block_keys, k1 - k0);
+        P->max_block_pairs = std::max(P->max_block_pairs, hi - lo);
         lo = hi;
+    }
+    // work order of the pairs inside each block: by (b2, b1), so that the bin
+    // pairs sharing a warp in the D=3, N=4 coupling have similar b2
+    P->task_pairs.clear();
+    for (const int4& kb : P->kblocks) {
+        std::vector<int> v;
+        for (int i = kb.x; i < kb.y; ++i) v.push_back(i);
+        std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+            return P->pairs[a].y != P->pairs[b].y ? P->pairs[a].y < P->pairs[b].y : P->pairs[a].x < P->pairs[b].x;
+        });
+        P->task_pairs.insert(P->task_pairs.end(), v.begin(), v.end());
     }
 }
 
@@ -524,6 +539,7 @@ npcf_status setup_tables(npcf_plan_s* P)
     CUDA_TRY(upload(P->d_pairs, P->pairs));
     CUDA_TRY(upload(P->d_pair_key, P->pair_key));
     CUDA_TRY(upload(P->d_kblocks, P->kblocks));
+    CUDA_TRY(upload(P->d_task, P->task_pairs));
     return NPCF_OK;
 }
 
@@ -680,6 +696,8 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     kp.kblocks = P->d_kblocks.as<int4>();
     kp.nkb = nkb;
     kp.max_block_keys = P->max_block_keys;
+    kp.max_block_pairs = P->max_block_pairs;
+    kp.task_pairs = P->d_task.as<int>();
     kp.lam2 = P->d_lam2.as<int2>();
     kp.lam_odd = P->d_lamodd.as<signed char>();
     kp.pref = P->d_pref.p;
@@ -885,7 +903,7 @@ const char* npcf_last_error(void) { return g_err.c_str(); }
 void npcf_plan_destroy(npcf_plan_t P)
 {
     if (!P) return;
-    DevBuf* bufs[] = {&P->d_tab,   &P->d_qnorm, &P->d_invvb, &P->d_pairs, &P->d_pair_key, &P->d_kblocks,
+    DevBuf* bufs[] = {&P->d_task,  &P->d_tab,   &P->d_qnorm, &P->d_invvb, &P->d_pairs, &P->d_pair_key, &P->d_kblocks,
                       &P->d_lam2,  &P->d_lamodd, &P->d_pref, &P->d_stencil, &P->w_cid,    &P->w_perm,
                       &P->w_rec,   &P->w_cells, &P->w_items, &P->w_a,     &P->w_wprim,   &P->w_partial,
                       &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout};
@@ -1082,6 +1100,8 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     kp.kblocks = P->d_kblocks.as<int4>();
     kp.nkb = nkb;
     kp.max_block_keys = P->max_block_keys;
+    kp.max_block_pairs = P->max_block_pairs;
+    kp.task_pairs = P->d_task.as<int>();
     kp.lam2 = P->d_lam2.as<int2>();
     kp.lam_odd = P->d_lamodd.as<signed char>();
     kp.pref = P->d_pref.p;
