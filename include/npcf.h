@@ -166,8 +166,10 @@ NPCF_API npcf_status npcf_compute_noalloc(npcf_plan_t plan, const void* position
  * Work counters of the pair kernel in the last call (host, waits for its
  * stream), for profiling: [0] pairs, [1] candidate secondaries examined,
  * [2] consumption rounds, [3] lanes that found work in those rounds,
- * [4] 32-candidate chunks scanned, [5] rounds forced by full queues.
- * Writes min(n, 6) entries (the rest zero).
+ * [4] candidate iterations of a warp (64 candidates each), [5] rounds forced
+ * by full queues, [6] iterations with a pair in an edge-flagged table bucket,
+ * [7] iterations with a pair decided in FP64.  Writes min(n, 8) entries (the
+ * rest zero).
  */
 NPCF_API npcf_status npcf_last_counters(npcf_plan_t plan, int64_t* counters, int n);
 

@@ -77,7 +77,7 @@ struct PairParams {
     const void* inv_vb;          // nbins (T)
     void* a_out;                 // nprim x nbins x nq (T)
     void* w_out;                 // nprim (T)
-    unsigned long long* stats;   // [0] pairs, [1] candidates, [2] rounds, [3] busy lanes, [4] chunks, [5] forced rounds
+    unsigned long long* stats;   // [0] pairs, [1] candidates, [2] rounds, [3] busy lanes, [4] chunks, [5] forced rounds, [6] flagged-bucket iterations, [7] exact-FP64 iterations
 };
 
 // ----------------------------------------------------------- coupling kernel

@@ -5,9 +5,12 @@
 //
 // Design (GB300, sm_103a):
 //  * One CTA takes one work item = up to W primaries of one cell; warp w owns
-//    primary w.  The CTA walks the cell stencil (neighbour cells within r_max
-//    of the primary cell) and stages each neighbour cell through shared
-//    memory; every warp scans the staged candidates against its primary.
+//    primary w.  The CTA lists the item's neighbour cells (the stencil cells
+//    within r_max of the primary cell that are non-empty) in shared memory
+//    once; then every warp walks that list on its own, skips the cells its
+//    primary cannot reach, and streams the candidates from global memory
+//    (L1/L2 resident) with a two-deep register prefetch -- no block barriers
+//    while scanning.
 //  * Lanes own radial bins: lane l accumulates only bin lane_bin[l] (the host
 //    gives big shells more lanes).  A candidate that falls in bin b is
 //    appended to a per-(warp, bin) queue in shared memory; when enough are
@@ -33,7 +36,7 @@ struct PairCfg {
 };
 
 constexpr int kPool = 320;      // staged pairs per warp (shared by all bins)
-constexpr int kQCap = 128;      // entries of one bin's index queue
+constexpr int kQCap = 192;      // entries of one bin's index queue
 
 // Shared-memory carve-up of one CTA (host and device must agree):
 //   2 candidate tiles of `threads` records | radial table + edges + lane map (kTab + 576)
@@ -56,7 +59,9 @@ constexpr int kMaxJobs = 1024;  // neighbour cells of one item (the host keeps s
 
 __host__ __device__ inline int pair_fixed_bytes(int rec_bytes, int threads)
 {
-    return 2 * threads * rec_bytes + kTab + 576 + (3 * kMaxJobs + 4 + 72) * 4;
+    (void)rec_bytes;
+    (void)threads;
+    return kTab + 576 + (3 * kMaxJobs + 4 + 72) * 4;
 }
 
 template <int D, int LMAX, typename T>
@@ -127,6 +132,21 @@ __device__ __forceinline__ void block_scan2(int a, int b, int* ea, int* eb, int*
 }
 
 template <int D, typename T>
+__device__ __forceinline__ Rec<D, T> ldg_rec(const Rec<D, T>* src, int i)
+{
+    // read-only path, 16 bytes at a time
+    constexpr int kChunks = sizeof(Rec<D, T>) / 16;
+    const float4* s = reinterpret_cast<const float4*>(src + i);
+    union {
+        float4 f[kChunks];
+        Rec<D, T> r;
+    } u;
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) u.f[c] = __ldg(s + c);
+    return u.r;
+}
+
+template <int D, typename T>
 __device__ __forceinline__ void prefetch_records(Rec<D, T>* dst, const Rec<D, T>* rec, const int* job_a,
                                                  const int* job_pre, int njobs, int T0, int tn)
 {
@@ -160,8 +180,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int nbins = p.nbins;
-    R* tiles = reinterpret_cast<R*>(smem);  // [2][nthreads]
-    unsigned char* tab = smem + 2 * nthreads * sizeof(R);
+    unsigned char* tab = smem;
     float* s_edge = reinterpret_cast<float*>(tab + kTab);          // nbins + 1
     double* s_edge2 = reinterpret_cast<double*>(tab + kTab + 192);  // nbins + 1
     signed char* s_first = reinterpret_cast<signed char*>(tab + kTab + 192 + 272);
@@ -271,7 +290,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         __syncwarp();
         unsigned npairs = 0;
         unsigned long long ncand = 0;
-        unsigned nrounds = 0, nbusy = 0, nchunks = 0, nforced = 0;
+        unsigned nrounds = 0, nbusy = 0, nchunks = 0, nforced = 0, nflag = 0, nexact = 0;
 
         // one consumption round: every lane pops one staged pair of its own bin
         auto round = [&]() {
@@ -307,34 +326,12 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
             }
         };
 
-        int buf = 0;
-        if (V > 0) prefetch_records<D, T>(tiles, rec, job_a, job_pre, njobs, 0, min(nthreads, V));
-        for (int T0 = 0; T0 < V; T0 += nthreads) {
-            const int tn = min(nthreads, V - T0);
-            if (T0 + nthreads < V) {
-                prefetch_records<D, T>(tiles + (buf ^ 1) * nthreads, rec, job_a, job_pre, njobs, T0 + nthreads,
-                                       min(nthreads, V - T0 - nthreads));
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-            const R* tile = tiles + buf * nthreads;
-            // the cells (segments) this tile covers
-            int j;
-            {
-                int lo = 0, hi = njobs;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (job_pre[mid] <= T0) lo = mid;
-                    else hi = mid;
-                }
-                j = lo;
-            }
-            for (; j < njobs && job_pre[j] < T0 + tn; ++j) {
-                if (!active) continue;
-                const int seg_lo = max(job_pre[j], T0) - T0;
-                const int seg_hi = min(job_pre[j + 1], T0 + tn) - T0;
+        // every warp walks the item's cells on its own, streaming candidates from
+        // global memory (L1/L2) with a two-deep register prefetch: no block barriers
+        if (active) {
+            for (int j = 0; j < njobs; ++j) {
+                const int seg_a = job_a[j];
+                const int seg_n = job_pre[j + 1] - job_pre[j];
                 const int packed = job_pk[j];
                 // geometry of this cell for this warp's primary, in T (FP32 on the FP32 path;
                 // the exact FP64 image shift is rebuilt only for ambiguous pairs)
@@ -361,11 +358,16 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                     dmax2 = fma(b, b, dmax2);
                 }
                 if (dmin2 >= T(p.rmax2f) || dmax2 < T(p.rmin2f)) continue;
-                ncand += seg_hi - seg_lo;
-                for (int c0 = seg_lo; c0 < seg_hi; c0 += 32) {
+                ncand += seg_n;
+                const R* src = rec + seg_a;
+                R nxt0 = ldg_rec(src, lane < seg_n ? lane : 0);
+                R nxt1 = ldg_rec(src, 32 + lane < seg_n ? 32 + lane : 0);
+                for (int c0 = 0; c0 < seg_n; c0 += 32) {
                     const int k = c0 + lane;
-                    const bool valid = k < seg_hi;
-                    R pk = tile[valid ? k : seg_lo];
+                    const bool valid = k < seg_n;
+                    const R pk = nxt0;
+                    nxt0 = nxt1;
+                    if (c0 + 64 < seg_n) nxt1 = ldg_rec(src, c0 + 64 + lane < seg_n ? c0 + 64 + lane : 0);
                     T dx[D];
                     T r2 = T(0);
 #pragma unroll
@@ -375,6 +377,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                         r2 = fma(dx[d], dx[d], r2);
                     }
                     int bin = -1;
+                    bool anyflag = false, anyexact = false;
                     if (valid && r2 > T(0) && r2 < T(p.rmax2f) && r2 >= T(p.rmin2f)) {
                         // radial table over r^2: bits 0-5 the bin (63: none), bit 6 set when an
                         // edge lies within the FP32 error window of the bucket
@@ -384,6 +387,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                         int b = (code & 63) == 63 ? -1 : (code & 63);
                         bool exact = !kFP32;
                         if (kFP32 && (code & 64)) {
+                            anyflag = true;
                             // an edge is close: decide in FP32 unless within its error window
                             const float r = (float)r2 * rsqrtf((float)r2);
                             int bb = 0;
@@ -392,6 +396,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                             exact = (bb >= 1 && r - s_edge[bb - 1] < tol) || (bb <= nbins && s_edge[bb] - r < tol);
                         }
                         if (exact) {
+                            anyexact = true;
                             // exact decision from the original coordinates, as the definition makes it
                             double sd = 0.0;
 #pragma unroll
@@ -412,9 +417,13 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                         }
                         bin = b;
                     }
+                    ++nchunks;
+                    nflag += __any_sync(full, anyflag) ? 1u : 0u;
+                    nexact += __any_sync(full, anyexact) ? 1u : 0u;
                     // stage the pair: a pool slot from the free stack, its index on the bin queue
                     const bool take = bin >= 0;
                     const unsigned tm = __ballot_sync(full, take);
+                    if (tm == 0u) continue;
                     // lanes staging into the same bin: AND of the ballots of the bin's bits
                     unsigned peers = tm;
 #pragma unroll
@@ -441,12 +450,9 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                     }
                     if (lane == 0) *ftop = ft - __popc(tm);
                     __syncwarp();
-                    ++nchunks;
                     consume(false);
                 }
             }
-            __syncthreads();  // every warp is done with this tile before it is refilled
-            buf ^= 1;
         }
         consume(true);
         // statistics
@@ -460,6 +466,8 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                 atomicAdd(&p.stats[3], (unsigned long long)busy);
                 atomicAdd(&p.stats[4], (unsigned long long)nchunks);
                 atomicAdd(&p.stats[5], (unsigned long long)nforced);
+                atomicAdd(&p.stats[6], (unsigned long long)nflag);
+                atomicAdd(&p.stats[7], (unsigned long long)nexact);
             }
         }
         // reduce the lanes of each bin and write a^b (normalised)

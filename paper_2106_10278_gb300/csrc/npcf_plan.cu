@@ -123,7 +123,7 @@ struct npcf_plan_s {
     // device facts
     int device = -1, nsm = 0, smem_optin = 0;
     // stats of the last run (host copies)
-    unsigned long long* h_stats = nullptr;  // pinned, 6 entries
+    unsigned long long* h_stats = nullptr;  // pinned, 8 entries
     int* h_small = nullptr;                 // pinned, 4 entries
     int64_t last_nprim = 0;
     cudaStream_t last_stream = nullptr;
@@ -713,7 +713,7 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     }
     P->last_launches = launch_counter();
     CUDA_TRY(cudaMemcpyAsync(P->h_small, small, 16, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 48, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 64, cudaMemcpyDeviceToHost, s));
     P->last_stream = s;
     P->last_nprim = nprim_max;
     return NPCF_OK;
@@ -894,7 +894,7 @@ npcf_status npcf_last_counters(npcf_plan_t P, int64_t* counters, int n)
 {
     if (!P || (!counters && n > 0)) return fail(NPCF_ERR_ARG, "NULL argument");
     CUDA_TRY(cudaStreamSynchronize(P->last_stream));
-    for (int i = 0; i < n; ++i) counters[i] = i < 6 ? (int64_t)P->h_stats[i] : 0;
+    for (int i = 0; i < n; ++i) counters[i] = i < 8 ? (int64_t)P->h_stats[i] : 0;
     return NPCF_OK;
 }
 
@@ -1111,7 +1111,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     CUDA_TRY(launch_reduce(partial, rows, (int)(2 * P->ncoeff), 1.0 / P->V, coeffs, s));
     P->last_launches = launch_counter();
     CUDA_TRY(cudaMemcpyAsync(P->h_small, small, 16, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 48, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 64, cudaMemcpyDeviceToHost, s));
     P->last_stream = s;
     P->last_nprim = nprim_max;
     return NPCF_OK;

@@ -203,9 +203,9 @@ class Plan:
     def counters(self) -> dict:
         """Pair-kernel work counters of the last call (profiling)."""
         lib = load_library()
-        c = (ctypes.c_int64 * 6)()
-        _check(lib.npcf_last_counters(self._h, c, 6))
-        names = ("pairs", "candidates", "rounds", "busy_lanes", "chunks", "forced_rounds")
+        c = (ctypes.c_int64 * 8)()
+        _check(lib.npcf_last_counters(self._h, c, 8))
+        names = ("pairs", "candidates", "rounds", "busy_lanes", "chunks", "forced_rounds", "flagged", "exact")
         return dict(zip(names, (int(x) for x in c)))
 
     def close(self):
