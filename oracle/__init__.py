@@ -174,10 +174,12 @@ def estimate(D, N, lmax, edges, box, pos, w, *, periodic=True, primaries=None, b
 
 def estimate_n3_closed(D, lmax, edges, box, pos, w, *, periodic=True, primaries=None, bin_lt=False,
                        grad_coeffs=None):
-    """N=3 coefficients through the addition theorem (D in {3, 4}).
+    """N=3 coefficients through the addition theorem (D in {3, 4}) or the plain
+    exponential of the relative angle (D = 2).
 
     With grad_coeffs (complex array over keys, or real) also returns the
-    gradient of L = sum_c Re(grad_c) * Re(zeta_c) in positions and weights.
+    gradient of L = sum_c Re(grad_c) Re(zeta_c) + Im(grad_c) Im(zeta_c) in
+    positions and weights (radial bins held fixed).
     Returns (keys, zeta) or (keys, zeta, grad_pos, grad_w).
     """
     lib = _load()

@@ -688,6 +688,11 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
  * with G_l = C_l/C_l(1).  This route uses no harmonic and no coupling table,
  * so it pins the separable estimator of N=3; its derivative in positions and
  * weights (bins held fixed) is the gradient oracle for the adjoint.
+ * For D=2 the basis is e^{il theta}/sqrt(2 pi) and the product of one
+ * secondary's conjugate with the other's is a plain exponential of the angle
+ * between them: a_l(b1) conj a_l(b2) sums w_k w_k' e^{-il phi}/(2 pi v_b1 v_b2),
+ * phi = theta_k - theta_k' = atan2(u_k x u_k', u_k . u_k') up to sign, so
+ *   zeta_l(b1,b2) = (1/V) sum_j w_j sum w_k w_k' (cos l phi - i sin l phi)/(2 pi v_b1 v_b2).
  */
 
 /* C^{(lam)}_n(x) by its explicit sum (DLMF 18.5.10) and its derivative */
@@ -722,15 +727,16 @@ static double dim_l(int D, int l)
 }
 
 /*
- * zeta (2*nkeys, imaginary parts zero) for N=3, D in {3,4}; if grad_coeffs is
- * non-NULL also the gradient of L = sum_c grad_coeffs[2c] * Re zeta_c with
- * respect to every position (grad_pos, n x D) and weight (grad_w, n).
+ * zeta (2*nkeys) for N=3, D in {2,3,4} (imaginary parts zero for D >= 3); if
+ * grad_coeffs is non-NULL also the gradient of
+ *     L = sum_c grad_coeffs[2c] Re zeta_c + grad_coeffs[2c+1] Im zeta_c
+ * with respect to every position (grad_pos, n x D) and weight (grad_w, n).
  */
 int npcf_oracle_n3_closed(int D, int lmax, int nbins, int bin_lt, const double *edges, const double *box,
                           int periodic, const double *pos, const double *w, int64_t n, int64_t pb, int64_t pe,
                           const double *grad_coeffs, double *out, double *grad_pos, double *grad_w)
 {
-    if (D < 3 || D > 4 || !supported(D, 3, lmax, nbins)) return -1;
+    if (D < 2 || D > 4 || !supported(D, 3, lmax, nbins)) return -1;
     if (pb < 0 || pe > n || pb > pe) return -2;
     int nk = enum_keys(D, 3, lmax, nbins, bin_lt, NULL);
     /* key index of (b1, b2, l) in enum_keys order */
@@ -755,7 +761,7 @@ int npcf_oracle_n3_closed(int D, int lmax, int nbins, int bin_lt, const double *
     double pref[OR_MAXL + 1];
     for (int l = 0; l <= lmax; ++l) pref[l] = sgn_pow(l) * sqrt(dim_l(D, l)) / S / gegenbauer_at_one(l, lam);
 
-    double *zeta = (double *)calloc(nk, sizeof(double));
+    double *zeta = (double *)calloc(2 * (size_t)nk, sizeof(double));
     int64_t *nb_idx = (int64_t *)malloc(sizeof(int64_t) * n);
     int *nb_bin = (int *)malloc(sizeof(int) * n);
     double *nb_u = (double *)malloc(sizeof(double) * n * D);  /* unit vectors */
@@ -789,11 +795,26 @@ int npcf_oracle_n3_closed(int D, int lmax, int nbins, int bin_lt, const double *
                 double wp = w[nb_idx[p]], wq = w[nb_idx[q]];
                 double scale = 1.0 / (vb[b1] * vb[b2] * V);
                 double dLdt = 0.0, L_no_w = 0.0;
+                double phi = 0.0, dLdphi = 0.0;
+                if (D == 2)
+                    phi = atan2(nb_u[p * 2 + 1] * nb_u[q * 2] - nb_u[p * 2] * nb_u[q * 2 + 1], t); /* theta_p - theta_q */
                 for (int l = 0; l <= lmax; ++l) {
+                    if (D == 2) {
+                        double re = cos(l * phi) / (2.0 * M_PI), im = -sin(l * phi) / (2.0 * M_PI);
+                        zeta[2 * (kb + l)] += w[j] * wp * wq * re * scale;
+                        zeta[2 * (kb + l) + 1] += w[j] * wp * wq * im * scale;
+                        if (grad_coeffs) {
+                            double Gr = grad_coeffs[2 * (kb + l)], Gi = grad_coeffs[2 * (kb + l) + 1];
+                            L_no_w += Gr * re + Gi * im;
+                            /* d re/d phi = l im, d im/d phi = -l re */
+                            dLdphi += Gr * l * im - Gi * l * re;
+                        }
+                        continue;
+                    }
                     double dg;
                     double g = pref[l] * gegenbauer(l, lam, t, &dg);
                     dg *= pref[l];
-                    zeta[kb + l] += w[j] * wp * wq * g * scale;
+                    zeta[2 * (kb + l)] += w[j] * wp * wq * g * scale;
                     if (grad_coeffs) {
                         double G = grad_coeffs[2 * (kb + l)];
                         dLdt += G * dg;
@@ -806,7 +827,20 @@ int npcf_oracle_n3_closed(int D, int lmax, int nbins, int bin_lt, const double *
                     grad_w[nb_idx[p]] += w[j] * wq * L_no_w * scale;
                     grad_w[nb_idx[q]] += w[j] * wp * L_no_w * scale;
                 }
-                if (grad_pos) {
+                if (grad_pos && D == 2) {
+                    /* d theta/d d = (-u_y, u_x)/r for d = r (u_x, u_y) */
+                    double f = w[j] * wp * wq * scale * dLdphi;
+                    double gp[2], gq[2];
+                    gp[0] = -f * nb_u[p * 2 + 1] / nb_r[p];
+                    gp[1] = f * nb_u[p * 2] / nb_r[p];
+                    gq[0] = f * nb_u[q * 2 + 1] / nb_r[q];
+                    gq[1] = -f * nb_u[q * 2] / nb_r[q];
+                    for (int a = 0; a < 2; ++a) {
+                        grad_pos[nb_idx[p] * 2 + a] += gp[a];
+                        grad_pos[nb_idx[q] * 2 + a] += gq[a];
+                        grad_pos[j * 2 + a] -= gp[a] + gq[a];
+                    }
+                } else if (grad_pos) {
                     double f = w[j] * wp * wq * scale * dLdt;
                     for (int a = 0; a < D; ++a) {
                         /* dt/dd_p = (u_q - t u_p)/|d_p|, d_p = y_p - y_j */
@@ -819,10 +853,7 @@ int npcf_oracle_n3_closed(int D, int lmax, int nbins, int bin_lt, const double *
                 }
             }
     }
-    for (int i = 0; i < nk; ++i) {
-        out[2 * i] = zeta[i];
-        out[2 * i + 1] = 0.0;
-    }
+    for (int i = 0; i < 2 * nk; ++i) out[i] = zeta[i];
     free(zeta); free(kidx); free(nb_idx); free(nb_bin); free(nb_u); free(nb_r);
     return nk;
 }

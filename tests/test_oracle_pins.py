@@ -313,11 +313,12 @@ def test_d2_3pcf_exponential_closed_form():
     np.testing.assert_allclose(z, ref, atol=1e-12 * np.max(np.abs(ref)))
 
 
-@pytest.mark.parametrize("D", [3, 4])
+@pytest.mark.parametrize("D", [2, 3, 4])
 def test_n3_separable_equals_addition_theorem(D):
     """Two routes to the same N=3 coefficients: harmonics + coupling (eq. NPCF-estimator-discrete)
-    and the addition theorem (Gegenbauer of r1.r2), which uses neither."""
-    lmax = 4 if D == 3 else 3
+    and the addition theorem (Gegenbauer of r1.r2; for D=2 the exponential of the relative
+    angle), which uses neither."""
+    lmax = {2: 6, 3: 4, 4: 3}[D]
     pos, w = _tiny(D, 70 if D == 3 else 60, 1.0, 31 + D)
     edges = np.linspace(0.1, 0.45, 4)
     k1, z1 = oracle.estimate(D, 3, lmax, edges, np.ones(D), pos, w)
@@ -416,23 +417,26 @@ def test_parity_reflection_and_reality(D, N):
         assert np.max(np.abs(z.imag)) > 1e-6 * scale  # odd parts exist for N > D
 
 
-def test_gradient_matches_finite_differences_and_identities():
+@pytest.mark.parametrize("D", [2, 3, 4])
+def test_gradient_matches_finite_differences_and_identities(D):
     """The N=3 gradient oracle: central differences away from bin edges, translation invariance
     (sum_i dL/dy_i = 0) and degree-3 homogeneity in the weights (sum_i w_i dL/dw_i = 3 L)."""
-    D, lmax = 4, 2
+    lmax = {2: 4, 3: 3, 4: 2}[D]
     g = np.random.default_rng(5)
     pos, w = _tiny(D, 40, 1.0, 81)
     edges = np.linspace(0.1, 0.5, 4)
     keys, z = oracle.estimate_n3_closed(D, lmax, edges, np.ones(D), pos, w)
-    gc = g.normal(size=len(keys))
+    gc = g.normal(size=len(keys)) + 1j * g.normal(size=len(keys))
     _, z0, gp, gw = oracle.estimate_n3_closed(D, lmax, edges, np.ones(D), pos, w, grad_coeffs=gc)
-    L0 = float(np.sum(gc * z0.real))
+    L0 = float(np.sum(gc.real * z0.real + gc.imag * z0.imag))
+    if D == 2:
+        assert np.max(np.abs(z0.imag)) > 1e-6 * np.max(np.abs(z0))  # the imaginary parts are exercised
     np.testing.assert_allclose(gp.sum(axis=0), 0.0, atol=1e-10 * np.max(np.abs(gp)))
     assert abs(np.sum(w * gw) - 3 * L0) < 1e-10 * max(1.0, abs(L0))
 
     def loss(p, ww):
         _, zz = oracle.estimate_n3_closed(D, lmax, edges, np.ones(D), p, ww)
-        return float(np.sum(gc * zz.real))
+        return float(np.sum(gc.real * zz.real + gc.imag * zz.imag))
 
     h = 1e-6
     # pick coordinates whose pairs are all far from the edges
