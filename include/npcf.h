@@ -119,6 +119,28 @@ NPCF_API npcf_status npcf_compute(npcf_plan_t plan, const void* positions, const
 NPCF_API npcf_status npcf_compute_host(npcf_plan_t plan, const void* positions, const void* weights, int64_t n,
                               double* coeffs, int64_t primary_begin, int64_t primary_end, npcf_stream_t stream);
 
+/*
+ * Gradient of a scalar loss through the N=3 estimator (the adjoint of
+ * eq. NPCF-estimator-discrete for N=3; the inner sums of eq. alm-bin-def are
+ * differentiated with the radial bin of every pair held fixed, the bin
+ * indicators being piecewise constant in the separation).
+ *   positions, weights, n, [primary_begin, primary_end), stream : as for
+ *               npcf_compute (the same call computes the same coefficients).
+ *   grad_coeffs : device, 2*ncoeff doubles: dL/dRe and dL/dIm of each coefficient.
+ *   grad_positions : device, n x D row-major in the plan's precision, or NULL;
+ *               overwritten with dL/dy_i (minimum-image separations when periodic).
+ *   grad_weights   : device, n in the plan's precision, or NULL; overwritten with dL/dw_i.
+ *               At least one of the two must be given when n > 0.
+ * Per-particle sums are accumulated in FP64 with atomics (not bit-reproducible
+ * from call to call).  Asynchronous on `stream` when opts.sync_check == 0.
+ * Errors: NPCF_ERR_UNSUPPORTED for N=4 plans or lmax without a compiled
+ * adjoint, NPCF_ERR_ARG, NPCF_ERR_NONFINITE (sync_check only),
+ * NPCF_ERR_WORKSPACE, NPCF_ERR_CUDA.
+ */
+NPCF_API npcf_status npcf_backward(npcf_plan_t plan, const void* positions, const void* weights, int64_t n,
+                                   const double* grad_coeffs, int64_t primary_begin, int64_t primary_end,
+                                   void* grad_positions, void* grad_weights, npcf_stream_t stream);
+
 /* Device-side input errors flagged by the last asynchronous npcf_compute (waits for its stream). */
 NPCF_API npcf_status npcf_device_status(npcf_plan_t plan);
 

@@ -133,4 +133,17 @@ cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, c
 int couple_smem(const CoupleParams& p, int fp64);
 cudaError_t launch_reduce(const double* partial, int rows, int ncols, double scale, double* out, cudaStream_t s);
 
+// adjoint of the N=3 estimator (npcf_backward.cu)
+int adjoint_compiled_lmax(int D, int lmax);
+int adjoint_pair_warps();
+int adjoint_pair_smem(int D, int Lc, int fp64, int nbins);
+cudaError_t launch_couple_adjoint(int D, int fp64, int nbins, int nq, int lmax, int64_t nprim, const void* a,
+                                  const void* wprim, const double* g, const int* key_base, const void* pref,
+                                  const void* qnorm, const void* inv_vb, double inv_V, void* cbuf, double* gwp,
+                                  int nsm, cudaStream_t s);
+cudaError_t launch_pairs_adjoint(const PairParams& p, int fp64, int Lc, const void* cbuf, const double* gwp,
+                                 const int* perm, double* gpos, double* gw, int nsm, cudaStream_t s);
+cudaError_t launch_finalize_grads(int64_t n, int D, int fp64, const double* gpos, const double* gw, void* grad_pos,
+                                  void* grad_w, cudaStream_t s);
+
 }  // namespace npcf

@@ -131,6 +131,87 @@ __device__ __forceinline__ void block_scan2(int a, int b, int* ea, int* eb, int*
     __syncthreads();
 }
 
+
+// The radial bin of one candidate pair, decided exactly as the FP64 definition
+// decides it ([e_b, e_{b+1}) on the FP64 r^2 of the original coordinates):
+// the FP32 r^2 indexes a table over r^2 (bits 0-5 the bin, 63 = none; bit 6:
+// an edge lies within the FP32 error window of the bucket); flagged buckets
+// are re-decided in FP32 unless the pair sits within that window, and those
+// few pairs in FP64.  Returns -1 outside the bins.  Shared by the forward and
+// adjoint pair kernels so that both see the same pair set.
+template <int D, typename T>
+__device__ __forceinline__ int decide_bin(const PairParams& p, const unsigned char* tab, const float* s_edge,
+                                          const double* s_edge2, const int* cc, int packed, const T* xj,
+                                          const Rec<D, T>& pk, T r2, bool* flagged, bool* exact_out)
+{
+    constexpr bool kFP32 = sizeof(T) == 4;
+    if (!(r2 > T(0) && r2 < T(p.rmax2f) && r2 >= T(p.rmin2f))) return -1;
+    int kk = (int)(((float)r2 - p.tab_lo) * p.tab_inv);
+    kk = kk < 0 ? 0 : (kk >= kTab ? kTab - 1 : kk);
+    const int code = tab[kk];
+    int b = (code & 63) == 63 ? -1 : (code & 63);
+    bool exact = !kFP32;
+    if (kFP32 && (code & 64)) {
+        *flagged = true;
+        const float r = (float)r2 * rsqrtf((float)r2);
+        int bb = 0;
+        while (bb <= p.nbins && r >= s_edge[bb]) ++bb;
+        b = (bb >= 1 && bb <= p.nbins) ? bb - 1 : -1;
+        exact = (bb >= 1 && r - s_edge[bb - 1] < p.tol) || (bb <= p.nbins && s_edge[bb] - r < p.tol);
+    }
+    if (exact) {
+        *exact_out = true;
+        double sd = 0.0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
+            const double shd = c < 0 ? -p.box[d] : (c >= p.nc[d] ? p.box[d] : 0.0);
+            const double dd = __dadd_rn(__dadd_rn((double)pk.x(d), -(double)xj[d]), shd);
+            sd = (d == 0) ? __dmul_rn(dd, dd) : __dadd_rn(sd, __dmul_rn(dd, dd));
+        }
+        b = -1;
+        if (sd > 0.0 && sd >= s_edge2[0]) {
+            for (int e = 0; e < p.nbins; ++e)
+                if (sd < s_edge2[e + 1]) {
+                    b = e;
+                    break;
+                }
+        }
+    }
+    return b;
+}
+
+// Cell geometry of one stencil cell for one primary: the shifted primary
+// position (so that pk - xjs is the minimum-image separation) and whether the
+// cell can hold a pair in [e_0, e_nb) of that primary.
+template <int D, typename T>
+__device__ __forceinline__ bool cell_geometry(const PairParams& p, const int* cc, int packed, const T* xj, T* xjs)
+{
+    constexpr bool kFP32 = sizeof(T) == 4;
+    T dmin2 = T(0), dmax2 = T(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
+        T side, box;
+        if constexpr (kFP32) {
+            side = p.sidef[d];
+            box = p.boxf[d];
+        } else {
+            side = p.side[d];
+            box = p.box[d];
+        }
+        const T lo = T(c) * side;
+        const T hi = lo + side;
+        const T sh = c < 0 ? -box : (c >= p.nc[d] ? box : T(0));
+        xjs[d] = xj[d] - sh;
+        const T a = fmax(fmax(lo - xj[d], xj[d] - hi), T(0));
+        dmin2 = fma(a, a, dmin2);
+        const T b = fmax(fabs(xj[d] - lo), fabs(xj[d] - hi));
+        dmax2 = fma(b, b, dmax2);
+    }
+    return !(dmin2 >= T(p.rmax2f) || dmax2 < T(p.rmin2f));
+}
+
 template <int D, typename T>
 __device__ __forceinline__ Rec<D, T> ldg_rec(const Rec<D, T>* src, int i)
 {
@@ -333,31 +414,8 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                 const int seg_a = job_a[j];
                 const int seg_n = job_pre[j + 1] - job_pre[j];
                 const int packed = job_pk[j];
-                // geometry of this cell for this warp's primary, in T (FP32 on the FP32 path;
-                // the exact FP64 image shift is rebuilt only for ambiguous pairs)
                 T xjs[D];
-                T dmin2 = T(0), dmax2 = T(0);
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
-                    T side, box;
-                    if constexpr (kFP32) {
-                        side = p.sidef[d];
-                        box = p.boxf[d];
-                    } else {
-                        side = p.side[d];
-                        box = p.box[d];
-                    }
-                    const T lo = T(c) * side;
-                    const T hi = lo + side;
-                    const T sh = c < 0 ? -box : (c >= p.nc[d] ? box : T(0));
-                    xjs[d] = xj[d] - sh;
-                    const T a = fmax(fmax(lo - xj[d], xj[d] - hi), T(0));
-                    dmin2 = fma(a, a, dmin2);
-                    const T b = fmax(fabs(xj[d] - lo), fabs(xj[d] - hi));
-                    dmax2 = fma(b, b, dmax2);
-                }
-                if (dmin2 >= T(p.rmax2f) || dmax2 < T(p.rmin2f)) continue;
+                if (!cell_geometry<D, T>(p, cc, packed, xj, xjs)) continue;
                 ncand += seg_n;
                 const R* src = rec + seg_a;
                 R nxt0 = ldg_rec(src, lane < seg_n ? lane : 0);
@@ -376,47 +434,9 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                         else dx[d] = (pk.x(d) - xj[d]) + (xj[d] - xjs[d]);
                         r2 = fma(dx[d], dx[d], r2);
                     }
-                    int bin = -1;
                     bool anyflag = false, anyexact = false;
-                    if (valid && r2 > T(0) && r2 < T(p.rmax2f) && r2 >= T(p.rmin2f)) {
-                        // radial table over r^2: bits 0-5 the bin (63: none), bit 6 set when an
-                        // edge lies within the FP32 error window of the bucket
-                        int kk = (int)(((float)r2 - p.tab_lo) * p.tab_inv);
-                        kk = kk < 0 ? 0 : (kk >= kTab ? kTab - 1 : kk);
-                        const int code = tab[kk];
-                        int b = (code & 63) == 63 ? -1 : (code & 63);
-                        bool exact = !kFP32;
-                        if (kFP32 && (code & 64)) {
-                            anyflag = true;
-                            // an edge is close: decide in FP32 unless within its error window
-                            const float r = (float)r2 * rsqrtf((float)r2);
-                            int bb = 0;
-                            while (bb <= nbins && r >= s_edge[bb]) ++bb;
-                            b = (bb >= 1 && bb <= nbins) ? bb - 1 : -1;
-                            exact = (bb >= 1 && r - s_edge[bb - 1] < tol) || (bb <= nbins && s_edge[bb] - r < tol);
-                        }
-                        if (exact) {
-                            anyexact = true;
-                            // exact decision from the original coordinates, as the definition makes it
-                            double sd = 0.0;
-#pragma unroll
-                            for (int d = 0; d < D; ++d) {
-                                const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
-                                const double shd = c < 0 ? -p.box[d] : (c >= p.nc[d] ? p.box[d] : 0.0);
-                                const double dd = __dadd_rn(__dadd_rn((double)pk.x(d), -(double)xj[d]), shd);
-                                sd = (d == 0) ? __dmul_rn(dd, dd) : __dadd_rn(sd, __dmul_rn(dd, dd));
-                            }
-                            b = -1;
-                            if (sd > 0.0 && sd >= s_edge2[0]) {
-                                for (int e = 0; e < nbins; ++e)
-                                    if (sd < s_edge2[e + 1]) {
-                                        b = e;
-                                        break;
-                                    }
-                            }
-                        }
-                        bin = b;
-                    }
+                    const int bin = valid ? decide_bin<D, T>(p, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &anyflag, &anyexact)
+                                          : -1;
                     ++nchunks;
                     nflag += __any_sync(full, anyflag) ? 1u : 0u;
                     nexact += __any_sync(full, anyexact) ? 1u : 0u;

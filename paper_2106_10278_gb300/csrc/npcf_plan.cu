@@ -114,6 +114,8 @@ struct npcf_plan_s {
     DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil, d_task;
     // workspace
     DevBuf w_cid, w_perm, w_rec, w_cells, w_items, w_a, w_wprim, w_partial, w_small, w_hpos, w_hw, w_hout;
+    // adjoint (npcf_backward)
+    DevBuf d_keybase, w_cbuf, w_gpos, w_gw, w_gwp;
     // cached cell grid
     int grid_c = -1;
     int nc[4] = {1, 1, 1, 1};
@@ -582,19 +584,19 @@ npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int 
     return NPCF_OK;
 }
 
-npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, double* coeffs, int64_t pb, int64_t pe,
-                cudaStream_t s)
-{
-    npcf_status st;
-    if ((st = ensure_device(P)) != NPCF_OK) return st;
-    if ((st = prepare_grid(P, n)) != NPCF_OK) return st;
-    const int64_t nprim_max = pe - pb;
-    const int chunk = 128;
-    const int nkb = (int)P->kblocks.size();
-    int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
-    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim_max + chunk - 1) / chunk));
-    if ((st = reserve_workspace(P, n, nprim_max, rows)) != NPCF_OK) return st;
+// What the cell-list and pair stages leave for the stages after them.
+struct PairStage {
+    ItemBuffers ib;
+    PairParams pp;
+    int* small = nullptr;
+    unsigned long long* stats = nullptr;
+};
 
+// Cell list, work items and the pair kernel (the a-array of every primary in
+// [pb, pe)), on workspace already reserved for n particles.
+npcf_status run_pairs(npcf_plan_s* P, const void* pos, const void* w, int64_t n, int64_t pb, int64_t pe,
+                      cudaStream_t s, PairStage* out)
+{
     const int nc = P->ncells;
     int* cells = P->w_cells.as<int>();
     int* cell_count = cells;                // nc + 1
@@ -677,6 +679,31 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     else e = launch_pairs_d4(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "pair kernel launch: %s", cudaGetErrorString(e));
     if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[2], s));
+    out->ib = ib;
+    out->pp = pp;
+    out->small = small;
+    out->stats = stats;
+    return NPCF_OK;
+}
+
+npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, double* coeffs, int64_t pb, int64_t pe,
+                cudaStream_t s)
+{
+    npcf_status st;
+    if ((st = ensure_device(P)) != NPCF_OK) return st;
+    if ((st = prepare_grid(P, n)) != NPCF_OK) return st;
+    const int64_t nprim_max = pe - pb;
+    const int chunk = 128;
+    const int nkb = (int)P->kblocks.size();
+    int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
+    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim_max + chunk - 1) / chunk));
+    if ((st = reserve_workspace(P, n, nprim_max, rows)) != NPCF_OK) return st;
+    PairStage ps;
+    if ((st = run_pairs(P, pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
+    const ItemBuffers& ib = ps.ib;
+    int* small = ps.small;
+    unsigned long long* stats = ps.stats;
+    cudaError_t e;
 
     CoupleParams kp{};
     kp.D = P->D;
@@ -716,6 +743,61 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 64, cudaMemcpyDeviceToHost, s));
     P->last_stream = s;
     P->last_nprim = nprim_max;
+    return NPCF_OK;
+}
+
+// The adjoint of the N=3 estimator: recompute the a-array with the forward
+// cell-list and pair stages, then the coupling adjoint (per-primary
+// c-coefficients and the primary-weight terms), then the pair adjoint (every
+// pair's contribution to the positions and weights), then the conversion.
+npcf_status run_backward(npcf_plan_s* P, const void* pos, const void* w, int64_t n, const double* g, int64_t pb,
+                         int64_t pe, void* grad_pos, void* grad_w, cudaStream_t s)
+{
+    npcf_status st;
+    if ((st = ensure_device(P)) != NPCF_OK) return st;
+    if ((st = prepare_grid(P, n)) != NPCF_OK) return st;
+    const int La = adjoint_compiled_lmax(P->D, P->lmax);
+    if (La < 0) return fail(NPCF_ERR_UNSUPPORTED, "the adjoint is not compiled for D=%d lmax=%d", P->D, P->lmax);
+    const int asmem = adjoint_pair_smem(P->D, La, P->fp64, P->nbins);
+    if (asmem > P->smem_optin)
+        return fail(NPCF_ERR_UNSUPPORTED, "the adjoint pair kernel needs %d bytes of shared memory", asmem);
+    const int64_t nprim = pe - pb;
+    if ((st = reserve_workspace(P, n, nprim, 1)) != NPCF_OK) return st;
+    const size_t tb = P->fp64 ? 8 : 4;
+    const size_t n1 = (size_t)std::max<int64_t>(n, 1), p1 = (size_t)std::max<int64_t>(nprim, 1);
+    if (P->w_cbuf.reserve(tb * p1 * P->nbins * P->nq) != cudaSuccess ||
+        P->w_gpos.reserve(sizeof(double) * P->D * n1) != cudaSuccess ||
+        P->w_gw.reserve(sizeof(double) * n1) != cudaSuccess || P->w_gwp.reserve(sizeof(double) * p1) != cudaSuccess)
+        return fail(NPCF_ERR_WORKSPACE, "device allocation of the adjoint workspace failed");
+    if (P->d_keybase.bytes == 0) {
+        std::vector<int> kb((size_t)P->nbins * P->nbins, -1);
+        for (size_t pr = 0; pr < P->pairs.size(); ++pr)
+            kb[(size_t)P->pairs[pr].x * P->nbins + P->pairs[pr].y] = P->pair_key[pr];
+        CUDA_TRY(upload(P->d_keybase, kb));
+    }
+    PairStage ps;
+    if ((st = run_pairs(P, pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
+    P->timed = 0;
+    double* gpos = P->w_gpos.as<double>();
+    double* gw = P->w_gw.as<double>();
+    CUDA_TRY(cudaMemsetAsync(gpos, 0, sizeof(double) * P->D * n1, s));
+    CUDA_TRY(cudaMemsetAsync(gw, 0, sizeof(double) * n1, s));
+    cudaError_t e = launch_couple_adjoint(P->D, P->fp64, P->nbins, P->nq, P->lmax, nprim, P->w_a.p, P->w_wprim.p, g,
+                                          P->d_keybase.as<int>(), P->d_pref.p, P->d_qnorm.p, P->d_invvb.p,
+                                          1.0 / P->V, P->w_cbuf.p, P->w_gwp.as<double>(), P->nsm, s);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling adjoint launch: %s", cudaGetErrorString(e));
+    // work items of adjoint_pair_warps() primaries (the a-array index of a primary does not depend on it)
+    CUDA_TRY(launch_make_items(ps.ib, ps.pp.cell_start, P->w_perm.as<int>(), P->ncells, pb, pe,
+                               adjoint_pair_warps(), s));
+    e = launch_pairs_adjoint(ps.pp, P->fp64, La, P->w_cbuf.p, P->w_gwp.as<double>(), P->w_perm.as<int>(), gpos, gw,
+                             P->nsm, s);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "pair adjoint launch: %s", cudaGetErrorString(e));
+    CUDA_TRY(launch_finalize_grads(n, P->D, P->fp64, gpos, gw, grad_pos, grad_w, s));
+    P->last_launches = launch_counter();
+    CUDA_TRY(cudaMemcpyAsync(P->h_small, ps.small, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, ps.stats, 64, cudaMemcpyDeviceToHost, s));
+    P->last_stream = s;
+    P->last_nprim = nprim;
     return NPCF_OK;
 }
 
@@ -898,6 +980,28 @@ npcf_status npcf_last_counters(npcf_plan_t P, int64_t* counters, int n)
     return NPCF_OK;
 }
 
+npcf_status npcf_backward(npcf_plan_t P, const void* pos, const void* w, int64_t n, const double* grad_coeffs,
+                          int64_t pb, int64_t pe, void* grad_pos, void* grad_w, npcf_stream_t stream)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (P->N != 3) return fail(NPCF_ERR_UNSUPPORTED, "the adjoint is implemented for N=3 plans");
+    if (n < 0 || n > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)n);
+    if (!grad_coeffs) return fail(NPCF_ERR_ARG, "grad_coeffs is NULL");
+    if (n > 0 && !grad_pos && !grad_w) return fail(NPCF_ERR_ARG, "grad_positions and grad_weights are both NULL");
+    if (n > 0 && (!pos || !w)) return fail(NPCF_ERR_ARG, "positions/weights are NULL");
+    if (pb == 0 && pe == 0) pe = n;
+    if (pb < 0 || pe > n || pb > pe) return fail(NPCF_ERR_ARG, "primary range [%lld, %lld) outside [0, %lld)",
+                                                 (long long)pb, (long long)pe, (long long)n);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    npcf_status st = run_backward(P, pos, w, n, grad_coeffs, pb, pe, grad_pos, grad_w, s);
+    if (st != NPCF_OK) return st;
+    if (P->opts.sync_check) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return check_flags(P);
+    }
+    return NPCF_OK;
+}
+
 const char* npcf_last_error(void) { return g_err.c_str(); }
 
 void npcf_plan_destroy(npcf_plan_t P)
@@ -906,7 +1010,8 @@ void npcf_plan_destroy(npcf_plan_t P)
     DevBuf* bufs[] = {&P->d_task,  &P->d_tab,   &P->d_qnorm, &P->d_invvb, &P->d_pairs, &P->d_pair_key, &P->d_kblocks,
                       &P->d_lam2,  &P->d_lamodd, &P->d_pref, &P->d_stencil, &P->w_cid,    &P->w_perm,
                       &P->w_rec,   &P->w_cells, &P->w_items, &P->w_a,     &P->w_wprim,   &P->w_partial,
-                      &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout};
+                      &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout,  &P->d_keybase, &P->w_cbuf,
+                      &P->w_gpos,  &P->w_gw,    &P->w_gwp};
     for (DevBuf* b : bufs) b->release();
     if (P->h_small) cudaFreeHost(P->h_small);
     for (auto& e : P->ev)

@@ -25,7 +25,7 @@ STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPC
 # every entry point declared in include/npcf.h
 EXPORTS = ("npcf_default_opts", "npcf_plan_create", "npcf_num_coeffs", "npcf_coeff_index", "npcf_compute",
            "npcf_compute_host", "npcf_device_status", "npcf_last_stats", "npcf_last_profile", "npcf_last_error",
-           "npcf_plan_destroy", "npcf_compute_noalloc", "npcf_last_counters")
+           "npcf_plan_destroy", "npcf_compute_noalloc", "npcf_last_counters", "npcf_backward")
 
 
 class NpcfError(RuntimeError):
@@ -77,6 +77,8 @@ def load_library(path: str = LIB_PATH):
         lib.npcf_last_profile.restype = i32
         lib.npcf_last_counters.argtypes = [P, ctypes.POINTER(i64), i32]
         lib.npcf_last_counters.restype = i32
+        lib.npcf_backward.argtypes = [P, P, P, i64, P, i64, i64, P, P, P]
+        lib.npcf_backward.restype = i32
         lib.npcf_last_error.argtypes = []
         lib.npcf_last_error.restype = ctypes.c_char_p
         lib.npcf_plan_destroy.argtypes = [P]
@@ -171,6 +173,37 @@ class Plan:
                                     ctypes.c_void_p(out.data_ptr()), pb, pe, ctypes.c_void_p(s.cuda_stream)))
         return torch.view_as_complex(out.view(-1, 2))
 
+    def backward(self, pos, w, grad_coeffs, primaries=None, stream=None, want_pos=True, want_w=True):
+        """dL/dpos (n, D) and dL/dw (n) for device tensors, given dL/dcoeff.
+
+        grad_coeffs: float64 device tensor of 2*ncoeff entries (dL/dRe, dL/dIm
+        interleaved) or a complex128 tensor of ncoeff entries.  N=3 plans only."""
+        import torch
+        lib = load_library()
+        dt = self._dtype()
+        if not (pos.is_cuda and w.is_cuda and grad_coeffs.is_cuda):
+            raise ValueError("pos, w and grad_coeffs must be CUDA tensors")
+        if pos.dtype != dt or w.dtype != dt:
+            raise TypeError(f"pos and w must be {dt} for a {self.precision} plan")
+        if pos.dim() != 2 or pos.shape[1] != self.D or w.shape != (pos.shape[0],):
+            raise ValueError("pos must be (n, D) and w (n,)")
+        g = torch.view_as_real(grad_coeffs).reshape(-1) if grad_coeffs.is_complex() else grad_coeffs.reshape(-1)
+        g = g.to(torch.float64).contiguous()
+        if g.numel() != 2 * self.ncoeff:
+            raise ValueError(f"grad_coeffs must hold {2 * self.ncoeff} doubles")
+        pos = pos.contiguous()
+        w = w.contiguous()
+        n = pos.shape[0]
+        gp = torch.empty_like(pos) if want_pos else None
+        gw = torch.empty_like(w) if want_w else None
+        pb, pe = (0, n) if primaries is None else (int(primaries[0]), int(primaries[1]))
+        s = stream if stream is not None else torch.cuda.current_stream(pos.device)
+        ptr = lambda t: ctypes.c_void_p(None if t is None else t.data_ptr())
+        with torch.cuda.device(pos.device):
+            _check(lib.npcf_backward(self._h, ptr(pos), ptr(w), n, ptr(g), pb, pe, ptr(gp), ptr(gw),
+                                     ctypes.c_void_p(s.cuda_stream)))
+        return gp, gw
+
     def compute_host(self, pos, w, primaries=None, stream=None) -> np.ndarray:
         """Coefficients for host arrays (copied in and out by the library)."""
         lib = load_library()
@@ -207,6 +240,28 @@ class Plan:
         _check(lib.npcf_last_counters(self._h, c, 8))
         names = ("pairs", "candidates", "rounds", "busy_lanes", "chunks", "forced_rounds", "flagged", "exact")
         return dict(zip(names, (int(x) for x in c)))
+
+    def function(self, primaries=None):
+        """A torch.autograd.Function-backed callable (pos, w) -> coefficients as an
+        (ncoeff, 2) float64 tensor (re, im), differentiable in pos and w (N=3)."""
+        plan = self
+
+        import torch
+
+        class _Estimate(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, pos, w):
+                ctx.save_for_backward(pos, w)
+                return torch.view_as_real(plan.compute(pos.detach(), w.detach(), primaries=primaries)).clone()
+
+            @staticmethod
+            def backward(ctx, grad_out):
+                pos, w = ctx.saved_tensors
+                gp, gw = plan.backward(pos, w, grad_out.reshape(-1), primaries=primaries,
+                                       want_pos=ctx.needs_input_grad[0], want_w=ctx.needs_input_grad[1])
+                return gp, gw
+
+        return _Estimate.apply
 
     def close(self):
         if getattr(self, "_h", None):
