@@ -120,6 +120,29 @@ NPCF_API npcf_status npcf_compute_host(npcf_plan_t plan, const void* positions, 
                               double* coeffs, int64_t primary_begin, int64_t primary_end, npcf_stream_t stream);
 
 /*
+ * The coefficients of ncat independent catalogues in one pass: one cell list
+ * over all of them, one persistent pair-kernel launch whose CTAs take work
+ * items of every catalogue from one queue, one coupling launch and one
+ * reduction (eq. NPCF-estimator-discrete applied to each catalogue on its own;
+ * the paper has no batched form, this exists to keep many small catalogues
+ * from leaving the GPU idle between calls).
+ *   positions, weights : device, the catalogues concatenated (n = offsets[ncat]
+ *               rows), plan precision; catalogue i is rows [offsets[i], offsets[i+1]).
+ *   offsets    : host, ncat + 1 nondecreasing values, offsets[0] = 0.
+ *   boxes      : host, ncat x D side lengths; catalogue i lies in [0, box_i) with
+ *               V_i = prod box_i; the plan's own box is not used.  Periodic plans
+ *               need r_max < box/2.25 on every side of every box.
+ *   coeffs     : device, ncat x 2*ncoeff doubles (catalogue-major), overwritten.
+ * Every particle of a catalogue is a primary of that catalogue.  The layout is
+ * cached: a repeated call with the same offsets and boxes copies no tables.
+ * Errors: NPCF_ERR_ARG, NPCF_ERR_UNSUPPORTED (no common grid), NPCF_ERR_NONFINITE
+ * (sync_check only), NPCF_ERR_WORKSPACE, NPCF_ERR_CUDA.
+ */
+NPCF_API npcf_status npcf_compute_batched(npcf_plan_t plan, const void* positions, const void* weights,
+                                          const int64_t* offsets, const double* boxes, int ncat, double* coeffs,
+                                          npcf_stream_t stream);
+
+/*
  * Gradient of a scalar loss through the N=3 estimator (the adjoint of
  * eq. NPCF-estimator-discrete for N=3; the inner sums of eq. alm-bin-def are
  * differentiated with the radial bin of every pair held fixed, the bin

@@ -63,6 +63,22 @@ def gaussian_blobs(n: int, D: int, L, n_centres: int, sigma: float, seed: int) -
     return _fp32_in_box(x, L)
 
 
+def _rfftn(x):
+    try:
+        import scipy.fft as sf
+        return sf.rfftn(x, workers=-1)
+    except ImportError:
+        return np.fft.rfftn(x)
+
+
+def _irfftn(x, shape):
+    try:
+        import scipy.fft as sf
+        return sf.irfftn(x, s=shape, workers=-1)
+    except ImportError:
+        return np.fft.irfftn(x, s=shape, axes=(0, 1, 2))
+
+
 def lognormal_poisson(n_mean: float, L: float, seed: int, grid: int = 256, slope: float = -1.5) -> np.ndarray:
     """Poisson draws from a lognormal density on a grid^3 mesh of a periodic cube.
 
@@ -72,7 +88,7 @@ def lognormal_poisson(n_mean: float, L: float, seed: int, grid: int = 256, slope
     """
     g = _rng(seed)
     white = g.standard_normal((grid, grid, grid))
-    fk = np.fft.rfftn(white)
+    fk = _rfftn(white)
     kx = np.fft.fftfreq(grid)[:, None, None]
     ky = np.fft.fftfreq(grid)[None, :, None]
     kz = np.fft.rfftfreq(grid)[None, None, :]
@@ -80,7 +96,7 @@ def lognormal_poisson(n_mean: float, L: float, seed: int, grid: int = 256, slope
     k2[0, 0, 0] = 1.0
     amp = k2 ** (slope / 4.0)  # sqrt(P(k)) with P ~ k^slope
     amp[0, 0, 0] = 0.0
-    G = np.fft.irfftn(fk * amp, s=(grid, grid, grid))
+    G = _irfftn(fk * amp, (grid, grid, grid))
     G /= G.std()
     rho = np.exp(G - 0.5)
     lam = n_mean * rho / rho.sum()
@@ -118,6 +134,48 @@ class Workload:
     @property
     def n(self) -> int:
         return int(self.pos.shape[0])
+
+
+@dataclass
+class Batch:
+    """Several catalogues concatenated: catalogue i is rows offsets[i]:offsets[i+1] in its box boxes[i]."""
+    name: str
+    D: int
+    edges: np.ndarray
+    boxes: np.ndarray   # (ncat, D)
+    offsets: np.ndarray  # (ncat + 1,) int64
+    pos: np.ndarray
+    w: np.ndarray
+
+    @property
+    def ncat(self) -> int:
+        return len(self.offsets) - 1
+
+    def catalogue(self, i: int):
+        a, b = int(self.offsets[i]), int(self.offsets[i + 1])
+        return self.pos[a:b], self.w[a:b], self.boxes[i]
+
+
+def batch64(ncat: int = 64, scale: float = 1.0, grid: int = 128) -> Batch:
+    """The batched D=3 workload: ncat catalogues with n_i log-uniform in [5e4, 5e5] (times
+    `scale`) and periodic cubes of side L_i uniform in [500, 1000] (both drawn with seed 3);
+    catalogue i (seed 1000 + i) is half uniform, half Poisson draws from a lognormal field
+    (P(k) ~ k^-1.5, sigma_ln = 1) on a grid^3 mesh of its box; weights 1; 8 bins over [10, 120]."""
+    g = _rng(3)
+    sizes = np.round(np.exp(g.uniform(np.log(5e4), np.log(5e5), ncat)) * scale).astype(np.int64)
+    sides = g.uniform(500.0, 1000.0, ncat)
+    parts = []
+    for i in range(ncat):
+        L = float(sides[i])
+        half = int(sizes[i]) // 2
+        uni = uniform(half, 3, L, 1000 + i)
+        ln = lognormal_poisson(float(sizes[i] - half), L, 1000 + i, grid=grid)
+        parts.append(np.concatenate([uni, ln]))
+    offsets = np.zeros(ncat + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum([len(p) for p in parts])
+    pos = np.concatenate(parts)
+    boxes = np.repeat(sides[:, None], 3, axis=1)
+    return Batch("batch64", 3, linear_edges(10.0, 120.0, 8), boxes, offsets, pos, np.ones(len(pos)))
 
 
 def workload(name: str, seed: int | None = None, scale: float = 1.0) -> Workload:

@@ -369,6 +369,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
     int* job_pk = job_a + kMaxJobs;
     int* job_pre = job_pk + kMaxJobs;
     int* ws = job_pre + kMaxJobs + 4;
+    CatGeom* s_geo = reinterpret_cast<CatGeom*>(smem + kGeomOffset);
     T* crow = reinterpret_cast<T*>(smem + pair_fixed_bytes(sizeof(R), nthreads)) + warp * nbins * NQ;
 
     for (int i = threadIdx.x; i < kTab / 4; i += nthreads)
@@ -388,31 +389,34 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
         const int item = s_item;
         if (item >= *p.nitems) break;
         const int4 it = p.items[item];
-        const bool active = warp < it.z;
+        load_geom(s_geo, p.geo, it.z >> 8);
+        __syncthreads();
+        const CatGeom& g = *s_geo;
+        const bool active = warp < (it.z & 0xff);
         const int jslot = it.y + (active ? warp : 0);
         const int pidx = it.w + warp;
         int cc[D];
 #pragma unroll
-        for (int d = 0; d < D; ++d) cc[d] = (it.x / p.stride[d]) % p.nc[d];
+        for (int d = 0; d < D; ++d) cc[d] = ((it.x - g.base) / g.stride[d]) % g.nc[d];
         int njobs = 0, V = 0;
         for (int base = 0; base < p.nstencil; base += nthreads) {
             const int sidx = base + threadIdx.x;
             int keep = 0, len = 0, a = 0, pk = 0;
             if (sidx < p.nstencil) {
                 pk = p.stencil[sidx];
-                int cell = 0;
+                int cell = g.base;
                 bool ok = true;
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
                     int c = cc[d] + (int)(signed char)((pk >> (8 * d)) & 0xff);
                     if (c < 0) {
                         ok = ok && p.periodic;
-                        c += p.nc[d];
-                    } else if (c >= p.nc[d]) {
+                        c += g.nc[d];
+                    } else if (c >= g.nc[d]) {
                         ok = ok && p.periodic;
-                        c -= p.nc[d];
+                        c -= g.nc[d];
                     }
-                    cell += c * p.stride[d];
+                    cell += c * g.stride[d];
                 }
                 if (ok) {
                     a = p.cell_start[cell];
@@ -451,7 +455,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
             const int seg_n = job_pre[j + 1] - job_pre[j];
             const int packed = job_pk[j];
             T xjs[D];
-            if (!cell_geometry<D, T>(p, cc, packed, xj, xjs)) continue;
+            if (!cell_geometry<D, T>(p, g, cc, packed, xj, xjs)) continue;
             for (int c0 = 0; c0 < seg_n; c0 += 32) {
                 const int k = c0 + lane;
                 if (k >= seg_n) break;
@@ -465,7 +469,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
                     r2 = fma(dx[d], dx[d], r2);
                 }
                 bool fl = false, ex = false;
-                const int b = decide_bin<D, T>(p, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &fl, &ex);
+                const int b = decide_bin<D, T>(p, g, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &fl, &ex);
                 if (b < 0) continue;
                 const T rinv = rsqrt_t(r2);
                 T u[D];

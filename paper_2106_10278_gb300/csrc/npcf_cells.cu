@@ -27,17 +27,26 @@ __global__ void k_cell_ids(const CellParams p)
     if (i >= p.n) return;
     const T* pos = static_cast<const T*>(p.pos) + i * p.D;
     const T w = static_cast<const T*>(p.w)[i];
+    int cat = 0;
+    if (p.ncat > 1) {  // the catalogue holding particle i: offsets[cat] <= i < offsets[cat + 1]
+        int lo = 0, hi = p.ncat;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (p.offsets[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        cat = lo;
+    }
+    const CatGeom& g = p.geo[cat];
     int bad = isfinite((double)w) ? 0 : 1;
-    int cell = 0;
-    int stride = 1;
+    int cell = g.base;
     for (int d = 0; d < p.D; ++d) {
         const double x = (double)pos[d];
         if (!isfinite(x)) bad |= 1;
-        else if (!(x >= 0.0 && x < p.box[d])) bad |= 2;
-        int c = isfinite(x) ? (int)floor(x * p.inv_side[d]) : 0;
-        c = c < 0 ? 0 : (c >= p.nc[d] ? p.nc[d] - 1 : c);
-        cell += c * stride;
-        stride *= p.nc[d];
+        else if (!(x >= 0.0 && x < g.box[d])) bad |= 2;
+        int c = isfinite(x) ? (int)floor(x * g.inv_side[d]) : 0;
+        c = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
+        cell += c * g.stride[d];
     }
     if (bad) atomicOr(p.err, bad);
     p.cid[i] = cell;
@@ -175,8 +184,10 @@ __global__ void k_cell_select(const int* cell_start, const int* perm, int ncells
     cell_items[c] = (hi - lo + warps - 1) / warps;
 }
 
+// item = (global cell, first slot, primaries | catalogue << 8, first primary)
 __global__ void k_write_items(int ncells, int warps, const int* cell_lo, const int* cell_prims,
-                              const int* prim_start, const int* item_start, int4* items)
+                              const int* prim_start, const int* item_start, int ncat, const int* cat_cells,
+                              int4* items)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
@@ -184,9 +195,19 @@ __global__ void k_write_items(int ncells, int warps, const int* cell_lo, const i
     const int lo = cell_lo[c];
     const int pbase = prim_start[c];
     const int ibase = item_start[c];
+    int cat = 0;
+    if (ncat > 1) {
+        int a = 0, b = ncat;
+        while (b - a > 1) {
+            const int mid = (a + b) >> 1;
+            if (cat_cells[mid] <= c) a = mid;
+            else b = mid;
+        }
+        cat = a;
+    }
     for (int k = 0; k * warps < np; ++k) {
         const int cnt = min(warps, np - k * warps);
-        items[ibase + k] = make_int4(c, lo + k * warps, cnt, pbase + k * warps);
+        items[ibase + k] = make_int4(c, lo + k * warps, cnt | (cat << 8), pbase + k * warps);
     }
 }
 
@@ -206,6 +227,17 @@ __global__ void k_reduce_rows(const double* partial, int rows, int ncols, double
     double s = 0.0;
     for (int r = 0; r < rows; ++r) s += partial[(size_t)r * ncols + k];
     out[k] = s * scale;
+}
+
+__global__ void k_reduce_cats(const double* partial, int rows, int ncols, const double* scales, double* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncols) return;
+    const int c = blockIdx.y;
+    const double* pc = partial + (size_t)c * rows * ncols;
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += pc[(size_t)r * ncols + k];
+    out[(size_t)c * ncols + k] = s * scales[c];
 }
 
 inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -278,7 +310,7 @@ cudaError_t launch_make_items(const ItemBuffers& b, const int* cell_start, const
     e = launch_exclusive_scan(b.cell_items, b.item_start, ncells, b.scan_scratch, s);
     if (e != cudaSuccess) return e;
     k_write_items<<<blocks_for(ncells, t), t, 0, s>>>(ncells, warps, b.cell_lo, b.cell_prims, b.prim_start,
-                                                      b.item_start, b.items); ++launch_counter();
+                                                      b.item_start, b.ncat, b.cat_cells, b.items); ++launch_counter();
     k_totals<<<1, 32, 0, s>>>(ncells, b.cell_prims, b.prim_start, b.cell_items, b.item_start, b.nprim, b.nitems); ++launch_counter();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -290,6 +322,15 @@ cudaError_t launch_reduce(const double* partial, int rows, int ncols, double sca
     if (ncols <= 0) return cudaSuccess;
     const int t = 256;
     k_reduce_rows<<<blocks_for(ncols, t), t, 0, s>>>(partial, rows, ncols, scale, out); ++launch_counter();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, int ncat, const double* scales, double* out,
+                               cudaStream_t s)
+{
+    if (ncols <= 0 || ncat <= 0) return cudaSuccess;
+    const int t = 256;
+    k_reduce_cats<<<dim3(blocks_for(ncols, t), ncat), t, 0, s>>>(partial, rows, ncols, scales, out); ++launch_counter();
     return cudaGetLastError();
 }
 

@@ -129,12 +129,15 @@ __global__ void __launch_bounds__(kCoupleThreads) k_couple(const CoupleParams p)
     const int nacc = (blk.w - blk.z) * comps;
     for (int k = threadIdx.x; k < nacc; k += blockDim.x) acc[k] = AccT(0);
 
-    const int nprim = *p.nprim;
+    // catalogue blockIdx.z: its primaries' rows of the a-array and its own partial rows
+    const int cat = blockIdx.z;
+    const int nprim = p.cat_count ? p.cat_count[cat] : *p.nprim;
+    const size_t first = p.cat_first ? (size_t)p.cat_first[cat] : 0;
     const int nchunk = (nprim + p.chunk - 1) / p.chunk;
-    double* prow = p.partial + (size_t)blockIdx.x * 2 * p.ncoeff;
-    const T* aglob = static_cast<const T*>(p.a);
-    const T* wglob = static_cast<const T*>(p.wprim);
+    double* prow = p.partial + ((size_t)cat * gridDim.x + blockIdx.x) * 2 * p.ncoeff;
     const int stride = p.nbins * p.nq;
+    const T* aglob = static_cast<const T*>(p.a) + first * stride;
+    const T* wglob = static_cast<const T*>(p.wprim) + first;
 
     for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
         const int p0 = ch * p.chunk;
@@ -177,7 +180,7 @@ cudaError_t launch_t(const CoupleParams& p, int grid, int smem, cudaStream_t s)
     auto kern = k_couple<MODE, D, LMAX, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(grid, p.nkb), kCoupleThreads, smem, s>>>(p); ++launch_counter();
+    kern<<<dim3(grid, p.nkb, p.ncat > 1 ? p.ncat : 1), kCoupleThreads, smem, s>>>(p); ++launch_counter();
     return cudaGetLastError();
 }
 

@@ -124,12 +124,15 @@ __global__ void __launch_bounds__(512) k_couple_d3n4(const CoupleParams p)
     const int npair = blk.y - blk.x;
     const int ntask = (npair + 3) / 4;
 
-    const int nprim = *p.nprim;
+    // catalogue blockIdx.z: its primaries' rows of the a-array and its own partial rows
+    const int cat = blockIdx.z;
+    const int nprim = p.cat_count ? p.cat_count[cat] : *p.nprim;
+    const size_t first = p.cat_first ? (size_t)p.cat_first[cat] : 0;
     const int nchunk = (nprim + p.chunk - 1) / p.chunk;
-    double* prow = p.partial + (size_t)blockIdx.x * 2 * p.ncoeff;
-    const T* aglob = static_cast<const T*>(p.a);
-    const T* wglob = static_cast<const T*>(p.wprim);
+    double* prow = p.partial + ((size_t)cat * gridDim.x + blockIdx.x) * 2 * p.ncoeff;
     const int gstride = nbins * p.nq;
+    const T* aglob = static_cast<const T*>(p.a) + first * gstride;
+    const T* wglob = static_cast<const T*>(p.wprim) + first;
 
     for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
         const int p0 = ch * p.chunk;
@@ -194,7 +197,7 @@ cudaError_t launch_t(const CoupleParams& p, int grid, int threads, int smem, cud
     auto kern = k_couple_d3n4<LMAX, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(grid, p.nkb), threads, smem, s>>>(p); ++launch_counter();
+    kern<<<dim3(grid, p.nkb, p.ncat > 1 ? p.ncat : 1), threads, smem, s>>>(p); ++launch_counter();
     return cudaGetLastError();
 }
 

@@ -23,14 +23,32 @@ inline int num_real_components(int D, int lmax)
     return s;
 }
 
+// ------------------------------------------------------- catalogue geometry
+// The cell grid of one catalogue.  A call covers one or more catalogues; their
+// cells are numbered consecutively (catalogue c owns global cells
+// [base, base + ncells)), so one cell list and one pair launch serve them all.
+struct CatGeom {
+    int nc[4];           // cells per axis
+    int stride[4];       // local cell index = sum c[d] * stride[d]
+    int base;            // first global cell
+    int ncells;
+    int64_t first;       // first particle (input index)
+    float boxf[4];
+    float sidef[4];
+    double box[4];
+    double side[4];
+    double inv_side[4];  // nc[d] / box[d]
+};
+constexpr int kGeomWords = (int)(sizeof(CatGeom) / 4);
+
 // ---------------------------------------------------------------- cell list
 struct CellParams {
     int D;
     int64_t n;
-    int nc[4];          // cells per axis
-    int ncells;
-    double box[4];
-    double inv_side[4]; // nc[d] / box[d]
+    int ncells;              // all catalogues
+    int ncat;
+    const CatGeom* geo;      // ncat (device)
+    const int64_t* offsets;  // ncat + 1 particle offsets (device; used when ncat > 1)
     int periodic;
     const void* pos;    // n x D (float or double)
     const void* w;      // n
@@ -47,12 +65,7 @@ struct CellParams {
 struct PairParams {
     int D, nbins, lmax, nq;
     int periodic;
-    int nc[4];
-    int stride[4];         // cell index = sum c[d] * stride[d]
-    double box[4];
-    float boxf[4];
-    float sidef[4];
-    double side[4];
+    const CatGeom* geo;    // per-catalogue grids (device)
     float rmax2f, rmin2f;  // squared outer / inner radius (FP32, widened by the tolerance)
     float tol;             // absolute half-width of the near-edge window (FP32 path)
     float edgef[kMaxBins + 1];
@@ -70,7 +83,7 @@ struct PairParams {
     const unsigned char* tab;    // kTab entries
     const void* rec;             // sorted records
     const int* cell_start;
-    const int4* items;           // (cell, slot_lo, count, primary_base)
+    const int4* items;           // (global cell, slot_lo, count | catalogue << 8, primary_base)
     const int* nitems;
     int* ticket;
     const void* qnorm;           // nq normalisation constants (T)
@@ -99,6 +112,9 @@ struct CoupleParams {
     const int2* lam2;          // D=2, N=4: (l1, l2) per Lambda index
     const signed char* lam_odd;// D=3, N=4: 1 if l1+l2+l3 is odd (coefficient imaginary)
     const void* pref;          // N=3: per-l factor of the zero coupling (T)
+    int ncat;                  // catalogues (blockIdx.z); 0 or 1 for a single one
+    const int* cat_first;      // ncat: first primary of each catalogue in the a-array (NULL: one catalogue)
+    const int* cat_count;      // ncat: its primaries
 };
 
 // ------------------------------------------------------------- launchers
@@ -123,6 +139,8 @@ struct ItemBuffers {
     int* nitems;       // 1
     int* nprim;        // 1
     int* ticket;       // 1
+    int ncat = 1;
+    const int* cat_cells = nullptr;  // ncat + 1 first global cells (used when ncat > 1)
 };
 cudaError_t launch_make_items(const ItemBuffers& b, const int* cell_start, const int* perm, int ncells, int64_t pb,
                               int64_t pe, int warps, cudaStream_t s);
@@ -132,6 +150,9 @@ int pair_kernel_compiled_lmax(int D, int fp64, int lmax);
 cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
 int couple_smem(const CoupleParams& p, int fp64);
 cudaError_t launch_reduce(const double* partial, int rows, int ncols, double scale, double* out, cudaStream_t s);
+// per catalogue c: out[c][k] = scales[c] * sum_r partial[c][r][k]
+cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, int ncat, const double* scales, double* out,
+                               cudaStream_t s);
 
 // adjoint of the N=3 estimator (npcf_backward.cu)
 int adjoint_compiled_lmax(int D, int lmax);

@@ -57,11 +57,21 @@ __host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int n
 
 constexpr int kMaxJobs = 1024;  // neighbour cells of one item (the host keeps stencils this small)
 
+// fixed part: radial table | edges + lane map (576) | job lists + scan scratch | the item's CatGeom
+constexpr int kGeomOffset = kTab + 576 + (3 * kMaxJobs + 4 + 72) * 4;
 __host__ __device__ inline int pair_fixed_bytes(int rec_bytes, int threads)
 {
     (void)rec_bytes;
     (void)threads;
-    return kTab + 576 + (3 * kMaxJobs + 4 + 72) * 4;
+    return kGeomOffset + ((int)sizeof(CatGeom) + 15) / 16 * 16;
+}
+
+// Thread-block-wide: copy catalogue `cat`'s grid into shared memory (the
+// caller synchronises before anyone reads it).
+__device__ __forceinline__ void load_geom(CatGeom* dst, const CatGeom* geo, int cat)
+{
+    if (threadIdx.x < kGeomWords)
+        reinterpret_cast<int*>(dst)[threadIdx.x] = reinterpret_cast<const int*>(geo + cat)[threadIdx.x];
 }
 
 template <int D, int LMAX, typename T>
@@ -140,9 +150,9 @@ __device__ __forceinline__ void block_scan2(int a, int b, int* ea, int* eb, int*
 // few pairs in FP64.  Returns -1 outside the bins.  Shared by the forward and
 // adjoint pair kernels so that both see the same pair set.
 template <int D, typename T>
-__device__ __forceinline__ int decide_bin(const PairParams& p, const unsigned char* tab, const float* s_edge,
-                                          const double* s_edge2, const int* cc, int packed, const T* xj,
-                                          const Rec<D, T>& pk, T r2, bool* flagged, bool* exact_out)
+__device__ __forceinline__ int decide_bin(const PairParams& p, const CatGeom& g, const unsigned char* tab,
+                                          const float* s_edge, const double* s_edge2, const int* cc, int packed,
+                                          const T* xj, const Rec<D, T>& pk, T r2, bool* flagged, bool* exact_out)
 {
     constexpr bool kFP32 = sizeof(T) == 4;
     if (!(r2 > T(0) && r2 < T(p.rmax2f) && r2 >= T(p.rmin2f))) return -1;
@@ -165,7 +175,7 @@ __device__ __forceinline__ int decide_bin(const PairParams& p, const unsigned ch
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
-            const double shd = c < 0 ? -p.box[d] : (c >= p.nc[d] ? p.box[d] : 0.0);
+            const double shd = c < 0 ? -g.box[d] : (c >= g.nc[d] ? g.box[d] : 0.0);
             const double dd = __dadd_rn(__dadd_rn((double)pk.x(d), -(double)xj[d]), shd);
             sd = (d == 0) ? __dmul_rn(dd, dd) : __dadd_rn(sd, __dmul_rn(dd, dd));
         }
@@ -185,7 +195,8 @@ __device__ __forceinline__ int decide_bin(const PairParams& p, const unsigned ch
 // position (so that pk - xjs is the minimum-image separation) and whether the
 // cell can hold a pair in [e_0, e_nb) of that primary.
 template <int D, typename T>
-__device__ __forceinline__ bool cell_geometry(const PairParams& p, const int* cc, int packed, const T* xj, T* xjs)
+__device__ __forceinline__ bool cell_geometry(const PairParams& p, const CatGeom& g, const int* cc, int packed,
+                                              const T* xj, T* xjs)
 {
     constexpr bool kFP32 = sizeof(T) == 4;
     T dmin2 = T(0), dmax2 = T(0);
@@ -194,15 +205,15 @@ __device__ __forceinline__ bool cell_geometry(const PairParams& p, const int* cc
         const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
         T side, box;
         if constexpr (kFP32) {
-            side = p.sidef[d];
-            box = p.boxf[d];
+            side = g.sidef[d];
+            box = g.boxf[d];
         } else {
-            side = p.side[d];
-            box = p.box[d];
+            side = g.side[d];
+            box = g.box[d];
         }
         const T lo = T(c) * side;
         const T hi = lo + side;
-        const T sh = c < 0 ? -box : (c >= p.nc[d] ? box : T(0));
+        const T sh = c < 0 ? -box : (c >= g.nc[d] ? box : T(0));
         xjs[d] = xj[d] - sh;
         const T a = fmax(fmax(lo - xj[d], xj[d] - hi), T(0));
         dmin2 = fma(a, a, dmin2);
@@ -270,6 +281,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     int* job_pk = job_a + kMaxJobs;                          // kMaxJobs: packed stencil offset
     int* job_pre = job_pk + kMaxJobs;                        // kMaxJobs + 1: record prefix
     int* ws = job_pre + kMaxJobs + 4;                        // 68 ints of scan scratch
+    CatGeom* s_geo = reinterpret_cast<CatGeom*>(smem + kGeomOffset);
     unsigned char* wbase = smem + pair_fixed_bytes(sizeof(R), nthreads) +
                            warp * pair_warp_bytes(sizeof(R), sizeof(T), nbins, NQ);
     int* qcnt = reinterpret_cast<int*>(wbase);
@@ -307,13 +319,16 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         const int item = s_item;
         if (item >= *p.nitems) break;
         const int4 it = p.items[item];
-        const bool active = warp < it.z;
+        load_geom(s_geo, p.geo, it.z >> 8);
+        __syncthreads();
+        const CatGeom& g = *s_geo;
+        const bool active = warp < (it.z & 0xff);
         const int jslot = it.y + (active ? warp : 0);
         const int pidx = it.w + warp;
 
         int cc[D];
 #pragma unroll
-        for (int d = 0; d < D; ++d) cc[d] = (it.x / p.stride[d]) % p.nc[d];
+        for (int d = 0; d < D; ++d) cc[d] = ((it.x - g.base) / g.stride[d]) % g.nc[d];
 
         // the item's neighbour cells: valid (periodic or inside the grid) and non-empty,
         // in stencil order, with the prefix of their record counts
@@ -323,19 +338,19 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
             int keep = 0, len = 0, a = 0, pk = 0;
             if (sidx < p.nstencil) {
                 pk = p.stencil[sidx];
-                int cell = 0;
+                int cell = g.base;
                 bool ok = true;
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
                     int c = cc[d] + (int)(signed char)((pk >> (8 * d)) & 0xff);
                     if (c < 0) {
                         ok = ok && p.periodic;
-                        c += p.nc[d];
-                    } else if (c >= p.nc[d]) {
+                        c += g.nc[d];
+                    } else if (c >= g.nc[d]) {
                         ok = ok && p.periodic;
-                        c -= p.nc[d];
+                        c -= g.nc[d];
                     }
-                    cell += c * p.stride[d];
+                    cell += c * g.stride[d];
                 }
                 if (ok) {
                     a = p.cell_start[cell];
@@ -415,7 +430,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                 const int seg_n = job_pre[j + 1] - job_pre[j];
                 const int packed = job_pk[j];
                 T xjs[D];
-                if (!cell_geometry<D, T>(p, cc, packed, xj, xjs)) continue;
+                if (!cell_geometry<D, T>(p, g, cc, packed, xj, xjs)) continue;
                 ncand += seg_n;
                 const R* src = rec + seg_a;
                 R nxt0 = ldg_rec(src, lane < seg_n ? lane : 0);
@@ -435,7 +450,8 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                         r2 = fma(dx[d], dx[d], r2);
                     }
                     bool anyflag = false, anyexact = false;
-                    const int bin = valid ? decide_bin<D, T>(p, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &anyflag, &anyexact)
+                    const int bin = valid ? decide_bin<D, T>(p, g, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &anyflag,
+                                                             &anyexact)
                                           : -1;
                     ++nchunks;
                     nflag += __any_sync(full, anyflag) ? 1u : 0u;

@@ -116,6 +116,12 @@ struct npcf_plan_s {
     DevBuf w_cid, w_perm, w_rec, w_cells, w_items, w_a, w_wprim, w_partial, w_small, w_hpos, w_hw, w_hout;
     // adjoint (npcf_backward)
     DevBuf d_keybase, w_cbuf, w_gpos, w_gw, w_gwp;
+    // the single-catalogue grid (one CatGeom) and the last batched layout
+    DevBuf d_geo;
+    DevBuf b_geo, b_cells, b_offsets, b_first, b_count, b_scales, b_stencil;
+    std::vector<int64_t> b_key_off;
+    std::vector<double> b_key_box;
+    int b_ncat = 0, b_ncells = 0, b_nstencil = 0;
     // cached cell grid
     int grid_c = -1;
     int nc[4] = {1, 1, 1, 1};
@@ -352,6 +358,30 @@ GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
     return best.c > 0 ? best : any;
 }
 
+CatGeom make_geom(int D, const int* nc, const double* box, int base, int64_t first)
+{
+    CatGeom g{};
+    int stride = 1, ncells = 1;
+    for (int d = 0; d < 4; ++d) {
+        const bool on = d < D;
+        g.nc[d] = on ? nc[d] : 1;
+        g.stride[d] = stride;
+        g.box[d] = on ? box[d] : 1.0;
+        g.boxf[d] = (float)g.box[d];
+        g.side[d] = g.box[d] / g.nc[d];
+        g.sidef[d] = (float)g.side[d];
+        g.inv_side[d] = g.nc[d] / g.box[d];
+        if (on) {
+            stride *= nc[d];
+            ncells *= nc[d];
+        }
+    }
+    g.base = base;
+    g.ncells = ncells;
+    g.first = first;
+    return g;
+}
+
 // ------------------------------------------------------------ lane map
 void lane_map(npcf_plan_s* P)
 {
@@ -557,14 +587,15 @@ npcf_status prepare_grid(npcf_plan_s* P, int64_t n)
     P->ncells = g.ncells;
     P->nstencil = (int)g.stencil.size();
     CUDA_TRY(upload(P->d_stencil, g.stencil));
+    CUDA_TRY(upload(P->d_geo, std::vector<CatGeom>{make_geom(P->D, g.nc, P->box, 0, 0)}));
     P->grid_n = n;
     return NPCF_OK;
 }
 
-npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int rows)
+npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int rows, int ncells)
 {
     const int rb = rec_bytes(P->D, P->fp64), tb = P->fp64 ? 8 : 4;
-    const size_t nc = (size_t)P->ncells;
+    const size_t nc = (size_t)ncells;
     auto R = [&](DevBuf& b, size_t bytes) -> npcf_status {
         if (b.reserve(bytes) != cudaSuccess)
             return fail(NPCF_ERR_WORKSPACE, "device allocation of %zu bytes failed", bytes);
@@ -584,6 +615,58 @@ npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int 
     return NPCF_OK;
 }
 
+// The cell grid a call runs on: one catalogue (the plan's box) or a batch.
+struct GridView {
+    int ncells = 0;
+    int ncat = 1;
+    const CatGeom* geo = nullptr;      // device, ncat
+    const int64_t* offsets = nullptr;  // device, ncat + 1 (ncat > 1)
+    const int* cat_cells = nullptr;    // device, ncat + 1 (ncat > 1)
+    const int* stencil = nullptr;      // device
+    int nstencil = 0;
+};
+
+GridView single_view(const npcf_plan_s* P)
+{
+    GridView v;
+    v.ncells = P->ncells;
+    v.geo = P->d_geo.as<CatGeom>();
+    v.stencil = P->d_stencil.as<int>();
+    v.nstencil = P->nstencil;
+    return v;
+}
+
+// Coupling-kernel parameters for the plan's tables (one catalogue).
+CoupleParams couple_params(const npcf_plan_s* P, const void* a, const void* wprim, const int* nprim, int chunk,
+                           double* partial)
+{
+    CoupleParams kp{};
+    kp.D = P->D;
+    kp.N = P->N;
+    kp.nbins = P->nbins;
+    kp.lmax = P->lmax;
+    kp.nq = P->nq;
+    kp.nlam = P->nlam;
+    kp.a = a;
+    kp.wprim = wprim;
+    kp.nprim = nprim;
+    kp.chunk = chunk;
+    kp.ncoeff = (int)P->ncoeff;
+    kp.partial = partial;
+    kp.pairs = P->d_pairs.as<int2>();
+    kp.pair_key = P->d_pair_key.as<int>();
+    kp.kblocks = P->d_kblocks.as<int4>();
+    kp.nkb = (int)P->kblocks.size();
+    kp.max_block_keys = P->max_block_keys;
+    kp.max_block_pairs = P->max_block_pairs;
+    kp.task_pairs = P->d_task.as<int>();
+    kp.lam2 = P->d_lam2.as<int2>();
+    kp.lam_odd = P->d_lamodd.as<signed char>();
+    kp.pref = P->d_pref.p;
+    kp.ncat = 1;
+    return kp;
+}
+
 // What the cell-list and pair stages leave for the stages after them.
 struct PairStage {
     ItemBuffers ib;
@@ -594,10 +677,10 @@ struct PairStage {
 
 // Cell list, work items and the pair kernel (the a-array of every primary in
 // [pb, pe)), on workspace already reserved for n particles.
-npcf_status run_pairs(npcf_plan_s* P, const void* pos, const void* w, int64_t n, int64_t pb, int64_t pe,
-                      cudaStream_t s, PairStage* out)
+npcf_status run_pairs(npcf_plan_s* P, const GridView& gv, const void* pos, const void* w, int64_t n, int64_t pb,
+                      int64_t pe, cudaStream_t s, PairStage* out)
 {
-    const int nc = P->ncells;
+    const int nc = gv.ncells;
     int* cells = P->w_cells.as<int>();
     int* cell_count = cells;                // nc + 1
     int* cell_start = cells + (nc + 1);     // nc + 1
@@ -614,6 +697,8 @@ npcf_status run_pairs(npcf_plan_s* P, const void* pos, const void* w, int64_t n,
     ib.nitems = small + S_NITEMS;
     ib.nprim = small + S_NPRIM;
     ib.ticket = small + S_TICKET;
+    ib.ncat = gv.ncat;
+    ib.cat_cells = gv.cat_cells;
     unsigned long long* stats = reinterpret_cast<unsigned long long*>(small + 4);
 
     launch_counter() = 0;
@@ -630,12 +715,10 @@ npcf_status run_pairs(npcf_plan_s* P, const void* pos, const void* w, int64_t n,
     cp.D = P->D;
     cp.n = n;
     cp.ncells = nc;
+    cp.ncat = gv.ncat;
+    cp.geo = gv.geo;
+    cp.offsets = gv.offsets;
     cp.periodic = P->opts.periodic;
-    for (int d = 0; d < 4; ++d) {
-        cp.nc[d] = P->nc[d];
-        cp.box[d] = P->box[d];
-        cp.inv_side[d] = P->nc[d] / P->box[d];
-    }
     cp.pos = pos;
     cp.w = w;
     cp.cid = P->w_cid.as<int>();
@@ -652,18 +735,9 @@ npcf_status run_pairs(npcf_plan_s* P, const void* pos, const void* w, int64_t n,
 
     if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[1], s));
     PairParams pp = P->pp;
-    int stride = 1;
-    for (int d = 0; d < P->D; ++d) {
-        pp.nc[d] = P->nc[d];
-        pp.stride[d] = stride;
-        stride *= P->nc[d];
-        pp.box[d] = P->box[d];
-        pp.boxf[d] = (float)P->box[d];
-        pp.side[d] = P->box[d] / P->nc[d];
-        pp.sidef[d] = (float)pp.side[d];
-    }
-    pp.nstencil = P->nstencil;
-    pp.stencil = P->d_stencil.as<int>();
+    pp.geo = gv.geo;
+    pp.nstencil = gv.nstencil;
+    pp.stencil = gv.stencil;
     pp.rec = P->w_rec.p;
     pp.cell_start = cell_start;
     pp.items = ib.items;
@@ -697,37 +771,15 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     const int nkb = (int)P->kblocks.size();
     int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
     rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim_max + chunk - 1) / chunk));
-    if ((st = reserve_workspace(P, n, nprim_max, rows)) != NPCF_OK) return st;
+    if ((st = reserve_workspace(P, n, nprim_max, rows, P->ncells)) != NPCF_OK) return st;
     PairStage ps;
-    if ((st = run_pairs(P, pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
+    if ((st = run_pairs(P, single_view(P), pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
     const ItemBuffers& ib = ps.ib;
     int* small = ps.small;
     unsigned long long* stats = ps.stats;
     cudaError_t e;
 
-    CoupleParams kp{};
-    kp.D = P->D;
-    kp.N = P->N;
-    kp.nbins = P->nbins;
-    kp.lmax = P->lmax;
-    kp.nq = P->nq;
-    kp.nlam = P->nlam;
-    kp.a = P->w_a.p;
-    kp.wprim = P->w_wprim.p;
-    kp.nprim = ib.nprim;
-    kp.chunk = chunk;
-    kp.ncoeff = (int)P->ncoeff;
-    kp.partial = P->w_partial.as<double>();
-    kp.pairs = P->d_pairs.as<int2>();
-    kp.pair_key = P->d_pair_key.as<int>();
-    kp.kblocks = P->d_kblocks.as<int4>();
-    kp.nkb = nkb;
-    kp.max_block_keys = P->max_block_keys;
-    kp.max_block_pairs = P->max_block_pairs;
-    kp.task_pairs = P->d_task.as<int>();
-    kp.lam2 = P->d_lam2.as<int2>();
-    kp.lam_odd = P->d_lamodd.as<signed char>();
-    kp.pref = P->d_pref.p;
+    CoupleParams kp = couple_params(P, P->w_a.p, P->w_wprim.p, ib.nprim, chunk, P->w_partial.as<double>());
     CUDA_TRY(cudaMemsetAsync(kp.partial, 0, sizeof(double) * rows * 2 * P->ncoeff, s));
     const int csm = couple_smem(kp, P->fp64);
     e = launch_couple(kp, P->fp64, rows, csm, s);
@@ -762,7 +814,7 @@ npcf_status run_backward(npcf_plan_s* P, const void* pos, const void* w, int64_t
     if (asmem > P->smem_optin)
         return fail(NPCF_ERR_UNSUPPORTED, "the adjoint pair kernel needs %d bytes of shared memory", asmem);
     const int64_t nprim = pe - pb;
-    if ((st = reserve_workspace(P, n, nprim, 1)) != NPCF_OK) return st;
+    if ((st = reserve_workspace(P, n, nprim, 1, P->ncells)) != NPCF_OK) return st;
     const size_t tb = P->fp64 ? 8 : 4;
     const size_t n1 = (size_t)std::max<int64_t>(n, 1), p1 = (size_t)std::max<int64_t>(nprim, 1);
     if (P->w_cbuf.reserve(tb * p1 * P->nbins * P->nq) != cudaSuccess ||
@@ -776,7 +828,7 @@ npcf_status run_backward(npcf_plan_s* P, const void* pos, const void* w, int64_t
         CUDA_TRY(upload(P->d_keybase, kb));
     }
     PairStage ps;
-    if ((st = run_pairs(P, pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
+    if ((st = run_pairs(P, single_view(P), pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
     P->timed = 0;
     double* gpos = P->w_gpos.as<double>();
     double* gw = P->w_gw.as<double>();
@@ -798,6 +850,139 @@ npcf_status run_backward(npcf_plan_s* P, const void* pos, const void* w, int64_t
     CUDA_TRY(cudaMemcpyAsync(P->h_stats, ps.stats, 64, cudaMemcpyDeviceToHost, s));
     P->last_stream = s;
     P->last_nprim = nprim;
+    return NPCF_OK;
+}
+
+// The cell grids of a batch.  Every catalogue is cut with the same
+// subdivision c (cells of side >= r_max/c), so one stencil -- built for side
+// exactly r_max/c, a superset of each catalogue's own -- serves them all;
+// catalogue i's cells follow catalogue i-1's.  c minimises the same
+// candidates-plus-overhead cost as the single-catalogue grid, summed over the
+// catalogues.  Cached: an unchanged layout uploads nothing.
+npcf_status prepare_batch(npcf_plan_s* P, const int64_t* offsets, const double* boxes, int ncat)
+{
+    std::vector<int64_t> off(offsets, offsets + ncat + 1);
+    std::vector<double> bx(boxes, boxes + (size_t)ncat * P->D);
+    if (P->b_ncat == ncat && P->b_key_off == off && P->b_key_box == bx) return NPCF_OK;
+    const int D = P->D;
+    const double rmax = P->edges[P->nbins];
+    const double reach = rmax * (1.0 + 1e-6) + 1e-12;
+    int best_c = 0;
+    double best_cost = 1e300;
+    std::vector<int> best_stencil;
+    for (int c = 1; c <= 4; ++c) {
+        double side[4] = {rmax / c, rmax / c, rmax / c, rmax / c};
+        std::vector<int> st = make_stencil(D, c, side, reach);
+        if ((int)st.size() > kMaxJobs) continue;
+        bool ok = true;
+        double cost = 0.0;
+        int64_t total = 0;
+        for (int i = 0; i < ncat && ok; ++i) {
+            int64_t cells = 1;
+            for (int d = 0; d < D; ++d) {
+                int k = (int)std::floor(bx[(size_t)i * D + d] * c / rmax);
+                if (k < 1) k = 1;
+                if (P->opts.periodic && k < 2 * c + 1) ok = false;
+                if (k > 4096) k = 4096;
+                cells *= k;
+            }
+            total += cells;
+            const double ni = (double)(off[i + 1] - off[i]);
+            cost += ni * st.size() * (ni / cells + 24.0);
+        }
+        if (!ok || total >= (int64_t(1) << 26)) continue;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best_c = c;
+            best_stencil = st;
+        }
+    }
+    if (best_c == 0)
+        return fail(NPCF_ERR_UNSUPPORTED, "no common cell grid fits r_max=%g in every box (need r_max < box/2.25)",
+                    rmax);
+    std::vector<CatGeom> geo(ncat);
+    std::vector<int> cells(ncat + 1), first(ncat), count(ncat);
+    std::vector<double> scales(ncat);
+    int base = 0;
+    for (int i = 0; i < ncat; ++i) {
+        int nc[4] = {1, 1, 1, 1};
+        double V = 1.0;
+        for (int d = 0; d < D; ++d) {
+            const double b = bx[(size_t)i * D + d];
+            nc[d] = std::min(4096, std::max(1, (int)std::floor(b * best_c / rmax)));
+            V *= b;
+        }
+        geo[i] = make_geom(D, nc, &bx[(size_t)i * D], base, off[i]);
+        cells[i] = base;
+        first[i] = (int)off[i];
+        count[i] = (int)(off[i + 1] - off[i]);
+        scales[i] = 1.0 / V;
+        base += geo[i].ncells;
+    }
+    cells[ncat] = base;
+    P->b_ncat = 0;  // invalid until every upload succeeded
+    CUDA_TRY(upload(P->b_geo, geo));
+    CUDA_TRY(upload(P->b_cells, cells));
+    CUDA_TRY(upload(P->b_offsets, off));
+    CUDA_TRY(upload(P->b_first, first));
+    CUDA_TRY(upload(P->b_count, count));
+    CUDA_TRY(upload(P->b_scales, scales));
+    CUDA_TRY(upload(P->b_stencil, best_stencil));
+    P->b_ncells = base;
+    P->b_nstencil = (int)best_stencil.size();
+    P->b_key_off = off;
+    P->b_key_box = bx;
+    P->b_ncat = ncat;
+    return NPCF_OK;
+}
+
+// ncat catalogues in one pass: one cell list over all of them, one pair-kernel
+// launch over every catalogue's work items (the persistent CTAs take items
+// from one queue, so small and large catalogues share the GPU), one coupling
+// launch with a grid layer per catalogue and one reduction that applies each
+// catalogue's 1/V.
+npcf_status run_batched(npcf_plan_s* P, const void* pos, const void* w, const int64_t* offsets, const double* boxes,
+                        int ncat, double* coeffs, cudaStream_t s)
+{
+    npcf_status st;
+    if ((st = ensure_device(P)) != NPCF_OK) return st;
+    if ((st = prepare_batch(P, offsets, boxes, ncat)) != NPCF_OK) return st;
+    const int64_t n = offsets[ncat];
+    int64_t nmax = 0;
+    for (int i = 0; i < ncat; ++i) nmax = std::max<int64_t>(nmax, offsets[i + 1] - offsets[i]);
+    const int chunk = 128;
+    const int nkb = (int)P->kblocks.size();
+    int rows = std::max(1, (2 * P->nsm + nkb * ncat - 1) / (nkb * ncat));
+    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nmax + chunk - 1) / chunk));
+    if ((st = reserve_workspace(P, n, n, rows * ncat, P->b_ncells)) != NPCF_OK) return st;
+    GridView gv;
+    gv.ncells = P->b_ncells;
+    gv.ncat = ncat;
+    gv.geo = P->b_geo.as<CatGeom>();
+    gv.offsets = P->b_offsets.as<int64_t>();
+    gv.cat_cells = P->b_cells.as<int>();
+    gv.stencil = P->b_stencil.as<int>();
+    gv.nstencil = P->b_nstencil;
+    PairStage ps;
+    if ((st = run_pairs(P, gv, pos, w, n, 0, n, s, &ps)) != NPCF_OK) return st;
+    CoupleParams kp = couple_params(P, P->w_a.p, P->w_wprim.p, ps.ib.nprim, chunk, P->w_partial.as<double>());
+    kp.ncat = ncat;
+    kp.cat_first = P->b_first.as<int>();
+    kp.cat_count = P->b_count.as<int>();
+    CUDA_TRY(cudaMemsetAsync(kp.partial, 0, sizeof(double) * rows * ncat * 2 * P->ncoeff, s));
+    cudaError_t e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
+    if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[3], s));
+    CUDA_TRY(launch_reduce_cats(kp.partial, rows, (int)(2 * P->ncoeff), ncat, P->b_scales.as<double>(), coeffs, s));
+    if (P->opts.timing) {
+        CUDA_TRY(cudaEventRecord(P->ev[4], s));
+        P->timed = 1;
+    }
+    P->last_launches = launch_counter();
+    CUDA_TRY(cudaMemcpyAsync(P->h_small, ps.small, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, ps.stats, 64, cudaMemcpyDeviceToHost, s));
+    P->last_stream = s;
+    P->last_nprim = n;
     return NPCF_OK;
 }
 
@@ -980,6 +1165,30 @@ npcf_status npcf_last_counters(npcf_plan_t P, int64_t* counters, int n)
     return NPCF_OK;
 }
 
+npcf_status npcf_compute_batched(npcf_plan_t P, const void* pos, const void* w, const int64_t* offsets,
+                                 const double* boxes, int ncat, double* coeffs, npcf_stream_t stream)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (ncat < 1 || ncat > (1 << 20)) return fail(NPCF_ERR_ARG, "ncat=%d out of range", ncat);
+    if (!offsets || !boxes || !coeffs) return fail(NPCF_ERR_ARG, "offsets/boxes/coeffs is NULL");
+    if (offsets[0] != 0) return fail(NPCF_ERR_ARG, "offsets[0] must be 0");
+    for (int i = 0; i < ncat; ++i)
+        if (offsets[i + 1] < offsets[i]) return fail(NPCF_ERR_ARG, "offsets decrease at catalogue %d", i);
+    if (offsets[ncat] > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)offsets[ncat]);
+    for (int i = 0; i < ncat * P->D; ++i)
+        if (!(boxes[i] > 0.0) || !std::isfinite(boxes[i]))
+            return fail(NPCF_ERR_ARG, "box side %d of catalogue %d is not positive", i % P->D, i / P->D);
+    if (offsets[ncat] > 0 && (!pos || !w)) return fail(NPCF_ERR_ARG, "positions/weights are NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    npcf_status st = run_batched(P, pos, w, offsets, boxes, ncat, coeffs, s);
+    if (st != NPCF_OK) return st;
+    if (P->opts.sync_check) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return check_flags(P);
+    }
+    return NPCF_OK;
+}
+
 npcf_status npcf_backward(npcf_plan_t P, const void* pos, const void* w, int64_t n, const double* grad_coeffs,
                           int64_t pb, int64_t pe, void* grad_pos, void* grad_w, npcf_stream_t stream)
 {
@@ -1011,7 +1220,8 @@ void npcf_plan_destroy(npcf_plan_t P)
                       &P->d_lam2,  &P->d_lamodd, &P->d_pref, &P->d_stencil, &P->w_cid,    &P->w_perm,
                       &P->w_rec,   &P->w_cells, &P->w_items, &P->w_a,     &P->w_wprim,   &P->w_partial,
                       &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout,  &P->d_keybase, &P->w_cbuf,
-                      &P->w_gpos,  &P->w_gw,    &P->w_gwp};
+                      &P->w_gpos,  &P->w_gw,    &P->w_gwp,   &P->d_geo,   &P->b_geo,     &P->b_cells,
+                      &P->b_offsets, &P->b_first, &P->b_count, &P->b_scales, &P->b_stencil};
     for (DevBuf* b : bufs) b->release();
     if (P->h_small) cudaFreeHost(P->h_small);
     for (auto& e : P->ev)
@@ -1093,6 +1303,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     const int rb = rec_bytes(P->D, P->fp64), tb = P->fp64 ? 8 : 4;
 
     Carve cv{base};
+    CatGeom* geo = static_cast<CatGeom*>(cv.take(sizeof(CatGeom)));
     int* stencil = static_cast<int*>(cv.take(sizeof(int) * g.stencil.size()));
     int* cid = static_cast<int*>(cv.take(sizeof(int) * (n + 1)));
     int* perm = static_cast<int*>(cv.take(sizeof(int) * (n + 1)));
@@ -1116,6 +1327,8 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     double* partial = static_cast<double*>(cv.take(row_bytes * rows));
 
     CUDA_TRY(cudaMemcpyAsync(stencil, g.stencil.data(), sizeof(int) * g.stencil.size(), cudaMemcpyHostToDevice, s));
+    const CatGeom hgeo = make_geom(P->D, g.nc, P->box, 0, 0);
+    CUDA_TRY(cudaMemcpyAsync(geo, &hgeo, sizeof(CatGeom), cudaMemcpyHostToDevice, s));
     int* cell_count = cells;
     int* cell_start = cells + (nc + 1);
     int* cell_fill = cells + 2 * (nc + 1);
@@ -1140,12 +1353,9 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     cp.D = P->D;
     cp.n = n;
     cp.ncells = nc;
+    cp.ncat = 1;
+    cp.geo = geo;
     cp.periodic = P->opts.periodic;
-    for (int d = 0; d < 4; ++d) {
-        cp.nc[d] = g.nc[d];
-        cp.box[d] = P->box[d];
-        cp.inv_side[d] = g.nc[d] / P->box[d];
-    }
     cp.pos = pos;
     cp.w = w;
     cp.cid = cid;
@@ -1161,16 +1371,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     CUDA_TRY(launch_make_items(ib, cell_start, perm, nc, pb, pe, P->warps, s));
 
     PairParams pp = P->pp;
-    int stride = 1;
-    for (int d = 0; d < P->D; ++d) {
-        pp.nc[d] = g.nc[d];
-        pp.stride[d] = stride;
-        stride *= g.nc[d];
-        pp.box[d] = P->box[d];
-        pp.boxf[d] = (float)P->box[d];
-        pp.side[d] = P->box[d] / g.nc[d];
-        pp.sidef[d] = (float)pp.side[d];
-    }
+    pp.geo = geo;
     pp.nstencil = (int)g.stencil.size();
     pp.stencil = stencil;
     pp.rec = rec;

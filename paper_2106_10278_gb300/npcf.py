@@ -25,7 +25,8 @@ STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPC
 # every entry point declared in include/npcf.h
 EXPORTS = ("npcf_default_opts", "npcf_plan_create", "npcf_num_coeffs", "npcf_coeff_index", "npcf_compute",
            "npcf_compute_host", "npcf_device_status", "npcf_last_stats", "npcf_last_profile", "npcf_last_error",
-           "npcf_plan_destroy", "npcf_compute_noalloc", "npcf_last_counters", "npcf_backward")
+           "npcf_plan_destroy", "npcf_compute_noalloc", "npcf_last_counters", "npcf_backward",
+           "npcf_compute_batched")
 
 
 class NpcfError(RuntimeError):
@@ -77,6 +78,9 @@ def load_library(path: str = LIB_PATH):
         lib.npcf_last_profile.restype = i32
         lib.npcf_last_counters.argtypes = [P, ctypes.POINTER(i64), i32]
         lib.npcf_last_counters.restype = i32
+        lib.npcf_compute_batched.argtypes = [P, P, P, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double), i32, P,
+                                             P]
+        lib.npcf_compute_batched.restype = i32
         lib.npcf_backward.argtypes = [P, P, P, i64, P, i64, i64, P, P, P]
         lib.npcf_backward.restype = i32
         lib.npcf_last_error.argtypes = []
@@ -172,6 +176,36 @@ class Plan:
             _check(lib.npcf_compute(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(w.data_ptr()), n,
                                     ctypes.c_void_p(out.data_ptr()), pb, pe, ctypes.c_void_p(s.cuda_stream)))
         return torch.view_as_complex(out.view(-1, 2))
+
+    def compute_batched(self, pos, w, offsets, boxes, out=None, stream=None):
+        """Coefficients of several catalogues in one pass.
+
+        pos (n, D) and w (n) are the catalogues concatenated on the device;
+        offsets (ncat + 1) delimits them and boxes (ncat, D) gives each one's box.
+        Returns a complex128 tensor (ncat, ncoeff)."""
+        import torch
+        lib = load_library()
+        dt = self._dtype()
+        if not (pos.is_cuda and w.is_cuda):
+            raise ValueError("pos and w must be CUDA tensors")
+        if pos.dtype != dt or w.dtype != dt:
+            raise TypeError(f"pos and w must be {dt} for a {self.precision} plan")
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        ncat = len(off) - 1
+        bx = np.ascontiguousarray(np.broadcast_to(np.asarray(boxes, dtype=np.float64), (ncat, self.D)))
+        if pos.dim() != 2 or pos.shape[1] != self.D or w.shape != (pos.shape[0],) or off[-1] != pos.shape[0]:
+            raise ValueError("pos must be (n, D), w (n,) and offsets[-1] == n")
+        pos = pos.contiguous()
+        w = w.contiguous()
+        if out is None:
+            out = torch.empty(ncat * 2 * self.ncoeff, dtype=torch.float64, device=pos.device)
+        s = stream if stream is not None else torch.cuda.current_stream(pos.device)
+        with torch.cuda.device(pos.device):
+            _check(lib.npcf_compute_batched(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                            off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                            bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ncat,
+                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
+        return torch.view_as_complex(out.view(ncat, -1, 2))
 
     def backward(self, pos, w, grad_coeffs, primaries=None, stream=None, want_pos=True, want_w=True):
         """dL/dpos (n, D) and dL/dw (n) for device tensors, given dL/dcoeff.
