@@ -8,6 +8,13 @@ uniform randoms with weight -1, periodic box of side 1000, 10 radial bins
 over [20, 160], lmax = 5 (13,320 complex coefficients).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload d3n4|d3n3_fp64|d2n3|d2n4|d4n3|d4n3-grad|batch64] [--scale S]
+
+Other workloads: d4n3-grad times one gradient step of the D=4 3PCF (forward,
+chi^2 upstream gradient, backward: npcf_backward); batch64 times the 64
+catalogues of the batched workload through npcf_compute_batched (the 3PCF at
+lmax 10 and the 4PCF at lmax 4, one call each).  --scale < 1 shrinks a
+workload for profiling; --no-cpu-baseline / --no-e2e skip those legs.
 
 Under torchrun (N > 1) every rank runs its own catalogue (seed + rank):
 independent problems, no data-path collective ("scaling": "weak").
@@ -44,6 +51,9 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="d3n4")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -86,6 +96,15 @@ def coupling_terms_per_primary(D: int, N: int, lmax: int, nbins: int) -> int:
                         if abs(m1 + m2) <= l3:
                             t += 1
     return ntrip * t
+
+
+def adjoint_flops_per_pair(D: int, lmax: int) -> int:
+    """Algorithmic FP32 operations of one pair in the adjoint pair kernel: the
+    separation and direction, the harmonics carried as dual numbers (value and
+    D partials: every product costs 2D + 1 operations, every FMA with the
+    c-coefficients D + 1 FMAs), and the tangential projection."""
+    fwd = pair_flops_per_pair(D, lmax)
+    return 3 * D + 2 + D + (2 * D + 1) * fwd + 6 * D
 
 
 def count_pairs_numpy(pos, edges, box, primaries):
@@ -236,7 +255,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     base_seed = {"d3n4": 2, "d2n3": 1, "d2n4": 1, "d4n3": 4, "d3n3_fp64": 0}[args.workload]
-    wl = catalogs.workload(args.workload, seed=base_seed + 1000 * rank)
+    wl = catalogs.workload(args.workload, seed=base_seed + 1000 * rank, scale=args.scale)
     prec = "fp64" if wl.precision == "fp64" else "fp32"
     tdt = torch.float64 if prec == "fp64" else torch.float32
     plan = Plan(wl.D, wl.N, wl.lmax, wl.edges, wl.box, precision=prec, sync_check=False, timing=True)
@@ -306,19 +325,21 @@ def run_ours(args, rank, world):
                 "pair_kernel_ms": float(np.mean(pair_ms))}
 
     # end to end through the public host-buffer entry point (pinned inputs)
-    hp = torch.tensor(wl.pos, dtype=tdt).pin_memory()
-    hw = torch.tensor(wl.w, dtype=tdt).pin_memory()
-    plan.compute_host(hp.numpy(), hw.numpy())  # warm
-    e2e_t = []
-    for _ in range(max(2, min(args.steps, 5))):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        plan.compute_host(hp.numpy(), hw.numpy())
-        e2e_t.append(time.perf_counter() - t0)
-    e2e = {"value": world * pairs_per_step / float(np.mean(e2e_t)), "unit": "pairs/s",
-           "h2d_bytes_per_step": int(hp.numel() * hp.element_size() + hw.numel() * hw.element_size()),
-           "d2h_bytes_per_step": int(2 * plan.ncoeff * 8)}
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.tensor(wl.pos, dtype=tdt).pin_memory()
+        hw = torch.tensor(wl.w, dtype=tdt).pin_memory()
+        plan.compute_host(hp.numpy(), hw.numpy())  # warm
+        e2e_t = []
+        for _ in range(max(2, min(args.steps, 5))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.compute_host(hp.numpy(), hw.numpy())
+            e2e_t.append(time.perf_counter() - t0)
+        e2e = {"value": world * pairs_per_step / float(np.mean(e2e_t)), "unit": "pairs/s",
+               "h2d_bytes_per_step": int(hp.numel() * hp.element_size() + hw.numel() * hw.element_size()),
+               "d2h_bytes_per_step": int(2 * plan.ncoeff * 8)}
 
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -334,8 +355,189 @@ def run_ours(args, rank, world):
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "wall_s_timed_region": wall,
     }
-    if rank == 0 and world == 1:
+    if args.scale != 1.0:
+        line["config"]["scale"] = args.scale
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _timed(args, world, step, flush, stream, after=None):
+    """W untimed steps, then K steps each bracketed by CUDA events on `stream`
+    (L2 flushed before each, outside the events); clocks sampled meanwhile.
+    Returns (per-step ms, max over ranks of the summed seconds, wall s, clocks)."""
+    import torch
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        if after is not None:
+            after()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t = sum(ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt[0])
+    return ms, t, wall, clk
+
+
+def _alu_peak():
+    return SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+
+
+def run_batch64(args, rank, world):
+    """The batched workload: 64 catalogues (sizes log-uniform in [5e4, 5e5], periodic cubes of side
+    500-1000, half uniform and half lognormal-Poisson, 8 bins over [10, 120]); one step is the 3PCF at
+    lmax 10 and the 4PCF at lmax 4 of every catalogue, one npcf_compute_batched call each."""
+    import torch
+
+    from paper_2106_10278_gb300 import build as pbuild
+    from paper_2106_10278_gb300 import catalogs
+    from paper_2106_10278_gb300.npcf import Plan
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    bw = catalogs.batch64(ncat=max(1, int(round(64 * min(1.0, args.scale)))))
+    pos = torch.tensor(bw.pos, dtype=torch.float32, device=dev)
+    w = torch.tensor(bw.w, dtype=torch.float32, device=dev)
+    plans = [Plan(3, N, L, bw.edges, np.full(3, 1000.0), precision="fp32", sync_check=False, timing=True)
+             for N, L in ((3, 10), (4, 4))]
+    outs = [torch.empty(bw.ncat * 2 * p.ncoeff, dtype=torch.float64, device=dev) for p in plans]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    prof = []
+
+    def step():
+        for p, o in zip(plans, outs):
+            p.compute_batched(pos, w, bw.offsets, bw.boxes, out=o)
+
+    def after():  # stage times of the step just timed (each plan reports its last call)
+        prof.append([p.profile() for p in plans])
+
+    ms, t_max, wall, clk = _timed(args, world, step, flush, stream, after)
+    pairs = plans[0].stats()["pairs"]
+    prof = prof[-args.steps:]
+    pair_ms = [float(np.mean([pp[i]["pairs_ms"] for pp in prof])) for i in range(2)]
+    couple_ms = [float(np.mean([pp[i]["couple_ms"] for pp in prof])) for i in range(2)]
+    launches = sum(pp[i]["launches"] for pp in prof for i in range(2))
+    fpp = pair_flops_per_pair(3, 10)
+    achieved = fpp * pairs / (pair_ms[0] / 1e3) / 1e12
+    value = world * pairs * args.steps / t_max
+    line = {
+        "metric": "pairs/s, batched D=3 3PCF (lmax 10) + 4PCF (lmax 4) of 64 catalogues", "value": value,
+        "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch64: {bw.ncat} catalogues, n={len(bw.pos)}, boxes 500-1000, 8 bins over "
+                               "[10,120]; 3PCF lmax 10 and 4PCF lmax 4 (two batched calls, pairs counted once)",
+                   "pairs_per_step": pairs, "ncoeff": [p.ncoeff for p in plans],
+                   "l2": "256 MB buffer written before every timed step (outside the events)"},
+        "stages_ms": {"pairs_3pcf_l10": pair_ms[0], "couple_3pcf": couple_ms[0], "pairs_4pcf_l4": pair_ms[1],
+                      "couple_4pcf": couple_ms[1]},
+        "roofline": {"bound": "alu", "kernel": "k_pairs (lmax 10)", "achieved": achieved, "peak": _alu_peak(),
+                     "unit": "TFLOP/s", "frac": achieved / _alu_peak(), "traffic": None,
+                     "flops_per_pair": fpp, "pairs_per_launch": pairs, "pair_kernel_ms": pair_ms[0]},
+        "gpu_launches": launches, "clocks": clk, "wall_s_timed_region": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_grad(args, rank, world):
+    """One gradient step of the D=4 3PCF workload (n=100k in the unit 4-cube, 8 bins over [0.01, 0.12],
+    lmax 4, FP32): coefficients, the chi^2 upstream gradient 2 (zeta - t) against the seed-104 catalogue's
+    coefficients, and dL/dpos, dL/dw through npcf_backward."""
+    import torch
+
+    from paper_2106_10278_gb300 import build as pbuild
+    from paper_2106_10278_gb300 import catalogs
+    from paper_2106_10278_gb300.npcf import Plan
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    wl = catalogs.workload("d4n3", seed=4 + 1000 * rank, scale=args.scale)
+    tgt = catalogs.workload("d4n3", seed=104, scale=args.scale)
+    plan = Plan(4, 3, 4, wl.edges, wl.box, precision="fp32", sync_check=False, timing=True)
+    pos = torch.tensor(wl.pos, dtype=torch.float32, device=dev)
+    w = torch.tensor(wl.w, dtype=torch.float32, device=dev)
+    t = plan.compute(torch.tensor(tgt.pos, dtype=torch.float32, device=dev),
+                     torch.tensor(tgt.w, dtype=torch.float32, device=dev)).clone()
+    out = torch.empty(2 * plan.ncoeff, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = {}
+    bwd_ms, bwd_launches = [], []
+
+    def step():
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        z = plan.compute(pos, w, out=out)
+        g = torch.view_as_real(2.0 * (z - t)).reshape(-1)
+        a.record(stream)
+        plan.backward(pos, w, g)
+        b.record(stream)
+        ev["bwd"] = (a, b)
+
+    def after():
+        bwd_ms.append(ev["bwd"][0].elapsed_time(ev["bwd"][1]))
+        bwd_launches.append(plan.profile()["launches"])
+
+    ms, t_max, wall, clk = _timed(args, world, step, flush, stream, after)
+    torch.cuda.synchronize()
+    pairs = plan.stats()["pairs"]
+    plan.compute(pos, w, out=out)  # one more forward (untimed) for its stage times and launch count
+    fwd = plan.profile()
+    bwd_ms = float(np.mean(bwd_ms))
+    value = world * pairs * args.steps / t_max
+    line = {
+        "metric": "pairs/s, D=4 3PCF gradient step (forward + chi^2 + backward)", "value": value, "unit": "pairs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "d4n3-grad: D=4 3PCF, n=100k (50k uniform + 50k in 200 Gaussian blobs, sigma 0.01) "
+                               "in the periodic unit 4-cube, 8 bins over [0.01,0.12], lmax 4; chi^2 loss against "
+                               "the seed-104 catalogue", "n": wl.n, "pairs_per_step": pairs,
+                   "l2": "256 MB buffer written before every timed step (outside the events)"},
+        "stages_ms": {"forward_pairs": fwd["pairs_ms"], "forward_couple": fwd["couple_ms"], "backward": bwd_ms},
+        "roofline": {"bound": "alu", "kernel": "npcf_backward (cell list, pair recompute, adjoint kernels)",
+                     "achieved": adjoint_flops_per_pair(4, 4) * pairs / (bwd_ms / 1e3) / 1e12, "peak": _alu_peak(),
+                     "unit": "TFLOP/s", "traffic": None, "flops_per_pair": adjoint_flops_per_pair(4, 4),
+                     "note": "achieved counts the adjoint pair work only, over the whole backward call"},
+        "gpu_launches": args.steps * fwd["launches"] + sum(bwd_launches), "clocks": clk,
+        "wall_s_timed_region": wall,
+    }
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+    if args.scale != 1.0:
+        line["config"]["scale"] = args.scale
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -352,7 +554,12 @@ def main():
 
         torch.distributed.init_process_group("nccl")
     try:
-        run_ours(args, rank, world)
+        if args.workload == "batch64":
+            run_batch64(args, rank, world)
+        elif args.workload == "d4n3-grad":
+            run_grad(args, rank, world)
+        else:
+            run_ours(args, rank, world)
     finally:
         if world > 1:
             import torch
