@@ -269,6 +269,7 @@ def run_ours(args, rank, world):
         plan.compute(pos, w, out=out)
     torch.cuda.synchronize()
     st = plan.stats()
+    counters = plan.counters()
     pairs_per_step = st["pairs"]
     nprim = st["primaries"]
     cand_per_step = st["candidates"]
@@ -349,7 +350,7 @@ def run_ours(args, rank, world):
                    "primaries": nprim, "pairs_per_step": pairs_per_step, "candidates_per_step": cand_per_step,
                    "ncoeff": plan.ncoeff,
                    "l2": "256 MB buffer written before every timed step (outside the events)"},
-        "coeffs_per_s": coeffs_per_s, "coupling_terms_per_primary": terms,
+        "coeffs_per_s": coeffs_per_s, "coupling_terms_per_primary": terms, "pair_counters": counters,
         "stages_ms": {"cells": float(np.mean(cells_ms)), "pairs": float(np.mean(pair_ms)),
                       "couple": float(np.mean(couple_ms))},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -508,9 +509,13 @@ def run_grad(args, rank, world):
         b.record(stream)
         ev["bwd"] = (a, b)
 
+    bwd_stages = []
+
     def after():
         bwd_ms.append(ev["bwd"][0].elapsed_time(ev["bwd"][1]))
-        bwd_launches.append(plan.profile()["launches"])
+        pr = plan.profile()  # the backward call's stages
+        bwd_launches.append(pr["launches"])
+        bwd_stages.append([pr["cells_ms"], pr["pairs_ms"], pr["couple_ms"], pr["reduce_ms"]])
 
     ms, t_max, wall, clk = _timed(args, world, step, flush, stream, after)
     torch.cuda.synchronize()
@@ -527,7 +532,9 @@ def run_grad(args, rank, world):
                                "in the periodic unit 4-cube, 8 bins over [0.01,0.12], lmax 4; chi^2 loss against "
                                "the seed-104 catalogue", "n": wl.n, "pairs_per_step": pairs,
                    "l2": "256 MB buffer written before every timed step (outside the events)"},
-        "stages_ms": {"forward_pairs": fwd["pairs_ms"], "forward_couple": fwd["couple_ms"], "backward": bwd_ms},
+        "stages_ms": {"forward_pairs": fwd["pairs_ms"], "forward_couple": fwd["couple_ms"], "backward": bwd_ms,
+                      "backward_stages": dict(zip(("cells", "pair_recompute", "couple_adjoint", "pair_adjoint"),
+                                                  np.mean(bwd_stages, axis=0).tolist()))},
         "roofline": {"bound": "alu", "kernel": "npcf_backward (cell list, pair recompute, adjoint kernels)",
                      "achieved": adjoint_flops_per_pair(4, 4) * pairs / (bwd_ms / 1e3) / 1e12, "peak": _alu_peak(),
                      "unit": "TFLOP/s", "traffic": None, "flops_per_pair": adjoint_flops_per_pair(4, 4),

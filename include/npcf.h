@@ -175,11 +175,13 @@ NPCF_API npcf_status npcf_device_status(npcf_plan_t plan);
 NPCF_API npcf_status npcf_last_stats(npcf_plan_t plan, int64_t* pairs, int64_t* primaries, int64_t* candidates);
 
 /*
- * Stage timings and kernel count of the last npcf_compute (host, waits for its
+ * Stage timings and kernel count of the last npcf_compute or npcf_backward (host, waits for its
  * stream).  stage_ms (may be NULL) receives 4 values measured with CUDA events
  * on the compute stream when opts.timing = 1 (else -1): cell list + work items,
- * pair kernel, coupling kernel, final reduction.  launches (may be NULL)
- * receives the number of kernels the call launched.
+ * pair kernel, coupling kernel, final reduction; after npcf_backward: cell list +
+ * work items, the forward pair kernel (recomputing the a-array), the coupling
+ * adjoint, the pair adjoint + conversion.  launches (may be NULL) receives the
+ * number of kernels the call launched.
  */
 NPCF_API npcf_status npcf_last_profile(npcf_plan_t plan, double* stage_ms, int* launches);
 

@@ -12,6 +12,8 @@
 // coupling kernel (c_j, dL/dw_j) and one adjoint pair kernel (h and its
 // gradient by dual numbers through the same harmonic recurrences) suffice.
 // Per-particle gradients accumulate in FP64 (atomics) and are converted once.
+// The adjoint pair kernel compacts each warp's accepted pairs into a small ring
+// so that the (expensive) dual-number evaluation always runs on full warps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -235,6 +237,9 @@ struct AdjCoupleParams {
     double inv_V;
     void* cbuf;            // nprim x nbins x nq (T)
     double* gwp;           // nprim
+    int ncoeff;
+    int g_in_smem;         // the upstream gradient is copied to shared memory (as T)
+    int tables_off;        // byte offset of that copy
 };
 
 // the l of a real component and its multiplicity in sum_[l] a(b1) conj(a(b2))
@@ -268,6 +273,32 @@ __global__ void __launch_bounds__(256) k_couple_adjoint_n3(const AdjCoupleParams
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nb = p.nbins, nq = p.nq, L1 = p.lmax + 1;
     T* aw = reinterpret_cast<T*>(smem) + warp * nb * nq;
+    // per component: its l and multiplicity; per l: its contiguous component range [qs[l], qs[l+1])
+    int* s_lq = reinterpret_cast<int*>(smem + (size_t)nw * nb * nq * sizeof(T));
+    int* s_mult = s_lq + nq;
+    int* s_qs = s_mult + nq;
+    // loop-invariant tables: the first key of every ordered bin pair, and (when it fits) the
+    // upstream gradient in T
+    int* s_kb = s_qs + (L1 + 1);
+    T* s_g = reinterpret_cast<T*>(smem + p.tables_off);
+    for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) {
+        const int b = i / nb, b2 = i - (i / nb) * nb;
+        s_kb[i] = p.key_base[(b < b2 ? b : b2) * nb + (b < b2 ? b2 : b)];
+    }
+    if (p.g_in_smem)
+        for (int i = threadIdx.x; i < 2 * p.ncoeff; i += blockDim.x) s_g[i] = (T)p.g[i];
+    auto gat = [&](int i) -> T { return p.g_in_smem ? s_g[i] : (T)p.g[i]; };
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        int l, mult;
+        q_label<D>(q, &l, &mult);
+        s_lq[q] = l;
+        s_mult[q] = mult;
+    }
+    if (threadIdx.x <= L1) {
+        const int l = threadIdx.x;
+        s_qs[l] = D == 2 ? (l == 0 ? 0 : 2 * l - 1) : (D == 3 ? l * l : q_base_d4(l));
+    }
+    __syncthreads();
     const T* A = static_cast<const T*>(p.a);
     const T* pref = static_cast<const T*>(p.pref);
     const T* qnorm = static_cast<const T*>(p.qnorm);
@@ -276,36 +307,36 @@ __global__ void __launch_bounds__(256) k_couple_adjoint_n3(const AdjCoupleParams
     for (int64_t j = (int64_t)blockIdx.x * nw + warp; j < p.nprim; j += (int64_t)gridDim.x * nw) {
         for (int i = lane; i < nb * nq; i += 32) aw[i] = A[j * nb * nq + i];
         __syncwarp();
-        const double wj = (double)static_cast<const T*>(p.wprim)[j];
+        const T wj = static_cast<const T*>(p.wprim)[j];
         for (int i = lane; i < nb * nq; i += 32) {
             const int b = i / nq, q = i - (i / nq) * nq;
-            int l, mult;
-            q_label<D>(q, &l, &mult);
-            double G = 0.0;
+            const int l = s_lq[q];
+            T G = T(0);
             for (int b2 = 0; b2 < nb; ++b2) {
-                const int kb = p.key_base[(b < b2 ? b : b2) * nb + (b < b2 ? b2 : b)];
+                const int kb = s_kb[b * nb + b2];
                 if (kb < 0) continue;
-                const double gre = p.g[2 * (kb + l)], gim = p.g[2 * (kb + l) + 1];
+                const T gre = gat(2 * (kb + l));
                 if constexpr (D == 2) {
                     // zeta_l = a_l(b1) conj(a_l(b2)); this component is Re (q = 0 or odd) or Im (q even > 0)
+                    const T gim = gat(2 * (kb + l) + 1);
                     const bool is_im = q > 0 && (q & 1) == 0;
                     const int qr = is_im ? q - 1 : q;
-                    const double xr = aw[b2 * nq + qr];
-                    const double xi = l > 0 ? (double)aw[b2 * nq + qr + 1] : 0.0;
+                    const T xr = aw[b2 * nq + qr];
+                    const T xi = l > 0 ? aw[b2 * nq + qr + 1] : T(0);
                     if (b <= b2) G += is_im ? (gre * xi + gim * xr) : (gre * xr - gim * xi);  // b is b1
                     if (b >= b2) G += is_im ? (gre * xi - gim * xr) : (gre * xr + gim * xi);  // b is b2
                 } else {
-                    const double v = (double)aw[b2 * nq + q] * (b2 == b ? 2.0 : 1.0);
-                    G += gre * (double)pref[l] * mult * v;
+                    G = fma(gre, aw[b2 * nq + q] * (b2 == b ? T(2) : T(1)), G);
                 }
             }
-            cb[j * nb * nq + i] = (T)(G * wj * p.inv_V * (double)qnorm[q] * (double)ivb[b]);
+            if constexpr (D != 2) G *= pref[l] * T(s_mult[q]);
+            cb[j * nb * nq + i] = G * wj * T(p.inv_V) * qnorm[q] * ivb[b];
         }
         double s = 0.0;
         for (int i = lane; i < nb * nb * L1; i += 32) {
             const int l = i % L1, bb = i / L1, b1 = bb / nb, b2 = bb % nb;
             if (b1 > b2) continue;
-            const int kb = p.key_base[b1 * nb + b2];
+            const int kb = s_kb[b1 * nb + b2];
             if (kb < 0) continue;
             const int key = kb + l;
             if constexpr (D == 2) {
@@ -322,13 +353,9 @@ __global__ void __launch_bounds__(256) k_couple_adjoint_n3(const AdjCoupleParams
                 }
                 s += p.g[2 * key] * re + p.g[2 * key + 1] * im;
             } else {
-                double f = 0.0;
-                for (int q = 0; q < nq; ++q) {
-                    int lq, mult;
-                    q_label<D>(q, &lq, &mult);
-                    if (lq == l) f += mult * (double)aw[b1 * nq + q] * aw[b2 * nq + q];
-                }
-                s += p.g[2 * key] * (double)pref[l] * f;
+                T f = T(0);
+                for (int q = s_qs[l]; q < s_qs[l + 1]; ++q) f = fma(T(s_mult[q]) * aw[b1 * nq + q], aw[b2 * nq + q], f);
+                s += p.g[2 * key] * (double)(pref[l] * f);
             }
         }
 #pragma unroll
@@ -348,6 +375,9 @@ struct AdjPairExtra {
 };
 
 constexpr int kAdjThreads = 256;
+constexpr int kRing = 64;  // accepted pairs queued per warp (a power of two >= 64)
+
+__host__ __device__ inline int adjoint_ring_bytes(int D, int tbytes) { return kRing * ((D + 1) * tbytes + 8); }
 
 // same item, neighbour-cell and bin logic as the forward pair kernel; each
 // lane takes one candidate of the current cell at a time
@@ -371,6 +401,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
     int* ws = job_pre + kMaxJobs + 4;
     CatGeom* s_geo = reinterpret_cast<CatGeom*>(smem + kGeomOffset);
     T* crow = reinterpret_cast<T*>(smem + pair_fixed_bytes(sizeof(R), nthreads)) + warp * nbins * NQ;
+    // this warp's ring of accepted pairs: unit vectors, w/r, input index, c-row offset
+    unsigned char* rbase = smem + pair_fixed_bytes(sizeof(R), nthreads) +
+                           (nthreads / 32) * nbins * NQ * (int)sizeof(T) + warp * adjoint_ring_bytes(D, sizeof(T));
+    T* ring_u = reinterpret_cast<T*>(rbase);
+    T* ring_s = ring_u + D * kRing;
+    int* ring_k = reinterpret_cast<int*>(ring_s + kRing);
+    int* ring_b = ring_k + kRing;
+    const unsigned lt_mask = (1u << lane) - 1u;
 
     for (int i = threadIdx.x; i < kTab / 4; i += nthreads)
         reinterpret_cast<int*>(tab)[i] = reinterpret_cast<const int*>(p.tab)[i];
@@ -450,16 +488,37 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
         double gj[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) gj[d] = 0.0;
+        // accepted pairs go into a per-warp ring of kRing entries; every time 32 are queued
+        // all lanes evaluate one each, so the dual-number harmonics run on full warps
+        int head = 0, cnt = 0;  // warp-uniform
+        auto process = [&](int e) {
+            T u[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) u[d] = ring_u[d * kRing + e];
+            const T sc = ring_s[e];
+            const int korig = ring_k[e];
+            const Dual<T, D> h = adjoint_harmonics<D, LMAX, T>(crow + ring_b[e], u);
+            atomicAdd(&x.gw[korig], (double)h.v);
+            T ug = T(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) ug = fma(u[d], h.d[d], ug);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const double gd = (double)(sc * (h.d[d] - ug * u[d]));
+                atomicAdd(&x.gpos[(size_t)korig * D + d], gd);
+                gj[d] -= gd;
+            }
+        };
         for (int j = 0; j < njobs; ++j) {
             const int seg_a = job_a[j];
             const int seg_n = job_pre[j + 1] - job_pre[j];
             const int packed = job_pk[j];
             T xjs[D];
             if (!cell_geometry<D, T>(p, g, cc, packed, xj, xjs)) continue;
-            for (int c0 = 0; c0 < seg_n; c0 += 32) {
+            for (int c0 = 0; c0 < seg_n; c0 += 32) {  // warp-uniform trip count
                 const int k = c0 + lane;
-                if (k >= seg_n) break;
-                const R pk = ldg_rec(rec + seg_a, k);
+                const bool valid = k < seg_n;
+                const R pk = ldg_rec(rec + seg_a, valid ? k : 0);
                 T dx[D];
                 T r2 = T(0);
 #pragma unroll
@@ -469,27 +528,29 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
                     r2 = fma(dx[d], dx[d], r2);
                 }
                 bool fl = false, ex = false;
-                const int b = decide_bin<D, T>(p, g, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &fl, &ex);
-                if (b < 0) continue;
-                const T rinv = rsqrt_t(r2);
-                T u[D];
+                const int b = valid ? decide_bin<D, T>(p, g, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &fl, &ex) : -1;
+                const unsigned m = __ballot_sync(full, b >= 0);
+                if (b >= 0) {
+                    const int e = (head + cnt + __popc(m & lt_mask)) & (kRing - 1);
+                    const T rinv = rsqrt_t(r2);
 #pragma unroll
-                for (int d = 0; d < D; ++d) u[d] = dx[d] * rinv;
-                const Dual<T, D> h = adjoint_harmonics<D, LMAX, T>(crow + b * NQ, u);
-                const int korig = x.perm[seg_a + k];
-                atomicAdd(&x.gw[korig], (double)h.v);
-                T ug = T(0);
-#pragma unroll
-                for (int d = 0; d < D; ++d) ug = fma(u[d], h.d[d], ug);
-                const T sc = pk.w() * rinv;
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    const double gd = (double)(sc * (h.d[d] - ug * u[d]));
-                    atomicAdd(&x.gpos[(size_t)korig * D + d], gd);
-                    gj[d] -= gd;
+                    for (int d = 0; d < D; ++d) ring_u[d * kRing + e] = dx[d] * rinv;
+                    ring_s[e] = pk.w() * rinv;
+                    ring_k[e] = x.perm[seg_a + k];
+                    ring_b[e] = b * NQ;
+                }
+                cnt += __popc(m);
+                __syncwarp();
+                if (cnt >= 32) {
+                    process((head + lane) & (kRing - 1));
+                    head = (head + 32) & (kRing - 1);
+                    cnt -= 32;
+                    __syncwarp();
                 }
             }
         }
+        if (lane < cnt) process((head + lane) & (kRing - 1));
+        __syncwarp();
         const int jorig = x.perm[jslot];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
@@ -539,11 +600,11 @@ int adjoint_pair_smem(int D, int Lc, int fp64, int nbins)
 {
     const int tb = fp64 ? 8 : 4;
     const int rb = tb * 4 * (D <= 3 ? 1 : 2);
-    return pair_fixed_bytes(rb, kAdjThreads) + (kAdjThreads / 32) * nbins * num_q(D, Lc) * tb;
+    return pair_fixed_bytes(rb, kAdjThreads) + (kAdjThreads / 32) * (nbins * num_q(D, Lc) * tb + adjoint_ring_bytes(D, tb));
 }
 
 cudaError_t launch_couple_adjoint(int D, int fp64, int nbins, int nq, int lmax, int64_t nprim, const void* a,
-                                  const void* wprim, const double* g, const int* key_base, const void* pref,
+                                  const void* wprim, const double* g, int ncoeff, const int* key_base, const void* pref,
                                   const void* qnorm, const void* inv_vb, double inv_V, void* cbuf, double* gwp,
                                   int nsm, cudaStream_t s)
 {
@@ -551,8 +612,12 @@ cudaError_t launch_couple_adjoint(int D, int fp64, int nbins, int nq, int lmax, 
     AdjCoupleParams cp{nbins, nq, lmax, nprim, a, wprim, g, key_base, pref, qnorm, inv_vb, inv_V, cbuf, gwp};
     const int tb = fp64 ? 8 : 4;
     int warps = 8;  // one primary per warp; its a-row is staged in shared memory
-    while (warps > 1 && warps * nbins * nq * tb > 160 * 1024) --warps;
-    const int smem = warps * nbins * nq * tb;
+    while (warps > 1 && warps * nbins * nq * tb > 120 * 1024) --warps;
+    const int ints = 2 * nq + lmax + 2 + nbins * nbins;
+    cp.ncoeff = ncoeff;
+    cp.tables_off = ((warps * nbins * nq * tb + ints * (int)sizeof(int)) + 15) / 16 * 16;
+    cp.g_in_smem = 2 * ncoeff * tb <= 48 * 1024;
+    const int smem = cp.tables_off + (cp.g_in_smem ? 2 * ncoeff * tb : 0);
     const int grid = (int)std::min<int64_t>((nprim + warps - 1) / warps, 8 * (int64_t)nsm);
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern) {

@@ -159,7 +159,7 @@ int adjoint_compiled_lmax(int D, int lmax);
 int adjoint_pair_warps();
 int adjoint_pair_smem(int D, int Lc, int fp64, int nbins);
 cudaError_t launch_couple_adjoint(int D, int fp64, int nbins, int nq, int lmax, int64_t nprim, const void* a,
-                                  const void* wprim, const double* g, const int* key_base, const void* pref,
+                                  const void* wprim, const double* g, int ncoeff, const int* key_base, const void* pref,
                                   const void* qnorm, const void* inv_vb, double inv_V, void* cbuf, double* gwp,
                                   int nsm, cudaStream_t s);
 cudaError_t launch_pairs_adjoint(const PairParams& p, int fp64, int Lc, const void* cbuf, const double* gwp,

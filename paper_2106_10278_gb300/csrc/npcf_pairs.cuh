@@ -39,9 +39,10 @@ constexpr int kPool = 320;      // staged pairs per warp (shared by all bins)
 constexpr int kQCap = 192;      // entries of one bin's index queue
 
 // Shared-memory carve-up of one CTA (host and device must agree):
-//   2 candidate tiles of `threads` records | radial table + edges + lane map (kTab + 576)
-//   | per warp: [qcnt[32] ints | ftop + pad | fstack[kPool] u16 | binq[nbins][kQCap] u16 | pool]
-// where the pool region also holds the final cross-lane reduction scratch.
+//   radial table + edges + lane map | job lists + scan scratch | the item's CatGeom
+//   | per warp: [fstack[kPool] u16 | binq[nbins][kQCap] u16 | pool]
+// where the pool region also holds the final cross-lane reduction scratch.  Queue
+// lengths and the free-stack top live in registers (lane b keeps bin b's length).
 __host__ __device__ inline int pair_pool_bytes(int rec_bytes, int t_bytes, int nq_compiled)
 {
     const int pool = kPool * rec_bytes;
@@ -51,7 +52,7 @@ __host__ __device__ inline int pair_pool_bytes(int rec_bytes, int t_bytes, int n
 
 __host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int nbins, int nq_compiled)
 {
-    const int head = 128 + 16 + kPool * 2 + nbins * kQCap * 2;
+    const int head = kPool * 2 + nbins * kQCap * 2;
     return ((head + 15) / 16) * 16 + ((pair_pool_bytes(rec_bytes, t_bytes, nq_compiled) + 15) / 16) * 16;
 }
 
@@ -284,11 +285,9 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     CatGeom* s_geo = reinterpret_cast<CatGeom*>(smem + kGeomOffset);
     unsigned char* wbase = smem + pair_fixed_bytes(sizeof(R), nthreads) +
                            warp * pair_warp_bytes(sizeof(R), sizeof(T), nbins, NQ);
-    int* qcnt = reinterpret_cast<int*>(wbase);
-    int* ftop = reinterpret_cast<int*>(wbase + 128);
-    unsigned short* fstack = reinterpret_cast<unsigned short*>(wbase + 144);
+    unsigned short* fstack = reinterpret_cast<unsigned short*>(wbase);
     unsigned short* binq = fstack + kPool;
-    R* pool = reinterpret_cast<R*>(wbase + ((128 + 16 + kPool * 2 + nbins * kQCap * 2 + 15) / 16) * 16);
+    R* pool = reinterpret_cast<R*>(wbase + ((kPool * 2 + nbins * kQCap * 2 + 15) / 16) * 16);
     T* scratch = reinterpret_cast<T*>(pool);
 
     for (int i = threadIdx.x; i < kTab / 4; i += nthreads)
@@ -380,9 +379,9 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         T acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = T(0);
-        if (lane < nbins) qcnt[lane] = 0;
+        int qlen = 0;                   // lane b < nbins: length of bin b's queue
+        int ftop_r = kPool, tot_r = 0;  // warp-uniform: free-stack top, staged pairs
         for (int i = lane; i < kPool; i += 32) fstack[i] = (unsigned short)i;
-        if (lane == 0) *ftop = kPool;
         __syncwarp();
         unsigned npairs = 0;
         unsigned long long ncand = 0;
@@ -390,7 +389,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
 
         // one consumption round: every lane pops one staged pair of its own bin
         auto round = [&]() {
-            const int q = qcnt[mybin];
+            const int q = __shfl_sync(full, qlen, mybin);
             const bool has = myrank < q;
             ++nrounds;
             nbusy += has ? 1u : 0u;
@@ -401,20 +400,18 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                 accum_pair<D, LMAX, T>(acc, e);
             }
             const unsigned fm = __ballot_sync(full, has);
-            const int ft = *ftop;
-            __syncwarp();
-            if (has) fstack[ft + __popc(fm & lt_mask)] = (unsigned short)idx;
-            if (lane == 0) *ftop = ft + __popc(fm);
-            if (myrank == 0) qcnt[mybin] = q > mynl ? q - mynl : 0;
+            if (has) fstack[ftop_r + __popc(fm & lt_mask)] = (unsigned short)idx;
+            ftop_r += __popc(fm);
+            tot_r -= __popc(fm);
+            qlen = qlen > lane_nl ? qlen - lane_nl : 0;
             __syncwarp();
         };
         auto consume = [&](bool drain) {
             for (;;) {
-                const int qv = lane < nbins ? qcnt[lane] : 0;
-                const int busy = __reduce_add_sync(full, qv < lane_nl ? qv : lane_nl);
-                const int tot = __reduce_add_sync(full, qv);
+                const int tot = tot_r;
                 if (tot == 0) break;
-                const bool over = __any_sync(full, qv > kQCap - 32) || tot > kPool - 32;
+                const int busy = __reduce_add_sync(full, qlen < lane_nl ? qlen : lane_nl);
+                const bool over = __any_sync(full, qlen > kQCap - 32) || tot > kPool - 32;
                 const bool want = busy >= p.busy_round || tot >= p.tot_round;
                 if (!drain && !want && !over) break;
                 if (!drain && !want) ++nforced;
@@ -461,18 +458,17 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                     const unsigned tm = __ballot_sync(full, take);
                     if (tm == 0u) continue;
                     // lanes staging into the same bin: AND of the ballots of the bin's bits
-                    unsigned peers = tm;
+                    unsigned peers = tm, mine = tm;  // mine: lanes staging into bin `lane`
 #pragma unroll
                     for (int kb = 0; kb < 5; ++kb) {
                         const unsigned bk = __ballot_sync(full, (bin >> kb) & 1);
                         peers &= ((bin >> kb) & 1) ? bk : ~bk;
+                        mine &= ((lane >> kb) & 1) ? bk : ~bk;
                     }
                     const int rank = __popc(peers & lt_mask);
-                    const int base = take ? qcnt[bin] : 0;
-                    const int ft = *ftop;
-                    __syncwarp();
+                    const int base = __shfl_sync(full, qlen, take ? bin : 0);
                     if (take) {
-                        const int slot = fstack[ft - 1 - __popc(tm & lt_mask)];
+                        const int slot = fstack[ftop_r - 1 - __popc(tm & lt_mask)];
                         R e;
                         T* f = reinterpret_cast<T*>(e.v);
                         const T rinv = rsqrt_t(r2);
@@ -481,10 +477,11 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                         f[D] = pk.w();
                         pool[slot] = e;
                         binq[bin * kQCap + base + rank] = (unsigned short)slot;
-                        if (rank == 0) qcnt[bin] = base + __popc(peers);
                         ++npairs;
                     }
-                    if (lane == 0) *ftop = ft - __popc(tm);
+                    if (lane < nbins) qlen += __popc(mine);
+                    ftop_r -= __popc(tm);
+                    tot_r += __popc(tm);
                     __syncwarp();
                     consume(false);
                 }

@@ -829,15 +829,17 @@ npcf_status run_backward(npcf_plan_s* P, const void* pos, const void* w, int64_t
     }
     PairStage ps;
     if ((st = run_pairs(P, single_view(P), pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
-    P->timed = 0;
+    // stage times: cell list, forward pair recompute (both from run_pairs), coupling adjoint, pair adjoint
     double* gpos = P->w_gpos.as<double>();
     double* gw = P->w_gw.as<double>();
     CUDA_TRY(cudaMemsetAsync(gpos, 0, sizeof(double) * P->D * n1, s));
     CUDA_TRY(cudaMemsetAsync(gw, 0, sizeof(double) * n1, s));
     cudaError_t e = launch_couple_adjoint(P->D, P->fp64, P->nbins, P->nq, P->lmax, nprim, P->w_a.p, P->w_wprim.p, g,
+                                          (int)P->ncoeff,
                                           P->d_keybase.as<int>(), P->d_pref.p, P->d_qnorm.p, P->d_invvb.p,
                                           1.0 / P->V, P->w_cbuf.p, P->w_gwp.as<double>(), P->nsm, s);
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling adjoint launch: %s", cudaGetErrorString(e));
+    if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[3], s));
     // work items of adjoint_pair_warps() primaries (the a-array index of a primary does not depend on it)
     CUDA_TRY(launch_make_items(ps.ib, ps.pp.cell_start, P->w_perm.as<int>(), P->ncells, pb, pe,
                                adjoint_pair_warps(), s));
@@ -845,6 +847,10 @@ npcf_status run_backward(npcf_plan_s* P, const void* pos, const void* w, int64_t
                              P->nsm, s);
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "pair adjoint launch: %s", cudaGetErrorString(e));
     CUDA_TRY(launch_finalize_grads(n, P->D, P->fp64, gpos, gw, grad_pos, grad_w, s));
+    if (P->opts.timing) {
+        CUDA_TRY(cudaEventRecord(P->ev[4], s));
+        P->timed = 1;
+    }
     P->last_launches = launch_counter();
     CUDA_TRY(cudaMemcpyAsync(P->h_small, ps.small, 16, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(P->h_stats, ps.stats, 64, cudaMemcpyDeviceToHost, s));
