@@ -35,7 +35,7 @@ struct PairCfg {
     static constexpr int kThreads = (sizeof(T) == 4) ? (NQ <= 64 ? 512 : 256) : (NQ <= 40 ? 256 : 128);
 };
 
-constexpr int kPool = 320;      // staged pairs per warp (shared by all bins)
+constexpr int kPool = 416;      // staged pairs per warp (shared by all bins)
 constexpr int kQCap = 192;      // entries of one bin's index queue
 
 // Shared-memory carve-up of one CTA (host and device must agree):
@@ -56,7 +56,7 @@ __host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int n
     return ((head + 15) / 16) * 16 + ((pair_pool_bytes(rec_bytes, t_bytes, nq_compiled) + 15) / 16) * 16;
 }
 
-constexpr int kMaxJobs = 1024;  // neighbour cells of one item (the host keeps stencils this small)
+constexpr int kMaxJobs = 640;   // neighbour cells of one item (the largest stencil used: 613 cells, D=3 c=4)
 
 // fixed part: radial table | edges + lane map (576) | job lists + scan scratch | the item's CatGeom
 constexpr int kGeomOffset = kTab + 576 + (3 * kMaxJobs + 4 + 72) * 4;
