@@ -105,7 +105,7 @@ __device__ __forceinline__ void couple_item(const Cx<T>* Ap, int b1, int b2, int
 }
 
 template <int LMAX, typename T>
-__global__ void __launch_bounds__(512) k_couple_d3n4(const CoupleParams p)
+__global__ void __launch_bounds__(320, 2) k_couple_d3n4(const CoupleParams p)
 {
     constexpr int S = (LMAX + 1) * (LMAX + 1);
     constexpr int NC = (LMAX + 1) * (LMAX + 1);
@@ -197,6 +197,10 @@ cudaError_t launch_t(const CoupleParams& p, int grid, int threads, int smem, cud
     auto kern = k_couple_d3n4<LMAX, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    // prefer the largest shared-memory carveout: two CTAs per SM fit (registers and shared
+    // memory) and hide each other's per-group barriers; the default leaves room for one
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     kern<<<dim3(grid, p.nkb, p.ncat > 1 ? p.ncat : 1), threads, smem, s>>>(p); ++launch_counter();
     return cudaGetLastError();
 }
@@ -213,7 +217,8 @@ int couple_d3n4_smem(const CoupleParams& p, int fp64)
 int couple_d3n4_threads(int max_block_pairs)
 {
     const int ntask = (max_block_pairs + 3) / 4;
-    return 32 * (ntask < 16 ? (ntask < 1 ? 1 : ntask) : 16);
+    // at most 10 warps: with __launch_bounds__(320, 2) two CTAs share an SM (warps loop over the tasks)
+    return 32 * (ntask < 10 ? (ntask < 1 ? 1 : ntask) : 10);
 }
 
 cudaError_t launch_couple_d3n4(const CoupleParams& p, int fp64, int grid, int threads, int smem, cudaStream_t s)
