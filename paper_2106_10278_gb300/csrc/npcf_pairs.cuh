@@ -35,24 +35,26 @@ struct PairCfg {
     static constexpr int kThreads = (sizeof(T) == 4) ? (NQ <= 64 ? 512 : 256) : (NQ <= 40 ? 256 : 128);
 };
 
-constexpr int kPool = 416;      // staged pairs per warp (shared by all bins)
+// staged pairs per warp (shared by all bins): 416 16-byte records (D <= 3, FP32) keep the
+// CTA within the 196 KB shared-memory carveout; larger records get 320
+__host__ __device__ constexpr int pool_slots(int rec_bytes) { return rec_bytes <= 16 ? 416 : 320; }
 constexpr int kQCap = 192;      // entries of one bin's index queue
 
 // Shared-memory carve-up of one CTA (host and device must agree):
 //   radial table + edges + lane map | job lists + scan scratch | the item's CatGeom
-//   | per warp: [fstack[kPool] u16 | binq[nbins][kQCap] u16 | pool]
+//   | per warp: [fstack[slots] u16 | binq[nbins][kQCap] u16 | pool of `slots` records]
 // where the pool region also holds the final cross-lane reduction scratch.  Queue
 // lengths and the free-stack top live in registers (lane b keeps bin b's length).
 __host__ __device__ inline int pair_pool_bytes(int rec_bytes, int t_bytes, int nq_compiled)
 {
-    const int pool = kPool * rec_bytes;
+    const int pool = pool_slots(rec_bytes) * rec_bytes;
     const int scratch = 32 * (nq_compiled + 1) * t_bytes;
     return pool > scratch ? pool : scratch;
 }
 
 __host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int nbins, int nq_compiled)
 {
-    const int head = kPool * 2 + nbins * kQCap * 2;
+    const int head = pool_slots(rec_bytes) * 2 + nbins * kQCap * 2;
     return ((head + 15) / 16) * 16 + ((pair_pool_bytes(rec_bytes, t_bytes, nq_compiled) + 15) / 16) * 16;
 }
 
@@ -165,8 +167,10 @@ __device__ __forceinline__ int decide_bin(const PairParams& p, const CatGeom& g,
     if (kFP32 && (code & 64)) {
         *flagged = true;
         const float r = (float)r2 * rsqrtf((float)r2);
-        int bb = 0;
+        // bb = number of edges <= r, walked from the bucket's own count (0-1 steps)
+        int bb = (code & 63) == 63 ? (r >= s_edge[p.nbins >> 1] ? p.nbins + 1 : 0) : (code & 63) + 1;
         while (bb <= p.nbins && r >= s_edge[bb]) ++bb;
+        while (bb > 0 && r < s_edge[bb - 1]) --bb;
         b = (bb >= 1 && bb <= p.nbins) ? bb - 1 : -1;
         exact = (bb >= 1 && r - s_edge[bb - 1] < p.tol) || (bb <= p.nbins && s_edge[bb] - r < p.tol);
     }
@@ -266,6 +270,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     using R = Rec<D, T>;
     constexpr int NQ = PairCfg<D, LMAX, T>::NQ;
     constexpr bool kFP32 = sizeof(T) == 4;
+    constexpr int kPool = pool_slots((int)sizeof(R));
     const unsigned full = 0xffffffffu;
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                            warp * pair_warp_bytes(sizeof(R), sizeof(T), nbins, NQ);
     unsigned short* fstack = reinterpret_cast<unsigned short*>(wbase);
     unsigned short* binq = fstack + kPool;
-    R* pool = reinterpret_cast<R*>(wbase + ((kPool * 2 + nbins * kQCap * 2 + 15) / 16) * 16);
+    R* pool = reinterpret_cast<R*>(wbase + ((kPool * 2 + nbins * kQCap * 2 + 15) / 16) * 16);  // as pair_warp_bytes
     T* scratch = reinterpret_cast<T*>(pool);
 
     for (int i = threadIdx.x; i < kTab / 4; i += nthreads)
