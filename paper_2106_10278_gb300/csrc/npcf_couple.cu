@@ -18,6 +18,8 @@
 //   N=4, D=3: in npcf_couple_d3n4.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "npcf_device.cuh"
 #include "npcf_internal.h"
 
@@ -174,6 +176,85 @@ __global__ void __launch_bounds__(kCoupleThreads) k_couple(const CoupleParams p)
     }
 }
 
+// --------------------------------------------------- D=2, N=4, FP32, registers
+// A thread owns one item (bin pair b1 < b2, label pair (l1, l2)) and keeps the
+// complex sums for every b3 > b2 in registers while it walks a group of G
+// primaries held in shared memory:
+//     acc[b3] += w u_{l1}(b1) u_{l2}(b2) u_{l3}(b3),   l3 = -(l1 + l2),
+// then adds them once into the CTA's FP64 partial row.  Shared memory is read,
+// never written, inside the group, so the terms cost FMAs and broadcast loads.
+template <int NB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_couple_d2n4_reg(const CoupleParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nb = p.nbins, L = p.lmax, S = 2 * p.lmax + 1, G = p.group;
+    float2* A = reinterpret_cast<float2*>(smem);                  // [G][nb][S], signed l
+    float* W = reinterpret_cast<float*>(A + (size_t)G * nb * S);  // [G]
+    const int cat = blockIdx.z;
+    const int nprim = p.cat_count ? p.cat_count[cat] : *p.nprim;
+    const size_t first = p.cat_first ? (size_t)p.cat_first[cat] : 0;
+    const int stride = nb * p.nq;
+    const float* aglob = static_cast<const float*>(p.a) + first * stride;
+    const float* wglob = static_cast<const float*>(p.wprim) + first;
+    double* prow = p.partial + ((size_t)cat * gridDim.x + blockIdx.x) * 2 * p.ncoeff;
+    const int npair = p.kblocks[0].y - p.kblocks[0].x;
+    const int nitems = npair * p.nlam;
+    const int ngroup = (nprim + G - 1) / G;
+    for (int gi = blockIdx.x; gi < ngroup; gi += gridDim.x) {
+        const int g0 = gi * G, gn = min(G, nprim - g0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < G * nb * S; i += blockDim.x) {
+            const int g = i / (nb * S), r = i - g * (nb * S), b = r / S, l = r - b * S - L;
+            float re = 0.f, im = 0.f;
+            if (g < gn) {
+                const int al = l < 0 ? -l : l;
+                const float* ap = aglob + (size_t)(g0 + g) * stride + b * p.nq + q_index_d2(al);
+                re = ap[0];
+                im = al > 0 ? (l < 0 ? -ap[1] : ap[1]) : 0.f;  // a_{-l} = conj(a_l)
+            }
+            A[i] = make_float2(re, im);
+        }
+        for (int g = threadIdx.x; g < G; g += blockDim.x) W[g] = g < gn ? wglob[g0 + g] : 0.f;
+        __syncthreads();
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int pr = it / p.nlam, il = it - (it / p.nlam) * p.nlam;
+            const int2 bb = p.pairs[p.kblocks[0].x + pr];
+            const int2 ll = p.lam2[il];
+            const int l3 = -(ll.x + ll.y);
+            const int nk = nb - bb.y - 1;
+            float ar[NB], ai[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) ar[k] = ai[k] = 0.f;
+            const float2* ub = A + bb.x * S + ll.x + L;
+            const float2* vb = A + bb.y * S + ll.y + L;
+            const float2* xb = A + (bb.y + 1) * S + l3 + L;
+            for (int g = 0; g < gn; ++g) {
+                const float w = W[g];
+                const float2 u = ub[g * nb * S], v = vb[g * nb * S];
+                const float tr = w * fmaf(u.x, v.x, -u.y * v.y), ti = w * fmaf(u.x, v.y, u.y * v.x);
+                const float2* x = xb + g * nb * S;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    if (k < nk) {
+                        const float2 xx = x[k * S];
+                        ar[k] = fmaf(tr, xx.x, fmaf(-ti, xx.y, ar[k]));
+                        ai[k] = fmaf(tr, xx.y, fmaf(ti, xx.x, ai[k]));
+                    }
+                }
+            }
+            const int key0 = p.pair_key[p.kblocks[0].x + pr] + il;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                if (k < nk) {
+                    double* d = prow + 2 * (key0 + k * p.nlam);
+                    d[0] += (double)ar[k];
+                    d[1] += (double)ai[k];
+                }
+            }
+        }
+    }
+}
+
 template <int MODE, int D, int LMAX, typename T>
 cudaError_t launch_t(const CoupleParams& p, int grid, int smem, cudaStream_t s)
 {
@@ -188,9 +269,20 @@ cudaError_t launch_t(const CoupleParams& p, int grid, int smem, cudaStream_t s)
 
 int couple_max_lmax_d3n4() { return 5; }
 
+// primaries per shared-memory group of the FP32 D=2 N=4 kernel (at most 64, within ~200 KB)
+int d2n4_group(int nbins, int lmax)
+{
+    const int per = nbins * (2 * lmax + 1) * 8 + 4;
+    return std::max(1, std::min(64, (200 * 1024) / per));
+}
+
 int couple_smem(const CoupleParams& p, int fp64)
 {
     if (p.N == 4 && p.D == 3) return couple_d3n4_smem(p, fp64);
+    if (p.N == 4 && p.D == 2 && !fp64) {
+        const int G = d2n4_group(p.nbins, p.lmax);
+        return G * p.nbins * (2 * p.lmax + 1) * 8 + G * 4;
+    }
     const int tb = fp64 ? 8 : 4;
     int a_elems;
     int comps;
@@ -218,8 +310,19 @@ cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, c
         }
     }
     if (p.D == 2) {
-        return fp64 ? launch_t<MODE_D2N4, 2, 0, double>(p, grid, smem, s)
-                    : launch_t<MODE_D2N4, 2, 0, float>(p, grid, smem, s);
+        if (fp64) return launch_t<MODE_D2N4, 2, 0, double>(p, grid, smem, s);
+        const int nbmax = p.nbins - 2;  // b3 values per bin pair
+        auto go = [&](auto kern, int threads) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            kern<<<dim3(grid, 1, p.ncat > 1 ? p.ncat : 1), threads, smem, s>>>(p);
+            ++launch_counter();
+            return cudaGetLastError();
+        };
+        // one CTA per SM (its group of a-rows fills shared memory): as many warps as registers allow
+        if (nbmax <= 8) return go(k_couple_d2n4_reg<8, 512>, 512);
+        if (nbmax <= 16) return go(k_couple_d2n4_reg<16, 512>, 512);
+        return go(k_couple_d2n4_reg<32, 256>, 256);
     }
     return launch_couple_d3n4(p, fp64, grid, couple_d3n4_threads(p.max_block_pairs), smem, s);
 }

@@ -112,6 +112,7 @@ struct CoupleParams {
     const int2* lam2;          // D=2, N=4: (l1, l2) per Lambda index
     const signed char* lam_odd;// D=3, N=4: 1 if l1+l2+l3 is odd (coefficient imaginary)
     const void* pref;          // N=3: per-l factor of the zero coupling (T)
+    int group;                 // D=2 N=4 FP32: primaries per shared-memory group
     int ncat;                  // catalogues (blockIdx.z); 0 or 1 for a single one
     const int* cat_first;      // ncat: first primary of each catalogue in the a-array (NULL: one catalogue)
     const int* cat_count;      // ncat: its primaries
@@ -149,6 +150,7 @@ int pair_kernel_smem(int D, int fp64, int nbins, int warps, int nq);
 int pair_kernel_compiled_lmax(int D, int fp64, int lmax);
 cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
 int couple_smem(const CoupleParams& p, int fp64);
+int d2n4_group(int nbins, int lmax);
 cudaError_t launch_reduce(const double* partial, int rows, int ncols, double scale, double* out, cudaStream_t s);
 // per catalogue c: out[c][k] = scales[c] * sum_r partial[c][r][k]
 cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, int ncat, const double* scales, double* out,

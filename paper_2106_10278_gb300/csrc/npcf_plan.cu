@@ -449,6 +449,10 @@ npcf_status ensure_device(npcf_plan_s* P)
     return NPCF_OK;
 }
 
+// The FP32 D=2 4PCF coupling accumulates in registers over groups of primaries
+// (one CTA per SM: its group of a-rows fills shared memory).
+bool d2n4_registers(const npcf_plan_s* P) { return P->N == 4 && P->D == 2 && !P->fp64; }
+
 npcf_status setup_tables(npcf_plan_s* P)
 {
     const int D = P->D, nb = P->nbins;
@@ -567,7 +571,13 @@ npcf_status setup_tables(npcf_plan_s* P)
     const int base = couple_smem(cp, P->fp64);
     const int comps = (P->N == 3 && D != 2) || (P->N == 4 && D == 3) ? 1 : 2;
     const int budget = std::min(P->smem_optin, 160 * 1024) - base;
-    build_key_blocks(P, std::max(1, budget / (comps * tb)));
+    if (d2n4_registers(P)) {
+        // the register kernel walks every (bin pair, label) item itself: one block of all keys
+        if (base > P->smem_optin) return fail(NPCF_ERR_UNSUPPORTED, "D=2 4PCF coupling needs %d bytes of shared memory", base);
+        build_key_blocks(P, (int)P->ncoeff);
+    } else {
+        build_key_blocks(P, std::max(1, budget / (comps * tb)));
+    }
     CUDA_TRY(upload(P->d_pairs, P->pairs));
     CUDA_TRY(upload(P->d_pair_key, P->pair_key));
     CUDA_TRY(upload(P->d_kblocks, P->kblocks));
@@ -663,6 +673,7 @@ CoupleParams couple_params(const npcf_plan_s* P, const void* a, const void* wpri
     kp.lam2 = P->d_lam2.as<int2>();
     kp.lam_odd = P->d_lamodd.as<signed char>();
     kp.pref = P->d_pref.p;
+    kp.group = d2n4_group(P->nbins, P->lmax);
     kp.ncat = 1;
     return kp;
 }
@@ -770,6 +781,7 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     const int chunk = 128;
     const int nkb = (int)P->kblocks.size();
     int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
+    if (d2n4_registers(P)) rows = P->nsm;
     rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim_max + chunk - 1) / chunk));
     if ((st = reserve_workspace(P, n, nprim_max, rows, P->ncells)) != NPCF_OK) return st;
     PairStage ps;
@@ -1417,6 +1429,8 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     kp.lam2 = P->d_lam2.as<int2>();
     kp.lam_odd = P->d_lamodd.as<signed char>();
     kp.pref = P->d_pref.p;
+    kp.group = d2n4_group(P->nbins, P->lmax);
+    kp.ncat = 1;
     CUDA_TRY(cudaMemsetAsync(partial, 0, row_bytes * rows, s));
     e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
