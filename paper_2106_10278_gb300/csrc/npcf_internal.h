@@ -10,18 +10,6 @@ namespace npcf {
 constexpr int kMaxBins = 32;   // lanes own bins in the pair kernel: at most one warp's worth
 constexpr int kMaxD = 4;
 constexpr int kTab = 4096;     // radial lookup-table entries
-constexpr int kStageCap = 64;  // staged pairs per (warp, bin) in the pair kernel
-
-// Number of real components of a^b per bin for dimension D and lmax, in the
-// order the pair kernel writes them (see pair_layout in npcf_device.cuh).
-inline int num_real_components(int D, int lmax)
-{
-    if (D == 2) return 2 * lmax + 1;
-    if (D == 3) return (lmax + 1) * (lmax + 1);
-    int s = 0;  // D == 4: sum_{l3 <= lmax} (l3 + 1)^2
-    for (int l = 0; l <= lmax; ++l) s += (l + 1) * (l + 1);
-    return s;
-}
 
 // ------------------------------------------------------- catalogue geometry
 // The cell grid of one catalogue.  A call covers one or more catalogues; their
@@ -145,9 +133,6 @@ struct ItemBuffers {
 };
 cudaError_t launch_make_items(const ItemBuffers& b, const int* cell_start, const int* perm, int ncells, int64_t pb,
                               int64_t pe, int warps, cudaStream_t s);
-cudaError_t launch_pairs(const PairParams& p, int fp64, int grid, int smem, cudaStream_t s);
-int pair_kernel_smem(int D, int fp64, int nbins, int warps, int nq);
-int pair_kernel_compiled_lmax(int D, int fp64, int lmax);
 cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
 int couple_smem(const CoupleParams& p, int fp64);
 int d2n4_group(int nbins, int lmax);

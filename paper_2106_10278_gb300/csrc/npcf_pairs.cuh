@@ -88,15 +88,6 @@ __device__ __forceinline__ void accum_pair(T* acc, const Rec<D, T>& e)
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
-{
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Exclusive block-wide scan of two ints per thread (deterministic), totals
 // returned to every thread.  `ws` holds 2 * 32 ints of shared scratch.
 __device__ __forceinline__ void block_scan2(int a, int b, int* ea, int* eb, int* ta, int* tb, int* ws)
@@ -241,27 +232,6 @@ __device__ __forceinline__ Rec<D, T> ldg_rec(const Rec<D, T>* src, int i)
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) u.f[c] = __ldg(s + c);
     return u.r;
-}
-
-template <int D, typename T>
-__device__ __forceinline__ void prefetch_records(Rec<D, T>* dst, const Rec<D, T>* rec, const int* job_a,
-                                                 const int* job_pre, int njobs, int T0, int tn)
-{
-    constexpr int kChunks = sizeof(Rec<D, T>) / 16;
-    if ((int)threadIdx.x < tn) {
-        const int v = T0 + threadIdx.x;
-        int lo = 0, hi = njobs;  // job j with job_pre[j] <= v < job_pre[j+1]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (job_pre[mid] <= v) lo = mid;
-            else hi = mid;
-        }
-        const Rec<D, T>* src = rec + job_a[lo] + (v - job_pre[lo]);
-#pragma unroll
-        for (int c = 0; c < kChunks; ++c)
-            cp_async16(reinterpret_cast<char*>(dst + threadIdx.x) + 16 * c, reinterpret_cast<const char*>(src) + 16 * c);
-    }
-    cp_async_commit();
 }
 
 template <int D, int LMAX, typename T>
