@@ -970,8 +970,16 @@ npcf_status run_batched(npcf_plan_s* P, const void* pos, const void* w, const in
     for (int i = 0; i < ncat; ++i) nmax = std::max<int64_t>(nmax, offsets[i + 1] - offsets[i]);
     const int chunk = 128;
     const int nkb = (int)P->kblocks.size();
-    int rows = std::max(1, (2 * P->nsm + nkb * ncat - 1) / (nkb * ncat));
-    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nmax + chunk - 1) / chunk));
+    // rows per catalogue: enough that the largest catalogue's row carries about the average CTA
+    // load of 2 CTAs per SM (catalogues with fewer chunks than rows leave CTAs that exit at
+    // once, and the hardware scheduler balances the rest), bounded by the partial-row memory
+    const int64_t max_chunks = (nmax + chunk - 1) / chunk;
+    const int64_t tot_chunks = std::max<int64_t>(1, (n + chunk - 1) / chunk);
+    int64_t r64 = std::max<int64_t>((2 * P->nsm + nkb * ncat - 1) / (nkb * ncat),
+                                    (max_chunks * 2 * P->nsm + tot_chunks - 1) / tot_chunks);
+    const int64_t row_bytes = (int64_t)sizeof(double) * 2 * P->ncoeff * ncat;
+    r64 = std::min<int64_t>(r64, std::max<int64_t>(1, (int64_t(512) << 20) / std::max<int64_t>(row_bytes, 1)));
+    int rows = (int)std::min<int64_t>(r64, std::max<int64_t>(1, max_chunks));
     if ((st = reserve_workspace(P, n, n, rows * ncat, P->b_ncells)) != NPCF_OK) return st;
     GridView gv;
     gv.ncells = P->b_ncells;
