@@ -95,4 +95,16 @@ def test_null_arguments(lib):
     assert lib.npcf_plan_create(None, 3, 3, 2, None, 1, None, None) == -1
     assert lib.npcf_num_coeffs(None, None) == -1
     assert lib.npcf_compute(None, None, None, 0, None, 0, 0, None) == -1
+    assert lib.npcf_compute_host(None, None, None, 0, None, 0, 0, None) == -1
+    assert lib.npcf_compute_noalloc(None, None, None, 0, None, 0, 0, None) == -1
+    off = (ctypes.c_int64 * 2)(0, 0)
+    box = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    assert lib.npcf_compute_batched(None, None, None, off, box, 1, None, None) == -1
+    assert lib.npcf_backward(None, None, None, 0, None, 0, 0, None, None, None) == -1
+    assert lib.npcf_coeff_index(None, 0, None, None) == -1
+    assert lib.npcf_device_status(None) == -1
+    assert lib.npcf_last_stats(None, None, None, None) == -1
+    assert lib.npcf_last_profile(None, None, None) == -1
+    assert lib.npcf_last_counters(None, None, 0) == -1
+    assert b"NULL" in lib.npcf_last_error()
     lib.npcf_plan_destroy(None)  # a no-op
