@@ -119,14 +119,16 @@ def ferrers_half(L: int, k: int, theta: float) -> float:
 
 
 def keys(D: int, N: int, lmax: int, nbins: int, bin_lt: bool = False) -> np.ndarray:
-    """Output keys (b1, b2, b3, l1, l2, l3) in the oracle's order; unused bins are -1."""
+    """Output keys in the oracle's order: (b1, b2, b3, l1, l2, l3) for N <= 4 (unused bins -1,
+    unused ells 0); (b1, b2, b3, b4, l1, l2, l12, l3, l4) for N = 5."""
     lib = _load()
     nk = lib.npcf_oracle_nkeys(D, N, lmax, nbins, int(bin_lt))
     if nk < 0:
         raise ValueError(f"unsupported (D={D}, N={N}, lmax={lmax}, nbins={nbins})")
-    out = np.zeros((nk, 6), dtype=np.int32)
+    out = np.zeros((max(nk, 1), 9), dtype=np.int32)
     lib.npcf_oracle_keys(D, N, lmax, nbins, int(bin_lt), _ip(out))
-    return out
+    out = out[:nk]
+    return out if N == 5 else out[:, [0, 1, 2, 4, 5, 6]].copy()
 
 
 def coupling_terms(D: int, N: int, lmax: int, lam_index: int):
@@ -135,10 +137,10 @@ def coupling_terms(D: int, N: int, lmax: int, lam_index: int):
     nt = lib.npcf_oracle_coupling(D, N, lmax, lam_index, None, None)
     if nt < 0:
         raise ValueError("bad lambda")
-    s = np.zeros((max(nt, 1), 3), dtype=np.int32)
+    s = np.zeros((max(nt, 1), 4), dtype=np.int32)
     c = np.zeros(max(nt, 1))
     lib.npcf_oracle_coupling(D, N, lmax, lam_index, _ip(s), _dp(c))
-    return s[:nt], c[:nt]
+    return (s[:nt] if N == 5 else s[:nt, :3].copy()), c[:nt]
 
 
 def _prep(pos, w, edges, box):
@@ -150,7 +152,8 @@ def _prep(pos, w, edges, box):
 
 
 def estimate(D, N, lmax, edges, box, pos, w, *, periodic=True, primaries=None, brute=False, bin_lt=False):
-    """The isotropic NPCF coefficients zeta^{0,b}_Lambda.
+    """The isotropic NPCF coefficients zeta^{0,b}_Lambda (N = 3: D = 2..4; N = 4: D = 2, 3;
+    N = 5: D = 3, lmax <= 6).
 
     brute=False: the separable estimator, eq. NPCF-estimator-discrete.
     brute=True:  the naive sum over N-tuplets, eq. NPCF-estimator-intro-discrete

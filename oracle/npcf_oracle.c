@@ -34,7 +34,12 @@
  *   R6 for D=4, N=3 the zero coupling is (-1)^(l-l_1)/sqrt(dim_l) on states
  *      with l_1' = -l_1 and equal higher indices (the D=3 value, extended);
  *   R7 periodic boxes use the minimum image; V_D is the box volume;
- *   R8 N=3 keys have b1 <= b2 (or b1 < b2 on request), N=4 keys b1<b2<b3.
+ *   R8 N=3 keys have b1 <= b2 (or b1 < b2 on request), N=4 keys b1<b2<b3,
+ *      N=5 keys b1<b2<b3<b4;
+ *   R15 the D=3 5PCF (eq. D=3-NPCF, intermediate label l12) keeps the even-parity labels
+ *      (l1+l2+l3+l4 even), which give the 585 angular components the paper counts for
+ *      lmax=4; its printed coefficient sqrt(2 l12 - 1) is read as sqrt(2 l12 + 1), the
+ *      value the CG chain of eq. Coupling-C gives.
  *
  * Floating point: compile with -ffp-contract=off so that no multiply-add is
  * fused; r^2 is formed as ((dx*dx + dy*dy) + dz*dz) + ... left to right.
@@ -229,24 +234,27 @@ static double cg_d3(int l1, int m1, int l2, int m2, int L, int M)
 /* ------------------------------------------------------------------ */
 /* Output keys and coupling terms.                                     */
 
-typedef struct { int b[3]; int l[3]; } okey_t;  /* unused entries are -1 (bins) / 0 (ells) */
+typedef struct { int b[4]; int l[5]; } okey_t;  /* unused entries are -1 (bins) / 0 (ells) */
 
 typedef struct {
-    int nl;            /* entries of Lambda used: 1 for N=3, 3 for N=4 */
-    int l[3];
+    int nl;            /* entries of Lambda used: 1 for N=3, 3 for N=4, 5 for N=5 */
+    int l[5];
 } lam_t;
 
 /* Angular labels Lambda of the isotropic basis.
  * N=3: Lambda = (l), l = 0..lmax (the final CG forces l^1 = l^2 = l).
  * N=4, D=3: Lambda = (l1, l2, l3) with l^12 = l3 forced by the final CG,
  *           every l <= lmax and (l1, l2, l3) obeying the triangle rule.
- * N=4, D=2: the signed (l1, l2, l3) with l1 + l2 + l3 = 0, l1 >= 0. */
+ * N=4, D=2: the signed (l1, l2, l3) with l1 + l2 + l3 = 0, l1 >= 0.
+ * N=5, D=3: (l1, l2, l12, l3, l4): l1..l4 <= lmax, l12 coupling l1 and l2 and then l12 and
+ *           l3 coupling to l4 (triangle rules), even parity l1+l2+l3+l4 (the components the
+ *           paper counts for its 5PCF, reading R15). */
 static int enum_lambdas(int D, int N, int lmax, lam_t *out)
 {
     int nl = 0;
     if (N == 3) {
         for (int l = 0; l <= lmax; ++l) {
-            if (out) { out[nl].nl = 1; out[nl].l[0] = l; out[nl].l[1] = 0; out[nl].l[2] = 0; }
+            if (out) { out[nl].nl = 1; out[nl].l[0] = l; out[nl].l[1] = 0; out[nl].l[2] = 0; out[nl].l[3] = 0; out[nl].l[4] = 0; }
             ++nl;
         }
     } else if (N == 4 && D == 3) {
@@ -254,7 +262,7 @@ static int enum_lambdas(int D, int N, int lmax, lam_t *out)
             for (int l2 = 0; l2 <= lmax; ++l2)
                 for (int l3 = 0; l3 <= lmax; ++l3) {
                     if (l3 < abs(l1 - l2) || l3 > l1 + l2) continue;
-                    if (out) { out[nl].nl = 3; out[nl].l[0] = l1; out[nl].l[1] = l2; out[nl].l[2] = l3; }
+                    if (out) { out[nl].nl = 3; out[nl].l[0] = l1; out[nl].l[1] = l2; out[nl].l[2] = l3; out[nl].l[3] = 0; out[nl].l[4] = 0; }
                     ++nl;
                 }
     } else if (N == 4 && D == 2) {
@@ -262,9 +270,24 @@ static int enum_lambdas(int D, int N, int lmax, lam_t *out)
             for (int l2 = -lmax; l2 <= lmax; ++l2) {
                 int l3 = -l1 - l2;
                 if (abs(l3) > lmax) continue;
-                if (out) { out[nl].nl = 3; out[nl].l[0] = l1; out[nl].l[1] = l2; out[nl].l[2] = l3; }
+                if (out) { out[nl].nl = 3; out[nl].l[0] = l1; out[nl].l[1] = l2; out[nl].l[2] = l3; out[nl].l[3] = 0; out[nl].l[4] = 0; }
                 ++nl;
             }
+    } else if (N == 5 && D == 3) {
+        for (int l1 = 0; l1 <= lmax; ++l1)
+            for (int l2 = 0; l2 <= lmax; ++l2)
+                for (int l12 = abs(l1 - l2); l12 <= l1 + l2; ++l12)
+                    for (int l3 = 0; l3 <= lmax; ++l3)
+                        for (int l4 = 0; l4 <= lmax; ++l4) {
+                            if (l4 < abs(l12 - l3) || l4 > l12 + l3) continue;
+                            if ((l1 + l2 + l3 + l4) % 2) continue;
+                            if (out) {
+                                out[nl].nl = 5;
+                                out[nl].l[0] = l1; out[nl].l[1] = l2; out[nl].l[2] = l12;
+                                out[nl].l[3] = l3; out[nl].l[4] = l4;
+                            }
+                            ++nl;
+                        }
     }
     return nl;
 }
@@ -274,6 +297,7 @@ static int supported(int D, int N, int lmax, int nbins)
     if (lmax < 0 || lmax > 12 || nbins < 1 || nbins > OR_MAXB) return 0;
     if (N == 3) return D >= 2 && D <= 4;
     if (N == 4) return D == 2 || D == 3;
+    if (N == 5) return D == 3 && lmax <= 6;
     return 0;
 }
 
@@ -289,11 +313,24 @@ static int enum_keys(int D, int N, int lmax, int nbins, int bin_lt, okey_t *out)
                 for (int il = 0; il < nl; ++il) {
                     if (out) {
                         okey_t *k = &out[nk];
-                        k->b[0] = b1; k->b[1] = b2; k->b[2] = -1;
-                        k->l[0] = lam[il].l[0]; k->l[1] = 0; k->l[2] = 0;
+                        k->b[0] = b1; k->b[1] = b2; k->b[2] = -1; k->b[3] = -1;
+                        k->l[0] = lam[il].l[0]; k->l[1] = 0; k->l[2] = 0; k->l[3] = 0; k->l[4] = 0;
                     }
                     ++nk;
                 }
+    } else if (N == 5) {
+        for (int b1 = 0; b1 < nbins; ++b1)
+            for (int b2 = b1 + 1; b2 < nbins; ++b2)
+                for (int b3 = b2 + 1; b3 < nbins; ++b3)
+                    for (int b4 = b3 + 1; b4 < nbins; ++b4)
+                        for (int il = 0; il < nl; ++il) {
+                            if (out) {
+                                okey_t *k = &out[nk];
+                                k->b[0] = b1; k->b[1] = b2; k->b[2] = b3; k->b[3] = b4;
+                                for (int a = 0; a < 5; ++a) k->l[a] = lam[il].l[a];
+                            }
+                            ++nk;
+                        }
     } else {
         for (int b1 = 0; b1 < nbins; ++b1)
             for (int b2 = b1 + 1; b2 < nbins; ++b2)
@@ -301,8 +338,9 @@ static int enum_keys(int D, int N, int lmax, int nbins, int bin_lt, okey_t *out)
                     for (int il = 0; il < nl; ++il) {
                         if (out) {
                             okey_t *k = &out[nk];
-                            k->b[0] = b1; k->b[1] = b2; k->b[2] = b3;
+                            k->b[0] = b1; k->b[1] = b2; k->b[2] = b3; k->b[3] = -1;
                             k->l[0] = lam[il].l[0]; k->l[1] = lam[il].l[1]; k->l[2] = lam[il].l[2];
+                            k->l[3] = 0; k->l[4] = 0;
                         }
                         ++nk;
                     }
@@ -312,7 +350,7 @@ static int enum_keys(int D, int N, int lmax, int nbins, int bin_lt, okey_t *out)
 }
 
 /* One term of P^0_Lambda = sum_terms C prod_i Y_{s_i}(r^i) (eq. N-1-particle-basis-wavefunction). */
-typedef struct { int s[3]; double c; } term_t;
+typedef struct { int s[4]; double c; } term_t;
 
 static int state_index(int D, int lmax, const state_t *st)
 {
@@ -339,6 +377,7 @@ static int lambda_terms(int D, int N, int lmax, const lam_t *lam, term_t *out)
                 out[nt].s[0] = state_index(D, lmax, &a);
                 out[nt].s[1] = state_index(D, lmax, &b);
                 out[nt].s[2] = -1;
+                out[nt].s[3] = -1;
                 out[nt].c = 1.0;
             }
             ++nt;
@@ -352,6 +391,7 @@ static int lambda_terms(int D, int N, int lmax, const lam_t *lam, term_t *out)
                         out[nt].s[0] = state_index(D, lmax, &a);
                         out[nt].s[1] = state_index(D, lmax, &b);
                         out[nt].s[2] = -1;
+                        out[nt].s[3] = -1;
                         out[nt].c = c;
                     }
                     ++nt;
@@ -366,6 +406,7 @@ static int lambda_terms(int D, int N, int lmax, const lam_t *lam, term_t *out)
                         out[nt].s[0] = state_index(D, lmax, &a);
                         out[nt].s[1] = state_index(D, lmax, &b);
                         out[nt].s[2] = -1;
+                        out[nt].s[3] = -1;
                         out[nt].c = sgn_pow(abs(l - l1)) / sqrt(dim);
                     }
                     ++nt;
@@ -378,6 +419,7 @@ static int lambda_terms(int D, int N, int lmax, const lam_t *lam, term_t *out)
             out[nt].s[0] = state_index(D, lmax, &a);
             out[nt].s[1] = state_index(D, lmax, &b);
             out[nt].s[2] = state_index(D, lmax, &c);
+            out[nt].s[3] = -1;
             out[nt].c = 1.0;
         }
         ++nt;
@@ -396,10 +438,37 @@ static int lambda_terms(int D, int N, int lmax, const lam_t *lam, term_t *out)
                         out[nt].s[0] = state_index(D, lmax, &a);
                         out[nt].s[1] = state_index(D, lmax, &b);
                         out[nt].s[2] = state_index(D, lmax, &cc);
+                        out[nt].s[3] = -1;
                         out[nt].c = c;
                     }
                     ++nt;
                 }
+    } else if (N == 5 && D == 3) {
+        /* <l1 m1 l2 m2 | l12 M12> <l12 M12 l3 m3 | l4 M> <l4 M l4 m4 | 0 0>, summed over the
+         * intermediate projections M12 and M (eq. Coupling-C with the CGs of eq. CG-examples) */
+        int l1 = lam->l[0], l2 = lam->l[1], l12 = lam->l[2], l3 = lam->l[3], l4 = lam->l[4];
+        for (int m1 = -l1; m1 <= l1; ++m1)
+            for (int m2 = -l2; m2 <= l2; ++m2)
+                for (int m3 = -l3; m3 <= l3; ++m3)
+                    for (int m4 = -l4; m4 <= l4; ++m4) {
+                        double c = 0.0;
+                        for (int M12 = -l12; M12 <= l12; ++M12) {
+                            double c12 = cg_d3(l1, m1, l2, m2, l12, M12);
+                            if (c12 == 0.0) continue;
+                            for (int M = -l4; M <= l4; ++M)
+                                c += c12 * cg_d3(l12, M12, l3, m3, l4, M) * cg_d3(l4, M, l4, m4, 0, 0);
+                        }
+                        if (c == 0.0) continue;
+                        if (out) {
+                            state_t a = {{m1, l1, 0}}, b = {{m2, l2, 0}}, cc = {{m3, l3, 0}}, dd = {{m4, l4, 0}};
+                            out[nt].s[0] = state_index(D, lmax, &a);
+                            out[nt].s[1] = state_index(D, lmax, &b);
+                            out[nt].s[2] = state_index(D, lmax, &cc);
+                            out[nt].s[3] = state_index(D, lmax, &dd);
+                            out[nt].c = c;
+                        }
+                        ++nt;
+                    }
     }
     return nt;
 }
@@ -494,24 +563,24 @@ int npcf_oracle_nkeys(int D, int N, int lmax, int nbins, int bin_lt)
     return enum_keys(D, N, lmax, nbins, bin_lt, NULL);
 }
 
-int npcf_oracle_keys(int D, int N, int lmax, int nbins, int bin_lt, int *keys /* nkeys x 6 */)
+int npcf_oracle_keys(int D, int N, int lmax, int nbins, int bin_lt, int *keys /* nkeys x 9 */)
 {
     if (!supported(D, N, lmax, nbins)) return -1;
     int nk = enum_keys(D, N, lmax, nbins, bin_lt, NULL);
     okey_t *k = (okey_t *)malloc(sizeof(okey_t) * (nk > 0 ? nk : 1));
     enum_keys(D, N, lmax, nbins, bin_lt, k);
-    for (int i = 0; i < nk; ++i) {
-        for (int a = 0; a < 3; ++a) keys[6 * i + a] = k[i].b[a];
-        for (int a = 0; a < 3; ++a) keys[6 * i + 3 + a] = k[i].l[a];
+    for (int i = 0; i < nk; ++i) {  /* b1..b4, l1..l5 */
+        for (int a = 0; a < 4; ++a) keys[9 * i + a] = k[i].b[a];
+        for (int a = 0; a < 5; ++a) keys[9 * i + 4 + a] = k[i].l[a];
     }
     free(k);
     return nk;
 }
 
 /* Coupling terms of every Lambda, flattened: for lambda index il the terms
- * are returned as (s1, s2, s3, c) rows.  Used by the tests to pin the
- * coupling against independent formulas. */
-int npcf_oracle_coupling(int D, int N, int lmax, int il, int *s_out /* nt x 3 */, double *c_out)
+ * are returned as (s1, s2, s3, s4, c) rows (unused states -1).  Used by the tests to pin
+ * the coupling against independent formulas. */
+int npcf_oracle_coupling(int D, int N, int lmax, int il, int *s_out /* nt x 4 */, double *c_out)
 {
     if (!supported(D, N, lmax, 1)) return -1;
     int nl = enum_lambdas(D, N, lmax, NULL);
@@ -523,7 +592,7 @@ int npcf_oracle_coupling(int D, int N, int lmax, int il, int *s_out /* nt x 3 */
         term_t *t = (term_t *)malloc(sizeof(term_t) * (nt > 0 ? nt : 1));
         lambda_terms(D, N, lmax, &lam[il], t);
         for (int i = 0; i < nt; ++i) {
-            for (int a = 0; a < 3; ++a) s_out[3 * i + a] = t[i].s[a];
+            for (int a = 0; a < 4; ++a) s_out[4 * i + a] = t[i].s[a];
             c_out[i] = t[i].c;
         }
         free(t);
@@ -535,8 +604,11 @@ int npcf_oracle_coupling(int D, int N, int lmax, int il, int *s_out /* nt x 3 */
 /* lambda index of a key's angular labels (keys are ordered bins-major) */
 static int key_lambda(const okey_t *k, const lam_t *lam, int nl)
 {
-    for (int i = 0; i < nl; ++i)
-        if (lam[i].l[0] == k->l[0] && lam[i].l[1] == k->l[1] && lam[i].l[2] == k->l[2]) return i;
+    for (int i = 0; i < nl; ++i) {
+        int same = 1;
+        for (int a = 0; a < 5; ++a) same = same && lam[i].l[a] == k->l[a];
+        if (same) return i;
+    }
     return -1;
 }
 
@@ -615,7 +687,8 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
                 cplx acc = 0.0;
                 for (int t = tstart[klam[i]]; t < tstart[klam[i] + 1]; ++t) {
                     cplx p = terms[t].c * a[kk->b[0] * ns + terms[t].s[0]] * a[kk->b[1] * ns + terms[t].s[1]];
-                    if (N == 4) p *= a[kk->b[2] * ns + terms[t].s[2]];
+                    if (N >= 4) p *= a[kk->b[2] * ns + terms[t].s[2]];
+                    if (N == 5) p *= a[kk->b[3] * ns + terms[t].s[3]];
                     acc += p;
                 }
                 zeta[i] += w[j] * acc;
@@ -645,7 +718,7 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
                                 P += terms[t].c * nb_y[p1 * ns + terms[t].s[0]] * nb_y[p2 * ns + terms[t].s[1]];
                             double wt = w[nb_idx[p1]] * w[nb_idx[p2]] / (vb[kk->b[0]] * vb[kk->b[1]]);
                             acc += wt * conj(P);
-                        } else {
+                        } else if (N == 4) {
                             for (int64_t p3 = 0; p3 < nn; ++p3) {
                                 if (nb_bin[p3] != kk->b[2]) continue;
                                 cplx P = 0.0;
@@ -655,6 +728,20 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
                                 double wt = w[nb_idx[p1]] * w[nb_idx[p2]] * w[nb_idx[p3]] /
                                             (vb[kk->b[0]] * vb[kk->b[1]] * vb[kk->b[2]]);
                                 acc += wt * conj(P);
+                            }
+                        } else {
+                            for (int64_t p3 = 0; p3 < nn; ++p3) {
+                                if (nb_bin[p3] != kk->b[2]) continue;
+                                for (int64_t p4 = 0; p4 < nn; ++p4) {
+                                    if (nb_bin[p4] != kk->b[3]) continue;
+                                    cplx P = 0.0;
+                                    for (int t = tstart[klam[i]]; t < tstart[klam[i] + 1]; ++t)
+                                        P += terms[t].c * nb_y[p1 * ns + terms[t].s[0]] * nb_y[p2 * ns + terms[t].s[1]] *
+                                             nb_y[p3 * ns + terms[t].s[2]] * nb_y[p4 * ns + terms[t].s[3]];
+                                    double wt = w[nb_idx[p1]] * w[nb_idx[p2]] * w[nb_idx[p3]] * w[nb_idx[p4]] /
+                                                (vb[kk->b[0]] * vb[kk->b[1]] * vb[kk->b[2]] * vb[kk->b[3]]);
+                                    acc += wt * conj(P);
+                                }
                             }
                         }
                     }

@@ -216,11 +216,100 @@ def test_isotropic_basis_rotation_invariant_d3_n4():
 
 
 # ------------------------------------------------------------------ counts
-def test_component_counts_printed_in_paper():
-    g = json.load(open(os.path.join(GOLDEN, "paper_counts.json")))["d2_4pcf_lmax4"]
+@pytest.mark.parametrize("name", ["d2_4pcf_lmax4", "d3_5pcf_lmax4"])
+def test_component_counts_printed_in_paper(name):
+    g = json.load(open(os.path.join(GOLDEN, "paper_counts.json")))[name]
     k = oracle.keys(g["D"], g["N"], g["lmax"], g["nbins"])
-    assert len({tuple(x) for x in k[:, 3:]}) == g["angular"]
-    assert len({tuple(x) for x in k[:, :3]}) == g["radial"]
+    nb = g["N"] - 1
+    assert len({tuple(x) for x in k[:, nb:]}) == g["angular"]
+    assert len({tuple(x) for x in k[:, :nb]}) == g["radial"]
+
+
+# ------------------------------------------------------------------ 5PCF (N = 5, D = 3)
+def _lams5(lmax, nbins=4):
+    keys = oracle.keys(3, 5, lmax, nbins)
+    lams = []
+    for k in keys[:, 4:]:
+        if tuple(k) not in lams:
+            lams.append(tuple(int(x) for x in k))
+    return lams
+
+
+def test_5pcf_coupling_equals_printed_3j_form():
+    """C^{Lambda;0} of the chain of eq. Coupling-C for N=5, D=3 equals the printed isotropic 5PCF
+    form (-1)^{l1+l2+l3+l4} (-1)^{l12-m12} sqrt(2 l12 + 1) (l1 l2 l12; m1 m2 -m12)(l12 l3 l4; m12 m3 m4)
+    (the printed sqrt(2 l12 - 1) read as sqrt(2 l12 + 1), eq. CG-examples), with sympy's 3j."""
+    from sympy.physics.wigner import wigner_3j
+
+    lmax = 2
+    st = [tuple(s) for s in oracle.states(3, lmax)]
+    for il, (l1, l2, l12, l3, l4) in enumerate(_lams5(lmax)):
+        s, c = oracle.coupling_terms(3, 5, lmax, il)
+        got = {tuple(st[x][0] for x in row): cc for row, cc in zip(s, c)}
+        for m1 in range(-l1, l1 + 1):
+            for m2 in range(-l2, l2 + 1):
+                m12 = m1 + m2
+                if abs(m12) > l12:
+                    continue
+                for m3 in range(-l3, l3 + 1):
+                    m4 = -m12 - m3
+                    if abs(m4) > l4:
+                        continue
+                    ref = ((-1) ** (l1 + l2 + l3 + l4 + l12 - m12) * np.sqrt(2 * l12 + 1) *
+                           float(wigner_3j(l1, l2, l12, m1, m2, -m12)) * float(wigner_3j(l12, l3, l4, m12, m3, m4)))
+                    assert abs(got.get((m1, m2, m3, m4), 0.0) - ref) < 1e-13, (l1, l2, l12, l3, l4, m1, m2, m3)
+
+
+def test_5pcf_basis_rotation_invariant():
+    lmax = 2
+    R = _random_rotation(3, 19)
+    rs = [_rand_dirs(3, 8, s) for s in (21, 22, 23, 24)]
+    Y = [oracle.harmonics(3, lmax, r) for r in rs]
+    YR = [oracle.harmonics(3, lmax, r @ R.T) for r in rs]
+    for il in range(len(_lams5(lmax))):
+        s, c = oracle.coupling_terms(3, 5, lmax, il)
+        P = sum(cc * Y[0][:, a] * Y[1][:, b] * Y[2][:, e] * Y[3][:, f] for (a, b, e, f), cc in zip(s, c))
+        PR = sum(cc * YR[0][:, a] * YR[1][:, b] * YR[2][:, e] * YR[3][:, f] for (a, b, e, f), cc in zip(s, c))
+        np.testing.assert_allclose(P, PR, atol=1e-12)
+
+
+def test_5pcf_separable_equals_naive_sum():
+    """Separable 5PCF = the naive 5-tuplet sum on the same basis (the paper's machine-precision check)."""
+    pos, w = _tiny(3, 40, 1.0, 131)
+    edges = np.array([0.1, 0.25, 0.33, 0.39, 0.44])
+    k1, z1 = oracle.estimate(3, 5, 2, edges, np.ones(3), pos, w, primaries=(0, 6))
+    k2, z2 = oracle.estimate(3, 5, 2, edges, np.ones(3), pos, w, primaries=(0, 6), brute=True)
+    assert np.array_equal(k1, k2)
+    scale = np.max(np.abs(z1))
+    assert scale > 0
+    np.testing.assert_allclose(z1, z2, rtol=0, atol=1e-12 * scale)
+
+
+def test_5pcf_l4_zero_slice_is_4pcf_times_a00():
+    """With l4 = 0 the last two couplings force l12 = l3 and leave the N=4 coupling, so for one
+    primary zeta_5(b1,b2,b3,b4; l1,l2,l3,l3,0) = zeta_4(b1,b2,b3; l1,l2,l3) * a_00(b4)."""
+    pos, w = _tiny(3, 60, 1.0, 141)
+    edges = np.linspace(0.05, 0.45, 6)
+    j = 7
+    k5, z5 = oracle.estimate(3, 5, 2, edges, np.ones(3), pos, w, primaries=(j, j + 1))
+    k4, z4 = oracle.estimate(3, 4, 2, edges, np.ones(3), pos, w, primaries=(j, j + 1))
+    idx4 = {tuple(int(x) for x in k): i for i, k in enumerate(k4)}
+    d = pos - pos[j]
+    d -= np.round(d)
+    r = np.sqrt((d * d).sum(1))
+    r[j] = -1.0
+    vb = 4 * np.pi / 3 * (edges[1:] ** 3 - edges[:-1] ** 3)
+    a00 = np.array([w[(r >= edges[b]) & (r < edges[b + 1])].sum() for b in range(5)]) / np.sqrt(4 * np.pi) / vb
+    checked = 0
+    for i, k in enumerate(k5):
+        b1, b2, b3, b4, l1, l2, l12, l3, l4 = (int(x) for x in k)
+        if l4 != 0:
+            continue
+        assert l12 == l3
+        ref = z4[idx4[(b1, b2, b3, l1, l2, l3)]] * a00[b4]
+        assert abs(z5[i] - ref) <= 1e-12 * max(1.0, np.max(np.abs(z5)))
+        checked += 1
+    assert checked > 50
 
 
 # --------------------------------------------------------------- estimator
