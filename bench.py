@@ -8,7 +8,7 @@ uniform randoms with weight -1, periodic box of side 1000, 10 radial bins
 over [20, 160], lmax = 5 (13,320 complex coefficients).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload d3n4|d3n3_fp64|d2n3|d2n4|d4n3|d4n3-grad|batch64] [--scale S]
+                    [--workload d3n4|d3n3_fp64|d2n3|d2n4|d4n3|d3n5|d4n3-grad|batch64] [--scale S]
 
 Other workloads: d4n3-grad times one gradient step of the D=4 3PCF (forward,
 chi^2 upstream gradient, backward: npcf_backward); batch64 times the 64
@@ -84,6 +84,20 @@ def coupling_terms_per_primary(D: int, N: int, lmax: int, nbins: int) -> int:
     if N == 3:
         per = sum(2 * l + 1 for l in range(lmax + 1)) if D == 3 else (lmax + 1)
         return per * nbins * (nbins + 1) // 2
+    if N == 5:  # D=3: (l1, l2, l12, l3, l4) even parity, (m1, m2, m3) with |m1 + m2| <= l12, |m4| <= l4
+        t = 0
+        for l1 in range(lmax + 1):
+            for l2 in range(lmax + 1):
+                for l12 in range(abs(l1 - l2), l1 + l2 + 1):
+                    for l3 in range(lmax + 1):
+                        for l4 in range(abs(l12 - l3), min(l12 + l3, lmax) + 1):
+                            if (l1 + l2 + l3 + l4) % 2:
+                                continue
+                            for m1 in range(-l1, l1 + 1):
+                                for m2 in range(-l2, l2 + 1):
+                                    if abs(m1 + m2) <= l12:
+                                        t += sum(1 for m3 in range(-l3, l3 + 1) if abs(m1 + m2 + m3) <= l4)
+        return math.comb(nbins, 4) * t
     ntrip = math.comb(nbins, 3)
     if D == 2:
         return ntrip * sum(1 for a in range(lmax + 1) for b in range(-lmax, lmax + 1) if abs(a + b) <= lmax)
@@ -254,7 +268,7 @@ def run_ours(args, rank, world):
         pbuild.build()
     if world > 1:
         torch.distributed.barrier()
-    base_seed = {"d3n4": 2, "d2n3": 1, "d2n4": 1, "d4n3": 4, "d3n3_fp64": 0}[args.workload]
+    base_seed = {"d3n4": 2, "d2n3": 1, "d2n4": 1, "d4n3": 4, "d3n3_fp64": 0, "d3n5": 5}[args.workload]
     wl = catalogs.workload(args.workload, seed=base_seed + 1000 * rank, scale=args.scale)
     prec = "fp64" if wl.precision == "fp64" else "fp32"
     tdt = torch.float64 if prec == "fp64" else torch.float32

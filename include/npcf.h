@@ -11,7 +11,8 @@
  *     zeta^{0,b}_Lambda = (1/V_D) sum_j w_j sum_[l] C^{Lambda;0} prod_i a^{b_i}_{l^i}(y_j),
  * with C the zero-total-angular-momentum coupling (eq. Coupling-C,
  * eq. zero-ang-mom-states).  Supported: N=3 for D in {2,3,4}; N=4 for
- * D in {2,3}.  Euclidean space (k = 0 in eq. metric).
+ * D in {2,3}; N=5 for D=3 (eq. D=3-NPCF, intermediate label l12, lmax <= 6).
+ * Euclidean space (k = 0 in eq. metric).
  *
  * Conventions (the readings of the paper this library takes):
  *   - bins are half-open [e_b, e_{b+1}); pairs with r = 0 are skipped;
@@ -93,7 +94,9 @@ NPCF_API npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, 
 /* Number of output coefficients (each one complex: 2 doubles). */
 NPCF_API npcf_status npcf_num_coeffs(npcf_plan_t plan, int64_t* ncoeff);
 
-/* Labels of coefficient i: bins (N-1 entries, host) and ells (1 for N=3, 3 for N=4, host). */
+/* Labels of coefficient i: bins (N-1 entries, host) and ells (host; 1 for N=3: l; 3 for N=4:
+ * l1, l2, l3; 5 for N=5: l1, l2, l12, l3, l4).  N=5 keys have b1 < b2 < b3 < b4 and the
+ * even-parity label sets (l1 + l2 + l3 + l4 even), 585 of them at lmax = 4. */
 NPCF_API npcf_status npcf_coeff_index(npcf_plan_t plan, int64_t i, int* bins, int* ells);
 
 /*

@@ -204,6 +204,11 @@ def workload(name: str, seed: int | None = None, scale: float = 1.0) -> Workload
         pos = np.concatenate([data, rand])
         w = np.concatenate([np.ones(data.shape[0]), -np.ones(nr)])
         return Workload(name, 3, 4, 5, linear_edges(20.0, 160.0, 10), np.full(3, L), pos, w)
+    if name == "d3n5":
+        # the paper's 5PCF example: uniform points in the periodic unit cube, ten bins in [0.1, 0.4], lmax 4
+        s = 5 if seed is None else seed
+        n = max(8, int(round(10_000 * scale)))
+        return Workload(name, 3, 5, 4, linear_edges(0.1, 0.4, 10), np.full(3, 1.0), uniform(n, 3, 1.0, s), np.ones(n))
     if name == "d4n3":
         s = 4 if seed is None else seed
         n_half = max(4, int(round(50_000 * scale)))

@@ -278,6 +278,7 @@ int d2n4_group(int nbins, int lmax)
 
 int couple_smem(const CoupleParams& p, int fp64)
 {
+    if (p.N == 5) return couple_d3n5_smem(p, fp64);
     if (p.N == 4 && p.D == 3) return couple_d3n4_smem(p, fp64);
     if (p.N == 4 && p.D == 2 && !fp64) {
         const int G = d2n4_group(p.nbins, p.lmax);
@@ -298,6 +299,7 @@ int couple_smem(const CoupleParams& p, int fp64)
 
 cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s)
 {
+    if (p.N == 5) return launch_couple_d3n5(p, fp64, grid, smem, s);
     if (p.N == 3) {
         switch (p.D * 2 + (fp64 ? 1 : 0)) {
             case 4: return launch_t<MODE_N3, 2, 0, float>(p, grid, smem, s);

@@ -100,7 +100,12 @@ struct CoupleParams {
     const int2* lam2;          // D=2, N=4: (l1, l2) per Lambda index
     const signed char* lam_odd;// D=3, N=4: 1 if l1+l2+l3 is odd (coefficient imaginary)
     const void* pref;          // N=3: per-l factor of the zero coupling (T)
-    int group;                 // D=2 N=4 FP32: primaries per shared-memory group
+    int group;                 // D=2 N=4 FP32 and N=5: primaries per shared-memory group
+    int ntriple;               // N=5: bin triples b1 < b2 < b3 < nbins - 1
+    const int4* triples;       // N=5: (b1, b2, b3, first key) per triple
+    const int4* lam5;          // N=5: (first term, end term, l4, 0) per label set
+    const int* terms5;         // N=5: state(l1,m1) | state(l2,m2) << 8 | state(l3,m3) << 16 | m4 << 24
+    const double* coef5;       // N=5: the coupling coefficient of each term
     int ncat;                  // catalogues (blockIdx.z); 0 or 1 for a single one
     const int* cat_first;      // ncat: first primary of each catalogue in the a-array (NULL: one catalogue)
     const int* cat_count;      // ncat: its primaries
@@ -136,6 +141,9 @@ cudaError_t launch_make_items(const ItemBuffers& b, const int* cell_start, const
 cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
 int couple_smem(const CoupleParams& p, int fp64);
 int d2n4_group(int nbins, int lmax);
+int d3n5_group(int nbins, int lmax, int fp64);
+int couple_d3n5_smem(const CoupleParams& p, int fp64);
+cudaError_t launch_couple_d3n5(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
 cudaError_t launch_reduce(const double* partial, int rows, int ncols, double scale, double* out, cudaStream_t s);
 // per catalogue c: out[c][k] = scales[c] * sum_r partial[c][r][k]
 cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, int ncat, const double* scales, double* out,

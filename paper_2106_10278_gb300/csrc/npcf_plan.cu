@@ -101,6 +101,7 @@ struct npcf_plan_s {
     std::vector<int2> pairs;
     std::vector<int> pair_key;
     std::vector<int4> kblocks;
+    std::vector<int4> triples;  // N=5: (b1, b2, b3, first key)
     int max_block_keys = 0;
     int max_block_pairs = 0;
     std::vector<int> task_pairs;
@@ -112,6 +113,7 @@ struct npcf_plan_s {
     PairParams pp{};
     // device tables
     DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil, d_task;
+    DevBuf d_triples, d_lam5, d_terms5, d_coef5;  // N=5 coupling tables
     // workspace
     DevBuf w_cid, w_perm, w_rec, w_cells, w_items, w_a, w_wprim, w_partial, w_small, w_hpos, w_hw, w_hout;
     // adjoint (npcf_backward)
@@ -150,21 +152,31 @@ void build_keys(npcf_plan_s* P)
 {
     const int nb = P->nbins, L = P->lmax;
     P->lam.clear();
+    // labels: 5 ints per set (unused entries 0): N=3 (l); N=4 (l1, l2, l3); N=5 (l1, l2, l12, l3, l4)
     if (P->N == 3) {
-        for (int l = 0; l <= L; ++l) P->lam.insert(P->lam.end(), {l, 0, 0});
+        for (int l = 0; l <= L; ++l) P->lam.insert(P->lam.end(), {l, 0, 0, 0, 0});
+    } else if (P->N == 5) {
+        // even parity (l1 + l2 + l3 + l4), the components counted for the paper's 5PCF
+        for (int l1 = 0; l1 <= L; ++l1)
+            for (int l2 = 0; l2 <= L; ++l2)
+                for (int l12 = std::abs(l1 - l2); l12 <= l1 + l2; ++l12)
+                    for (int l3 = 0; l3 <= L; ++l3)
+                        for (int l4 = 0; l4 <= L; ++l4)
+                            if (l4 >= std::abs(l12 - l3) && l4 <= l12 + l3 && (l1 + l2 + l3 + l4) % 2 == 0)
+                                P->lam.insert(P->lam.end(), {l1, l2, l12, l3, l4});
     } else if (P->D == 3) {
         for (int a = 0; a <= L; ++a)
             for (int b = 0; b <= L; ++b)
                 for (int c = 0; c <= L; ++c)
-                    if (c >= std::abs(a - b) && c <= a + b) P->lam.insert(P->lam.end(), {a, b, c});
+                    if (c >= std::abs(a - b) && c <= a + b) P->lam.insert(P->lam.end(), {a, b, c, 0, 0});
     } else {
         for (int a = 0; a <= L; ++a)
             for (int b = -L; b <= L; ++b) {
                 const int c = -a - b;
-                if (std::abs(c) <= L) P->lam.insert(P->lam.end(), {a, b, c});
+                if (std::abs(c) <= L) P->lam.insert(P->lam.end(), {a, b, c, 0, 0});
             }
     }
-    P->nlam = (int)P->lam.size() / 3;
+    P->nlam = (int)P->lam.size() / 5;
     P->key_bins.clear();
     P->key_lam.clear();
     P->pairs.clear();
@@ -176,10 +188,22 @@ void build_keys(npcf_plan_s* P)
                 P->pairs.push_back(make_int2(b1, b2));
                 P->pair_key.push_back((int)P->key_lam.size());
                 for (int il = 0; il < P->nlam; ++il) {
-                    P->key_bins.insert(P->key_bins.end(), {b1, b2, -1});
+                    P->key_bins.insert(P->key_bins.end(), {b1, b2, -1, -1});
                     P->key_lam.push_back(il);
                 }
             }
+    } else if (P->N == 5) {
+        // keys ordered (b1, b2, b3, b4, labels); work items are the triples that have a b4
+        for (int b1 = 0; b1 < nb; ++b1)
+            for (int b2 = b1 + 1; b2 < nb; ++b2)
+                for (int b3 = b2 + 1; b3 < nb; ++b3) {
+                    if (b3 + 1 < nb) P->triples.push_back(make_int4(b1, b2, b3, (int)P->key_lam.size()));
+                    for (int b4 = b3 + 1; b4 < nb; ++b4)
+                        for (int il = 0; il < P->nlam; ++il) {
+                            P->key_bins.insert(P->key_bins.end(), {b1, b2, b3, b4});
+                            P->key_lam.push_back(il);
+                        }
+                }
     } else {
         for (int b1 = 0; b1 < nb; ++b1)
             for (int b2 = b1 + 1; b2 < nb; ++b2) {
@@ -189,7 +213,7 @@ void build_keys(npcf_plan_s* P)
                 }
                 for (int b3 = b2 + 1; b3 < nb; ++b3)
                     for (int il = 0; il < P->nlam; ++il) {
-                        P->key_bins.insert(P->key_bins.end(), {b1, b2, b3});
+                        P->key_bins.insert(P->key_bins.end(), {b1, b2, b3, -1});
                         P->key_lam.push_back(il);
                     }
             }
@@ -555,11 +579,52 @@ npcf_status setup_tables(npcf_plan_s* P)
     std::vector<int2> lam2;
     std::vector<signed char> lamodd;
     for (int i = 0; i < P->nlam; ++i) {
-        lam2.push_back(make_int2(P->lam[3 * i], P->lam[3 * i + 1]));
-        lamodd.push_back((signed char)((P->lam[3 * i] + P->lam[3 * i + 1] + P->lam[3 * i + 2]) & 1));
+        lam2.push_back(make_int2(P->lam[5 * i], P->lam[5 * i + 1]));
+        lamodd.push_back((signed char)((P->lam[5 * i] + P->lam[5 * i + 1] + P->lam[5 * i + 2]) & 1));
     }
     CUDA_TRY(upload(P->d_lam2, lam2));
     CUDA_TRY(upload(P->d_lamodd, lamodd));
+    if (P->N == 5) {
+        // the coupling terms of every label set, from the CG chain of eq. Coupling-C
+        // <l1 m1 l2 m2|l12 m12><l12 m12 l3 m3|l4 M><l4 M l4 m4|0 0>, M = -m4, sorted by m4
+        auto cg = [](int j1, int m1, int j2, int m2, int J, int M) {
+            return cx::neg1_pow(j1 - j2 + M) * std::sqrt(2.0 * J + 1.0) * cx::wigner3j(j1, j2, J, m1, m2, -M);
+        };
+        std::vector<int4> lam5;
+        std::vector<int> terms;
+        std::vector<double> coef;
+        for (int i = 0; i < P->nlam; ++i) {
+            const int* l = &P->lam[5 * i];
+            const int l1 = l[0], l2 = l[1], l12 = l[2], l3 = l[3], l4 = l[4];
+            const int t0 = (int)terms.size();
+            for (int m4 = -l4; m4 <= l4; ++m4)
+                for (int m1 = -l1; m1 <= l1; ++m1)
+                    for (int m2 = -l2; m2 <= l2; ++m2) {
+                        const int m12 = m1 + m2, m3 = -m4 - m12;
+                        if (std::abs(m12) > l12 || std::abs(m3) > l3) continue;
+                        const double c = cg(l1, m1, l2, m2, l12, m12) * cg(l12, m12, l3, m3, l4, -m4) *
+                                         cg(l4, -m4, l4, m4, 0, 0);
+                        if (c == 0.0) continue;
+                        const int s1 = l1 * l1 + l1 + m1, s2 = l2 * l2 + l2 + m2, s3 = l3 * l3 + l3 + m3;
+                        terms.push_back((int)((unsigned)s1 | ((unsigned)s2 << 8) | ((unsigned)s3 << 16) |
+                                              ((unsigned)(m4 & 0xff) << 24)));
+                        coef.push_back(c);
+                    }
+            lam5.push_back(make_int4(t0, (int)terms.size(), l4, 0));
+        }
+        CUDA_TRY(upload(P->d_lam5, lam5));
+        CUDA_TRY(upload(P->d_terms5, terms));
+        CUDA_TRY(upload(P->d_coef5, coef));
+        CUDA_TRY(upload(P->d_triples, P->triples));
+        CoupleParams cp{};
+        cp.N = 5;
+        cp.nbins = nb;
+        cp.lmax = P->lmax;
+        cp.group = d3n5_group(nb, P->lmax, P->fp64);
+        if (couple_d3n5_smem(cp, P->fp64) > P->smem_optin)
+            return fail(NPCF_ERR_UNSUPPORTED, "the 5PCF coupling needs more shared memory than available");
+        return NPCF_OK;
+    }
     // key blocks: accumulators get what shared memory the per-primary copy leaves
     CoupleParams cp{};
     cp.D = D;
@@ -673,7 +738,12 @@ CoupleParams couple_params(const npcf_plan_s* P, const void* a, const void* wpri
     kp.lam2 = P->d_lam2.as<int2>();
     kp.lam_odd = P->d_lamodd.as<signed char>();
     kp.pref = P->d_pref.p;
-    kp.group = d2n4_group(P->nbins, P->lmax);
+    kp.group = P->N == 5 ? d3n5_group(P->nbins, P->lmax, P->fp64) : d2n4_group(P->nbins, P->lmax);
+    kp.ntriple = (int)P->triples.size();
+    kp.triples = P->d_triples.as<int4>();
+    kp.lam5 = P->d_lam5.as<int4>();
+    kp.terms5 = P->d_terms5.as<int>();
+    kp.coef5 = P->d_coef5.as<double>();
     kp.ncat = 1;
     return kp;
 }
@@ -782,7 +852,11 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     const int nkb = (int)P->kblocks.size();
     int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
     if (d2n4_registers(P)) rows = P->nsm;
-    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim_max + chunk - 1) / chunk));
+    if (P->N == 5) {  // groups of d3n5_group primaries; each partial row holds every coefficient
+        const int G = d3n5_group(P->nbins, P->lmax, P->fp64);
+        rows = (int)std::min<int64_t>(P->nsm, std::max<int64_t>(1, (nprim_max + G - 1) / G));
+    }
+    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, P->N == 5 ? rows : (nprim_max + chunk - 1) / chunk));
     if ((st = reserve_workspace(P, n, nprim_max, rows, P->ncells)) != NPCF_OK) return st;
     PairStage ps;
     if ((st = run_pairs(P, single_view(P), pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
@@ -1040,7 +1114,10 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
     if (!out) return fail(NPCF_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (D < 2 || D > 4) return fail(NPCF_ERR_UNSUPPORTED, "D=%d not supported (2..4)", D);
-    if (N != 3 && N != 4) return fail(NPCF_ERR_UNSUPPORTED, "N=%d not supported (3 or 4)", N);
+    if (N < 3 || N > 5) return fail(NPCF_ERR_UNSUPPORTED, "N=%d not supported (3, 4 or 5)", N);
+    if (N == 5 && D != 3) return fail(NPCF_ERR_UNSUPPORTED, "N=5 is provided for D=3 only");
+    if (N == 5 && lmax > 6) return fail(NPCF_ERR_UNSUPPORTED, "N=5 supports lmax <= 6");
+    if (N == 5 && nbins < 4) return fail(NPCF_ERR_ARG, "N=5 needs at least 4 bins");
     if (N == 4 && D == 4) return fail(NPCF_ERR_UNSUPPORTED, "N=4 needs the SO(4) coupling, not provided");
     if (lmax < 0) return fail(NPCF_ERR_ARG, "lmax must be >= 0");
     if (N == 4 && D == 3 && lmax > couple_max_lmax_d3n4())
@@ -1098,10 +1175,10 @@ npcf_status npcf_coeff_index(npcf_plan_t P, int64_t i, int* bins, int* ells)
 {
     if (!P || !bins || !ells) return fail(NPCF_ERR_ARG, "NULL argument");
     if (i < 0 || i >= P->ncoeff) return fail(NPCF_ERR_ARG, "index %lld out of range", (long long)i);
-    for (int k = 0; k < P->N - 1; ++k) bins[k] = P->key_bins[3 * i + k];
+    for (int k = 0; k < P->N - 1; ++k) bins[k] = P->key_bins[4 * i + k];
     const int il = P->key_lam[i];
-    const int ne = P->N == 3 ? 1 : 3;
-    for (int k = 0; k < ne; ++k) ells[k] = P->lam[3 * il + k];
+    const int ne = P->N == 3 ? 1 : (P->N == 4 ? 3 : 5);
+    for (int k = 0; k < ne; ++k) ells[k] = P->lam[5 * il + k];
     return NPCF_OK;
 }
 
@@ -1247,7 +1324,8 @@ void npcf_plan_destroy(npcf_plan_t P)
                       &P->w_rec,   &P->w_cells, &P->w_items, &P->w_a,     &P->w_wprim,   &P->w_partial,
                       &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout,  &P->d_keybase, &P->w_cbuf,
                       &P->w_gpos,  &P->w_gw,    &P->w_gwp,   &P->d_geo,   &P->b_geo,     &P->b_cells,
-                      &P->b_offsets, &P->b_first, &P->b_count, &P->b_scales, &P->b_stencil};
+                      &P->b_offsets, &P->b_first, &P->b_count, &P->b_scales, &P->b_stencil,
+                      &P->d_triples, &P->d_lam5, &P->d_terms5, &P->d_coef5};
     for (DevBuf* b : bufs) b->release();
     if (P->h_small) cudaFreeHost(P->h_small);
     for (auto& e : P->ev)
@@ -1437,7 +1515,12 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     kp.lam2 = P->d_lam2.as<int2>();
     kp.lam_odd = P->d_lamodd.as<signed char>();
     kp.pref = P->d_pref.p;
-    kp.group = d2n4_group(P->nbins, P->lmax);
+    kp.group = P->N == 5 ? d3n5_group(P->nbins, P->lmax, P->fp64) : d2n4_group(P->nbins, P->lmax);
+    kp.ntriple = (int)P->triples.size();
+    kp.triples = P->d_triples.as<int4>();
+    kp.lam5 = P->d_lam5.as<int4>();
+    kp.terms5 = P->d_terms5.as<int>();
+    kp.coef5 = P->d_coef5.as<double>();
     kp.ncat = 1;
     CUDA_TRY(cudaMemsetAsync(partial, 0, row_bytes * rows, s));
     e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);

@@ -131,19 +131,22 @@ class Plan:
 
     # ------------------------------------------------------------------
     def keys(self) -> np.ndarray:
-        """(ncoeff, 6) int array: b1, b2, b3 (-1 if unused), l1, l2, l3 (0 if unused)."""
+        """Output labels, one row per coefficient: (b1, b2, b3, l1, l2, l3) for N <= 4 (b3 = -1 and
+        l2 = l3 = 0 when unused); (b1, b2, b3, b4, l1, l2, l12, l3, l4) for N = 5."""
         if self._keys is None:
             lib = load_library()
-            k = np.zeros((self.ncoeff, 6), dtype=np.int32)
-            k[:, 2] = -1
-            bins = (ctypes.c_int * 3)()
-            ells = (ctypes.c_int * 3)()
+            nb, ne = (4, 5) if self.N == 5 else (3, 3)
+            k = np.zeros((self.ncoeff, nb + ne), dtype=np.int32)
+            k[:, nb - 1] = -1
+            bins = (ctypes.c_int * 4)()
+            ells = (ctypes.c_int * 5)()
+            nl = {3: 1, 4: 3, 5: 5}[self.N]
             for i in range(self.ncoeff):
                 _check(lib.npcf_coeff_index(self._h, i, bins, ells))
                 for a in range(self.N - 1):
                     k[i, a] = bins[a]
-                for a in range(1 if self.N == 3 else 3):
-                    k[i, 3 + a] = ells[a]
+                for a in range(nl):
+                    k[i, nb + a] = ells[a]
             self._keys = k
         return self._keys
 

@@ -73,7 +73,10 @@ def _create(lib, D, N, lmax, edges, box, opts=None):
     "D,N,lmax,edges,box,opts,status",
     [
         (5, 3, 2, [0.1, 0.2], [1] * 5, None, -2),  # dimension
-        (3, 5, 2, [0.1, 0.2], [1] * 3, None, -2),  # order
+        (3, 6, 2, [0.1, 0.2], [1] * 3, None, -2),  # order
+        (2, 5, 2, [0.1, 0.2, 0.3, 0.4, 0.45], [1] * 2, None, -2),  # N=5 is provided for D=3
+        (3, 5, 7, [0.1, 0.2, 0.3, 0.4, 0.45], [1] * 3, None, -2),  # N=5 lmax limit
+        (3, 5, 2, [0.1, 0.2, 0.3], [1] * 3, None, -1),  # N=5 needs 4 bins
         (4, 4, 2, [0.1, 0.2, 0.3, 0.4], [1] * 4, None, -2),  # N=4 in D=4 needs an SO(4) coupling
         (3, 4, 7, [0.1, 0.2, 0.3, 0.4], [1] * 3, None, -2),  # lmax beyond the compiled coupling
         (3, 3, 2, list(np.linspace(0.01, 0.3, 40)), [1] * 3, None, -2),  # more than 32 bins

@@ -15,6 +15,7 @@ def test_coupling_terms_per_primary():
     assert bench.coupling_terms_per_primary(3, 4, 5, 10) == math.comb(10, 3) * 3555
     assert bench.coupling_terms_per_primary(3, 4, 4, 8) == math.comb(8, 3) * 1439
     assert bench.coupling_terms_per_primary(2, 4, 10, 16) == math.comb(16, 3) * 176
+    assert bench.coupling_terms_per_primary(3, 5, 4, 10) == math.comb(10, 4) * 61749
     # N=3: one term per (l, m) per bin pair with b1 <= b2
     assert bench.coupling_terms_per_primary(3, 3, 5, 10) == 36 * 55
 
