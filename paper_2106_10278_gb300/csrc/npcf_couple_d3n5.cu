@@ -95,7 +95,9 @@ __global__ void __launch_bounds__(256) k_couple_d3n5(const CoupleParams p)
                         const int pk = p.terms5[e];
                         if ((signed char)((pk >> 24) & 0xff) != m4) break;
                         const Cx5<T> x = u1[pk & 0xff], y = u2[(pk >> 8) & 0xff], z = u3[(pk >> 16) & 0xff];
-                        const T c = (T)p.coef5[e];
+                        T c;
+                        if constexpr (sizeof(T) == 4) c = p.coef5f[e];
+                        else c = p.coef5[e];
                         const T xyr = x.r * y.r - x.i * y.i, xyi = x.r * y.i + x.i * y.r;
                         qr = fma(c, xyr * z.r - xyi * z.i, qr);
                         qi = fma(c, xyr * z.i + xyi * z.r, qi);

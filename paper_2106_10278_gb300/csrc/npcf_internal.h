@@ -106,6 +106,7 @@ struct CoupleParams {
     const int4* lam5;          // N=5: (first term, end term, l4, 0) per label set
     const int* terms5;         // N=5: state(l1,m1) | state(l2,m2) << 8 | state(l3,m3) << 16 | m4 << 24
     const double* coef5;       // N=5: the coupling coefficient of each term
+    const float* coef5f;       // N=5: the same in FP32 (FP32 plans)
     int ncat;                  // catalogues (blockIdx.z); 0 or 1 for a single one
     const int* cat_first;      // ncat: first primary of each catalogue in the a-array (NULL: one catalogue)
     const int* cat_count;      // ncat: its primaries

@@ -113,7 +113,7 @@ struct npcf_plan_s {
     PairParams pp{};
     // device tables
     DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil, d_task;
-    DevBuf d_triples, d_lam5, d_terms5, d_coef5;  // N=5 coupling tables
+    DevBuf d_triples, d_lam5, d_terms5, d_coef5, d_coef5f;  // N=5 coupling tables
     // workspace
     DevBuf w_cid, w_perm, w_rec, w_cells, w_items, w_a, w_wprim, w_partial, w_small, w_hpos, w_hw, w_hout;
     // adjoint (npcf_backward)
@@ -615,6 +615,7 @@ npcf_status setup_tables(npcf_plan_s* P)
         CUDA_TRY(upload(P->d_lam5, lam5));
         CUDA_TRY(upload(P->d_terms5, terms));
         CUDA_TRY(upload(P->d_coef5, coef));
+        CUDA_TRY(upload(P->d_coef5f, cast_vec<float>(coef)));
         CUDA_TRY(upload(P->d_triples, P->triples));
         CoupleParams cp{};
         cp.N = 5;
@@ -744,6 +745,7 @@ CoupleParams couple_params(const npcf_plan_s* P, const void* a, const void* wpri
     kp.lam5 = P->d_lam5.as<int4>();
     kp.terms5 = P->d_terms5.as<int>();
     kp.coef5 = P->d_coef5.as<double>();
+    kp.coef5f = P->d_coef5f.as<float>();
     kp.ncat = 1;
     return kp;
 }
@@ -1325,7 +1327,7 @@ void npcf_plan_destroy(npcf_plan_t P)
                       &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout,  &P->d_keybase, &P->w_cbuf,
                       &P->w_gpos,  &P->w_gw,    &P->w_gwp,   &P->d_geo,   &P->b_geo,     &P->b_cells,
                       &P->b_offsets, &P->b_first, &P->b_count, &P->b_scales, &P->b_stencil,
-                      &P->d_triples, &P->d_lam5, &P->d_terms5, &P->d_coef5};
+                      &P->d_triples, &P->d_lam5, &P->d_terms5, &P->d_coef5, &P->d_coef5f};
     for (DevBuf* b : bufs) b->release();
     if (P->h_small) cudaFreeHost(P->h_small);
     for (auto& e : P->ev)
@@ -1521,6 +1523,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     kp.lam5 = P->d_lam5.as<int4>();
     kp.terms5 = P->d_terms5.as<int>();
     kp.coef5 = P->d_coef5.as<double>();
+    kp.coef5f = P->d_coef5f.as<float>();
     kp.ncat = 1;
     CUDA_TRY(cudaMemsetAsync(partial, 0, row_bytes * rows, s));
     e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
