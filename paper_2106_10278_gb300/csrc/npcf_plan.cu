@@ -854,9 +854,9 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     const int nkb = (int)P->kblocks.size();
     int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
     if (d2n4_registers(P)) rows = P->nsm;
-    if (P->N == 5) {  // groups of d3n5_group primaries; each partial row holds every coefficient
+    if (P->N == 5) {  // groups of d3n5_group primaries (up to 3 CTAs per SM); a partial row holds every coefficient
         const int G = d3n5_group(P->nbins, P->lmax, P->fp64);
-        rows = (int)std::min<int64_t>(P->nsm, std::max<int64_t>(1, (nprim_max + G - 1) / G));
+        rows = (int)std::min<int64_t>(3 * P->nsm, std::max<int64_t>(1, (nprim_max + G - 1) / G));
     }
     rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, P->N == 5 ? rows : (nprim_max + chunk - 1) / chunk));
     if ((st = reserve_workspace(P, n, nprim_max, rows, P->ncells)) != NPCF_OK) return st;
