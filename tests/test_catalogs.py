@@ -1,0 +1,51 @@
+"""The seeded input generators: every position is FP32-representable and inside [0, L) (so the
+FP32 device copy and the FP64 oracle copy are the same points), draws are reproducible, and the
+named workloads carry the stated parameters."""
+import numpy as np
+
+from paper_2106_10278_gb300 import catalogs
+
+
+def _fp32_in_box(x, L):
+    L = np.broadcast_to(np.asarray(L, dtype=np.float64), (x.shape[1],))
+    assert np.all(x >= 0.0) and np.all(x < L)
+    assert np.array_equal(x.astype(np.float32).astype(np.float64), x)
+
+
+def test_generators_fp32_in_box_and_reproducible():
+    u = catalogs.uniform(5000, 3, [1.0, 2.0, 0.5], 7)
+    _fp32_in_box(u, [1.0, 2.0, 0.5])
+    assert np.array_equal(u, catalogs.uniform(5000, 3, [1.0, 2.0, 0.5], 7))
+    b = catalogs.gaussian_blobs(5000, 4, 1.0, 20, 0.05, 8)
+    _fp32_in_box(b, 1.0)
+    ln = catalogs.lognormal_poisson(2e4, 300.0, 9, grid=32)
+    _fp32_in_box(ln, 300.0)
+    assert abs(len(ln) - 2e4) < 5 * np.sqrt(2e4)  # Poisson total around the mean
+    w = catalogs.normal_weights(1000, 1.0, 0.1, 3)
+    assert np.array_equal(w.astype(np.float32).astype(np.float64), w)
+
+
+def test_named_workloads():
+    wl = catalogs.workload("d3n5", scale=0.1)
+    assert (wl.D, wl.N, wl.lmax) == (3, 5, 4)
+    np.testing.assert_allclose(wl.edges, np.linspace(0.1, 0.4, 11))
+    assert np.all(wl.box == 1.0) and wl.n == 1000
+    _fp32_in_box(wl.pos, wl.box)
+    wl = catalogs.workload("d3n4", scale=0.01)
+    assert (wl.D, wl.N, wl.lmax) == (3, 4, 5)
+    np.testing.assert_allclose(wl.edges, np.linspace(20.0, 160.0, 11))
+    assert set(np.unique(wl.w)) == {-1.0, 1.0}  # data +1, randoms -1
+    _fp32_in_box(wl.pos, wl.box)
+    wl = catalogs.workload("d4n3", scale=0.05)
+    assert (wl.D, wl.N, wl.lmax) == (4, 3, 4)
+    np.testing.assert_allclose(wl.edges, np.linspace(0.01, 0.12, 9))
+
+
+def test_batch_layout():
+    bw = catalogs.batch64(ncat=3, scale=0.02)
+    assert bw.ncat == 3 and bw.offsets[0] == 0 and bw.offsets[-1] == len(bw.pos)
+    assert np.all(np.diff(bw.offsets) > 0)
+    assert np.all((bw.boxes >= 500.0) & (bw.boxes <= 1000.0))
+    for i in range(bw.ncat):
+        p, w, box = bw.catalogue(i)
+        _fp32_in_box(p, box)
