@@ -65,6 +65,8 @@ def _load():
         lib.npcf_oracle_coupling.argtypes = [_i32, _i32, _i32, _i32, _pi, _pd]
         lib.npcf_oracle_estimate.argtypes = [_i32, _i32, _i32, _i32, _i32, _pd, _pd, _i32, _pd, _pd, _i64,
                                              _i64, _i64, _i32, _pd]
+        lib.npcf_oracle_estimate_ex.argtypes = [_i32, _i32, _i32, _i32, _i32, _pd, _pd, _i32, _pd, _pd, _i64,
+                                                _i64, _i64, _i32, _i32, _pd]
         lib.npcf_oracle_n3_closed.argtypes = [_i32, _i32, _i32, _i32, _pd, _pd, _i32, _pd, _pd, _i64, _i64,
                                               _i64, _pd, _pd, _pd, _pd]
         _lib = lib
@@ -151,7 +153,8 @@ def _prep(pos, w, edges, box):
     return pos, w, edges, box
 
 
-def estimate(D, N, lmax, edges, box, pos, w, *, periodic=True, primaries=None, brute=False, bin_lt=False):
+def estimate(D, N, lmax, edges, box, pos, w, *, periodic=True, primaries=None, brute=False, bin_lt=False,
+             remove_self=False):
     """The isotropic NPCF coefficients zeta^{0,b}_Lambda (N = 3: D = 2..4; N = 4: D = 2, 3;
     N = 5: D = 3, lmax <= 6).
 
@@ -159,6 +162,8 @@ def estimate(D, N, lmax, edges, box, pos, w, *, periodic=True, primaries=None, b
     brute=True:  the naive sum over N-tuplets, eq. NPCF-estimator-intro-discrete
                  with the basis of eq. B-hypersph.
     primaries: (begin, end) range of primary particles (all particles are secondaries).
+    remove_self: exclude the tuples whose secondaries coincide (only N=3 keys with b1 = b2 have
+                 them); by default they are kept, as in the naive N-tuplet sum.
     Returns (keys, complex coefficients) in the oracle's key order.
     """
     lib = _load()
@@ -168,8 +173,8 @@ def estimate(D, N, lmax, edges, box, pos, w, *, periodic=True, primaries=None, b
     nbins = len(edges) - 1
     k = keys(D, N, lmax, nbins, bin_lt)
     out = np.zeros((k.shape[0], 2))
-    rc = lib.npcf_oracle_estimate(D, N, lmax, nbins, int(bin_lt), _dp(edges), _dp(box), int(periodic),
-                                  _dp(pos), _dp(w), n, pb, pe, int(brute), _dp(out))
+    rc = lib.npcf_oracle_estimate_ex(D, N, lmax, nbins, int(bin_lt), _dp(edges), _dp(box), int(periodic),
+                                     _dp(pos), _dp(w), n, pb, pe, int(brute), int(remove_self), _dp(out))
     if rc < 0:
         raise ValueError(f"oracle estimate failed ({rc})")
     return k, out[:, 0] + 1j * out[:, 1]

@@ -26,7 +26,8 @@
  *   R1 the self pair k=j and any pair with r=0 exactly are skipped (Y(0) is
  *      undefined);
  *   R2 degenerate tuples (two secondaries equal) are kept, as in the naive
- *      sum over all N-tuplets;
+ *      sum over all N-tuplets; on request (remove_self) they are excluded
+ *      exactly, which concerns only N=3 keys with b1 = b2;
  *   R3 bins are half-open [e_b, e_{b+1}), decided by comparing the FP64 r^2
  *      with the FP64 square of the edge;
  *   R4 v_b is the volume of the shell, |S^{D-1}|/D (e_{b+1}^D - e_b^D);
@@ -622,9 +623,27 @@ static int key_lambda(const okey_t *k, const lam_t *lam, int nl)
  * Primaries are j in [pb, pe); secondaries are all particles.
  * out: 2*nkeys doubles (re, im), overwritten.
  */
+int npcf_oracle_estimate_ex(int D, int N, int lmax, int nbins, int bin_lt, const double *edges,
+                            const double *box, int periodic, const double *pos, const double *w, int64_t n,
+                            int64_t pb, int64_t pe, int brute, int remove_self, double *out);
+
 int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const double *edges,
                          const double *box, int periodic, const double *pos, const double *w, int64_t n,
                          int64_t pb, int64_t pe, int brute, double *out)
+{
+    return npcf_oracle_estimate_ex(D, N, lmax, nbins, bin_lt, edges, box, periodic, pos, w, n, pb, pe, brute, 0, out);
+}
+
+/*
+ * remove_self = 1 excludes the tuples whose secondaries coincide (reading R2 keeps them by
+ * default, as the naive sum of eq. NPCF-estimator-intro-discrete does).  Only N=3 keys with
+ * b1 = b2 have such tuples (N=4, 5 keys have strictly ordered bins):
+ * the separable form subtracts, per primary, sum_{k in b} w_k^2 sum_terms C Y*_s1 Y*_s2 / v_b^2;
+ * the naive form skips k = k'.
+ */
+int npcf_oracle_estimate_ex(int D, int N, int lmax, int nbins, int bin_lt, const double *edges,
+                            const double *box, int periodic, const double *pos, const double *w, int64_t n,
+                            int64_t pb, int64_t pe, int brute, int remove_self, double *out)
 {
     if (!supported(D, N, lmax, nbins)) return -1;
     if (pb < 0 || pe > n || pb > pe) return -2;
@@ -658,6 +677,7 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
 
     cplx *zeta = (cplx *)calloc(nk, sizeof(cplx));
     cplx *a = (cplx *)malloc(sizeof(cplx) * nbins * ns);
+    cplx *self = (cplx *)malloc(sizeof(cplx) * nbins * (nl > 0 ? nl : 1)); /* N=3 coincident terms */
     /* neighbour lists for the naive sum */
     int64_t *nb_idx = NULL;
     int *nb_bin = NULL;
@@ -673,12 +693,21 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
         const double *yj = pos + j * D;
         if (!brute) {
             for (int i = 0; i < nbins * ns; ++i) a[i] = 0.0;
+            for (int i = 0; i < nbins * nl; ++i) self[i] = 0.0;
             for (int64_t k = 0; k < n; ++k) {
                 if (k == j) continue;
                 separation(D, pos + k * D, yj, box, periodic, d);
                 int b = bin_of(norm2(D, d), nbins, edges);
                 if (b < 0) continue;
                 for (int s = 0; s < ns; ++s) a[b * ns + s] += w[k] * conj(harmonic(D, &st[s], d));
+                if (remove_self && N == 3)
+                    for (int il = 0; il < nl; ++il) {
+                        cplx t = 0.0;
+                        for (int q = tstart[il]; q < tstart[il + 1]; ++q)
+                            t += terms[q].c * conj(harmonic(D, &st[terms[q].s[0]], d)) *
+                                 conj(harmonic(D, &st[terms[q].s[1]], d));
+                        self[b * nl + il] += w[k] * w[k] * t;
+                    }
             }
             for (int b = 0; b < nbins; ++b)
                 for (int s = 0; s < ns; ++s) a[b * ns + s] /= vb[b];
@@ -691,6 +720,8 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
                     if (N == 5) p *= a[kk->b[3] * ns + terms[t].s[3]];
                     acc += p;
                 }
+                if (remove_self && N == 3 && kk->b[0] == kk->b[1])
+                    acc -= self[kk->b[0] * nl + klam[i]] / (vb[kk->b[0]] * vb[kk->b[0]]);
                 zeta[i] += w[j] * acc;
             }
         } else {
@@ -712,6 +743,7 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
                     if (nb_bin[p1] != kk->b[0]) continue;
                     for (int64_t p2 = 0; p2 < nn; ++p2) {
                         if (nb_bin[p2] != kk->b[1]) continue;
+                        if (remove_self && p2 == p1) continue;
                         if (N == 3) {
                             cplx P = 0.0;
                             for (int t = tstart[klam[i]]; t < tstart[klam[i] + 1]; ++t)
@@ -754,7 +786,7 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
         out[2 * i] = creal(zeta[i]) / V;
         out[2 * i + 1] = cimag(zeta[i]) / V;
     }
-    free(zeta); free(a); free(keys); free(klam); free(terms); free(tstart); free(lam); free(st);
+    free(zeta); free(a); free(self); free(keys); free(klam); free(terms); free(tstart); free(lam); free(st);
     free(nb_idx); free(nb_bin); free(nb_y);
     return nk;
 }

@@ -338,6 +338,57 @@ def test_separable_equals_naive_sum(D, N, lmax, nb):
     np.testing.assert_allclose(z1, z2, rtol=0, atol=1e-12 * scale)
 
 
+@pytest.mark.parametrize("D", [2, 3, 4])
+def test_remove_self_equals_naive_sum_over_distinct_secondaries(D):
+    """Excluding coincident secondaries (k = k', only on N=3 keys with b1 = b2): the separable
+    form minus its degenerate term equals the naive pair sum that skips k = k', and the amount
+    removed is the basis at coincident directions, (-1)^l sqrt(dim_l)/|S^{D-1}| for D >= 3 and
+    1/(2 pi) for D = 2, times (1/V) sum_j w_j sum_{k in b} w_k^2 / v_b^2 (numpy below)."""
+    lmax, nb = {2: 5, 3: 4, 4: 3}[D], 3
+    pos, w = _tiny(D, 50, 1.0, 70 + D)
+    edges = np.linspace(0.08, 0.45, nb + 1)
+    box = np.ones(D)
+    prim = (0, 20)
+    k0, z_keep = oracle.estimate(D, 3, lmax, edges, box, pos, w, primaries=prim)
+    k1, z_rm = oracle.estimate(D, 3, lmax, edges, box, pos, w, primaries=prim, remove_self=True)
+    k2, z_rm_naive = oracle.estimate(D, 3, lmax, edges, box, pos, w, primaries=prim, brute=True, remove_self=True)
+    assert np.array_equal(k0, k1) and np.array_equal(k1, k2)
+    scale = np.max(np.abs(z_keep))
+    np.testing.assert_allclose(z_rm, z_rm_naive, rtol=0, atol=1e-12 * scale)
+
+    area = {2: 2 * np.pi, 3: 4 * np.pi, 4: 2 * np.pi ** 2}[D]
+    vb = area / D * (edges[1:] ** D - edges[:-1] ** D)
+    if D == 2:
+        coinc = [1.0 / (2 * np.pi)] * (lmax + 1)
+    else:
+        dim = [2 * l + 1 if D == 3 else (l + 1) ** 2 for l in range(lmax + 1)]
+        coinc = [(-1) ** l * math.sqrt(dim[l]) / area for l in range(lmax + 1)]
+    s2 = np.zeros(nb)
+    for j in range(*prim):
+        d = pos - pos[j]
+        d -= np.round(d)
+        r = np.linalg.norm(d, axis=1)
+        b = np.searchsorted(edges, r, side="right") - 1
+        ok = (np.arange(len(pos)) != j) & (b >= 0) & (b < nb)
+        for bb in range(nb):
+            s2[bb] += w[j] * np.sum(w[ok][b[ok] == bb] ** 2)
+    ref = np.array([s2[k[0]] * coinc[k[3]] / vb[k[0]] ** 2 if k[0] == k[1] else 0.0 for k in k0])
+    assert np.count_nonzero(ref) > 0
+    np.testing.assert_allclose(z_keep - z_rm, ref, rtol=0, atol=1e-12 * scale)
+
+
+def test_remove_self_changes_nothing_without_coincident_bins():
+    """Keys with strictly ordered bins (N=4, or N=3 with b1 < b2) have no coincident secondaries."""
+    pos, w = _tiny(3, 30, 1.0, 90)
+    edges = np.linspace(0.05, 0.45, 5)
+    _, z = oracle.estimate(3, 4, 2, edges, np.ones(3), pos, w, primaries=(0, 8))
+    _, zr = oracle.estimate(3, 4, 2, edges, np.ones(3), pos, w, primaries=(0, 8), remove_self=True)
+    assert np.array_equal(z, zr)
+    _, z = oracle.estimate(3, 3, 3, edges, np.ones(3), pos, w, primaries=(0, 8), bin_lt=True)
+    _, zr = oracle.estimate(3, 3, 3, edges, np.ones(3), pos, w, primaries=(0, 8), bin_lt=True, remove_self=True)
+    assert np.array_equal(z, zr)
+
+
 def test_d3_3pcf_legendre_closed_form():
     """D=3, N=3: the basis is the Legendre polynomial rescaled by (-1)^l 4pi/sqrt(2l+1)
     (text after eq. zero-ang-mom-states), so zeta_l equals
