@@ -25,7 +25,10 @@
  *   - N=3 keys: b1 <= b2 (NPCF_BINS_LE) or b1 < b2 (NPCF_BINS_LT), l = 0..lmax;
  *     N=4 keys: b1 < b2 < b3 and, for D=3, (l1, l2, l3) <= lmax obeying the
  *     triangle rule (both parities); for D=2, signed (l1, l2, l3) with
- *     l1 + l2 + l3 = 0, 0 <= l1 <= lmax, |l2|, |l3| <= lmax.
+ *     l1 + l2 + l3 = 0, 0 <= l1 <= lmax, |l2|, |l3| <= lmax;
+ *     N=5 keys (D=3): b1 < b2 < b3 < b4 and labels (l1, l2, l12, l3, l4) <= lmax
+ *     with (l1, l2, l12), (l12, l3, l4) obeying the triangle rule and
+ *     l1 + l2 + l3 + l4 even.
  *
  * Ownership: the caller owns every data buffer; the plan owns its tables and
  * device workspace.  All pointers named "device" must be device memory of the
@@ -81,7 +84,7 @@ NPCF_API void npcf_default_opts(npcf_opts* opts);
 
 /*
  * Build a plan (host call; allocates the coupling tables on the current device).
- *   D, N, lmax : dimension (2..4), order (3 or 4), maximum total angular momentum.
+ *   D, N, lmax : dimension (2..4), order (3, 4 or 5), maximum total angular momentum.
  *   bin_edges  : host, nbins+1 ascending edges, bin_edges[0] >= 0; r_max = bin_edges[nbins].
  *   box        : host, D side lengths (> 0).  Required in both modes (gives V_D).
  *   opts       : host, may be NULL for the defaults.
