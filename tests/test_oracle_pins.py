@@ -121,6 +121,41 @@ def test_harmonics_addition_theorem(D, lmax):
         assert dim == np.count_nonzero(sel)
 
 
+def _rotate_plane(x, a, b, t):
+    y = x.copy()
+    c, s = math.cos(t), math.sin(t)
+    y[:, a] = c * x[:, a] - s * x[:, b]
+    y[:, b] = s * x[:, a] + c * x[:, b]
+    return y
+
+
+@pytest.mark.parametrize("D,lmax", [(2, 6), (3, 5), (4, 4)])
+def test_harmonics_casimir_eigenvalues_of_every_label(D, lmax):
+    """Every label of the chain is an eigenvalue label: the Laplacian of the sub-sphere S^K
+    spanned by coordinates 1..K+1, written as the sum of squared rotation generators L_ab,
+    a < b <= K+1, has Y as eigenfunction with eigenvalue -l_K (l_K + K - 1) (-l_1^2 for K = 1).
+    For K = D-1 this is the Casimir of eq. single-particle-eigenfun.  The second derivatives along
+    exact plane rotations are central differences with one Richardson step."""
+    x = np.random.default_rng(5).normal(size=(25, D))
+    Y = oracle.harmonics(D, lmax, x)
+    st = oracle.states(D, lmax)
+
+    def casimir(K, h):
+        acc = np.zeros_like(Y)
+        for b in range(1, K + 1):
+            for a in range(b):
+                acc += (oracle.harmonics(D, lmax, _rotate_plane(x, a, b, h)) - 2 * Y
+                        + oracle.harmonics(D, lmax, _rotate_plane(x, a, b, -h))) / h ** 2
+        return acc
+
+    h = 2e-2
+    for K in range(1, D):
+        lK = st[:, K - 1].astype(np.float64)
+        eig = -(lK * (lK + K - 1))
+        got = (4 * casimir(K, h / 2) - casimir(K, h)) / 3
+        np.testing.assert_allclose(got, eig[None, :] * Y, rtol=0, atol=2e-5)
+
+
 def test_harmonics_conjugation_and_parity():
     """eq. complex-conj-hypersph: Y* = (-1)^{l_1} Y_{-l_1...} (D>=3) and P[Y] = (-1)^{l_{D-1}} Y."""
     for D, lmax in [(3, 5), (4, 4)]:
@@ -532,6 +567,39 @@ def test_translation_and_rotation_invariance():
     _, zo = oracle.estimate(D, 4, 2, edges, np.ones(D), pos, w, periodic=False)
     _, zr = oracle.estimate(D, 4, 2, edges, np.ones(D), pos @ R.T, w, periodic=False)
     np.testing.assert_allclose(zr, zo, atol=1e-11 * np.max(np.abs(zo)))
+
+
+def test_periodic_cube_symmetries():
+    """The 48 signed axis permutations map the periodic unit cube onto itself: the 24 rotations
+    leave every D=3 4PCF coefficient unchanged; the 24 improper ones keep the even-parity
+    coefficients and flip the odd ones (eq. basis-parity-conj).  The 5PCF keeps only even
+    parity, so all 48 leave it unchanged."""
+    import itertools
+
+    pos, w = _tiny(3, 36, 1.0, 65)
+    edges = np.linspace(0.05, 0.45, 4)
+    keys, z = oracle.estimate(3, 4, 2, edges, np.ones(3), pos, w)
+    odd = (keys[:, 3] + keys[:, 4] + keys[:, 5]) % 2 == 1
+    scale = np.max(np.abs(z))
+    p5, w5 = _tiny(3, 24, 1.0, 66)
+    e5 = np.linspace(0.05, 0.45, 5)
+    _, z5 = oracle.estimate(3, 5, 2, e5, np.ones(3), p5, w5, primaries=(0, 6))
+    s5 = np.max(np.abs(z5))
+    assert s5 > 0 and np.any(odd)
+    count = 0
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1.0, -1.0), repeat=3):
+            M = np.zeros((3, 3))
+            for i in range(3):
+                M[i, perm[i]] = signs[i]
+            proper = np.linalg.det(M) > 0
+            _, zc = oracle.estimate(3, 4, 2, edges, np.ones(3), np.mod(pos @ M.T, 1.0), w)
+            expect = z if proper else np.where(odd, -z, z)
+            np.testing.assert_allclose(zc, expect, rtol=0, atol=1e-11 * scale)
+            _, zc5 = oracle.estimate(3, 5, 2, e5, np.ones(3), np.mod(p5 @ M.T, 1.0), w5, primaries=(0, 6))
+            np.testing.assert_allclose(zc5, z5, rtol=0, atol=1e-11 * s5)
+            count += 1
+    assert count == 48
 
 
 @pytest.mark.parametrize("D,N", [(3, 4), (2, 4), (2, 3)])
