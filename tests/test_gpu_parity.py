@@ -201,9 +201,26 @@ def test_host_entry_point_matches_device_entry_point():
 
 # ------------------------------------------- full-size workloads, sampled primaries
 @pytest.mark.parametrize("name,prims", [("d3n4", (0, 6)), ("d3n4", (1_000_100, 1_000_104)), ("d2n4", (0, 400)),
-                                        ("d2n3", (0, 3000)), ("d4n3", (0, 2000))])
+                                        ("d2n3", (0, 3000)), ("d4n3", (0, 2000)), ("d3n5", (0, 8))])
 def test_full_size_workload_sampled_primaries(name, prims):
     """The benchmark workloads at full size (same cell grid and launch as the
     benchmark), compared on a sample of primaries the oracle can afford."""
     wl = catalogs.workload(name)
     _compare(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, "fp32", primaries=prims)
+
+
+@pytest.mark.parametrize("name", ["d3n4", "d3n5"])
+def test_full_size_launch_equals_sum_of_ranges(name):
+    """The benchmark's own launch (every primary of the full-size workload, its coupling grid
+    and cross-CTA reduce) against two half-range calls: the coefficients are sums over
+    primaries, so the two must agree to FP32 rounding of the per-group sums."""
+    wl = catalogs.workload(name)
+    plan = _plan(wl.D, wl.N, wl.lmax, wl.edges, wl.box, "fp32")
+    pos = torch.tensor(wl.pos, dtype=torch.float32, device="cuda")
+    w = torch.tensor(wl.w, dtype=torch.float32, device="cuda")
+    full = plan.compute(pos, w).cpu().numpy()
+    half = wl.n // 2
+    parts = plan.compute(pos, w, primaries=(0, half)).cpu().numpy() + \
+        plan.compute(pos, w, primaries=(half, wl.n)).cpu().numpy()
+    err, scale = np.linalg.norm(full - parts), np.linalg.norm(full)
+    assert scale > 0 and err <= TOL32 * scale, f"rel err {err / scale:.3e}"
