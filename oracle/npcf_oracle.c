@@ -107,27 +107,33 @@ static double ferrers_int(int n, int mu, double x)
     return sgn_pow(m) * fact(n - m) / fact(n + m) * ferrers_int(n, m, x);
 }
 
-/* P^{-(k+1/2)}_{nu}(cos th) for half-odd degree nu = L + 1/2 and integer
- * k >= 0: the elementary forms DLMF 14.5.11 (mu = +1/2) and 14.5.12
- * (mu = -1/2), then the order recurrence DLMF 14.10.1 run downwards. */
+/* sin^{-1/2}(th) P^{-(k+1/2)}_{L+1/2}(cos th) for integers 0 <= k <= L.
+ * With mu = k + 1/2, the hypergeometric factor of DLMF 14.3.1 is (1-z)^mu when
+ * the degree equals minus the order, so P^{-mu}_{mu}(x) = (1-x^2)^{mu/2} /
+ * (2^mu Gamma(1+mu)), i.e. sin^{-1/2} P^{-mu}_{mu} = sin^k / (2^mu Gamma(1+mu));
+ * the degree recurrence DLMF 14.10.3, run upwards,
+ *   (nu - m + 1) P^m_{nu+1} = (2 nu + 1) x P^m_nu - (nu + m) P^m_{nu-1}   (m = -mu),
+ * whose last term vanishes at the first step, carries it to nu = L + 1/2.
+ * The factor sin^{-1/2} is linear in the recurrence, so nothing is singular at
+ * the poles (th = 0, pi), and the upward degree recurrence is stable there. */
+static double ferrers_half_reg(int L, int k, double th)
+{
+    double mu = k + 0.5, m = -mu, x = cos(th);
+    double prev = 0.0;
+    double cur = pow(sin(th), (double)k) / (pow(2.0, mu) * tgamma(1.0 + mu));
+    for (int step = k; step < L; ++step) { /* cur holds degree nu = step + 1/2 */
+        double nu = step + 0.5;
+        double next = ((2.0 * nu + 1.0) * x * cur - (nu + m) * prev) / (nu - m + 1.0);
+        prev = cur;
+        cur = next;
+    }
+    return cur;
+}
+
+/* P^{-(k+1/2)}_{L+1/2}(cos th) for 0 < th < pi (the D=4 factor of eq. hypersph-def) */
 static double ferrers_half(int L, int k, double th)
 {
-    double nu = L + 0.5;
-    double s = sin(th), x = cos(th);
-    double pre = sqrt(2.0 / (M_PI * s));
-    double p_up = pre * cos((nu + 0.5) * th);               /* mu = +1/2 */
-    double p_lo = pre * sin((nu + 0.5) * th) / (nu + 0.5);  /* mu = -1/2 */
-    if (k == 0) return p_lo;
-    double mu = -0.5;
-    for (int step = 1; step <= k; ++step) {
-        double m = mu - 1.0; /* new, lower order */
-        /* P^{m+2} + 2(m+1) x (1-x^2)^{-1/2} P^{m+1} + (nu-m)(nu+m+1) P^m = 0 */
-        double p_new = -(p_up + 2.0 * (m + 1.0) * x / s * p_lo) / ((nu - m) * (nu + m + 1.0));
-        p_up = p_lo;
-        p_lo = p_new;
-        mu = m;
-    }
-    return p_lo;
+    return sqrt(sin(th)) * ferrers_half_reg(L, k, th);
 }
 
 /* ------------------------------------------------------------------ */
@@ -169,7 +175,13 @@ static int enum_states(int D, int lmax, state_t *out)
  * Theta_1 = e^{i l_1 th_1}/sqrt(2 pi) (the D=2 form printed with the
  * paper's two- and three-dimensional harmonics) and, for 2 <= K <= D-1,
  * Theta_K = sqrt((2 l_K + K - 1)/2 (l_K + l_{K-1} + K - 2)!/(l_K - l_{K-1})!)
- *           sin^{1-K/2}(th_K) P^{-(l_{K-1}+K/2-1)}_{l_K+K/2-1}(cos th_K). */
+ *           sin^{1-K/2}(th_K) P^{-(l_{K-1}+K/2-1)}_{l_K+K/2-1}(cos th_K).
+ * For odd K the factor sin^{1-K/2} P is formed as sin^{(3-K)/2} times
+ * sin^{-1/2} P, which is regular at the poles.  Where x_1..x_{K+1} are all
+ * zero (lattice directions such as (0, 0, 0, 1)) th_K is undefined: the first
+ * factor above it with a non-zero component is proportional to
+ * sin^{l_{K'-1}}(th_{K'}) = 0 unless every lower label vanishes, in which case
+ * Theta_K does not depend on th_K; th_K = pi/2 is taken. */
 static cplx harmonic(int D, const state_t *s, const double *d)
 {
     double th1 = atan2(d[1], d[0]);
@@ -177,7 +189,7 @@ static cplx harmonic(int D, const state_t *s, const double *d)
     double rho2 = d[0] * d[0] + d[1] * d[1];
     for (int K = 2; K <= D - 1; ++K) {
         double rhoK2 = rho2 + d[K] * d[K];          /* |x_{1..K+1}|^2 */
-        double cth = d[K] / sqrt(rhoK2);
+        double cth = rhoK2 > 0.0 ? d[K] / sqrt(rhoK2) : 0.0;
         if (cth > 1.0) cth = 1.0;
         if (cth < -1.0) cth = -1.0;
         double th = acos(cth);
@@ -193,7 +205,7 @@ static cplx harmonic(int D, const state_t *s, const double *d)
             /* half-odd degree and order: K/2 - 1 = (K-3)/2 + 1/2 */
             int h = (K - 3) / 2;
             norm = sqrt((2.0 * lK + K - 1) / 2.0 * fact(lK + lKm1 + K - 2) / fact(lK - lKm1));
-            val = pow(sin(th), 1.0 - 0.5 * K) * ferrers_half(lK + h, lKm1 + h, th);
+            val = pow(sin(th), 1.5 - 0.5 * K) * ferrers_half_reg(lK + h, lKm1 + h, th);
         }
         y *= norm * val;
         rho2 = rhoK2;
@@ -976,3 +988,4 @@ int npcf_oracle_n3_closed(int D, int lmax, int nbins, int bin_lt, const double *
     free(zeta); free(kidx); free(nb_idx); free(nb_bin); free(nb_u); free(nb_r);
     return nk;
 }
+

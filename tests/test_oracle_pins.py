@@ -121,6 +121,22 @@ def test_harmonics_addition_theorem(D, lmax):
         assert dim == np.count_nonzero(sel)
 
 
+@pytest.mark.parametrize("D", [3, 4])
+def test_harmonics_continuous_at_axis_directions(D):
+    """Grid offsets hit the axes, where an angle of eq. hypersph-def is undefined or a factor
+    is 0 x infinity: the values there are finite and are the limits of nearby directions."""
+    lmax = 5
+    axes = np.vstack([np.eye(D), -np.eye(D), np.eye(D)[[0]] + np.eye(D)[[D - 1]]] +
+                     ([np.array([[0.0, 0.0, 2.0, 3.0], [0.0, 0.0, -1.0, -2.0]])] if D == 4 else []))
+    Y = oracle.harmonics(D, lmax, axes)
+    assert np.all(np.isfinite(Y))
+    g = np.random.default_rng(0)
+    for eps in (1e-7, 1e-9):
+        for _ in range(10):
+            near = oracle.harmonics(D, lmax, axes + eps * g.normal(size=axes.shape))
+            assert np.max(np.abs(near - Y)) < 100 * eps
+
+
 def _rotate_plane(x, a, b, t):
     y = x.copy()
     c, s = math.cos(t), math.sin(t)
