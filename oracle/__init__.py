@@ -69,6 +69,8 @@ def _load():
                                                 _i64, _i64, _i32, _i32, _pd]
         lib.npcf_oracle_n3_closed.argtypes = [_i32, _i32, _i32, _i32, _pd, _pd, _i32, _pd, _pd, _i64, _i64,
                                               _i64, _pd, _pd, _pd, _pd]
+        lib.npcf_oracle_grid_alm.argtypes = [_i32, _i32, _i32, _pd, _pd, _pi, _pd, _pd]
+        lib.npcf_oracle_grid_estimate.argtypes = [_i32, _i32, _i32, _i32, _i32, _pd, _pd, _pi, _pd, _pd]
         _lib = lib
         return lib
 
@@ -214,3 +216,43 @@ def estimate_n3_closed(D, lmax, edges, box, pos, w, *, periodic=True, primaries=
     if rc < 0:
         raise ValueError(f"oracle failed ({rc})")
     return k, out[:, 0] + 1j * out[:, 1], gpos, gw
+
+
+def _prep_grid(X, edges, box):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    D = X.ndim
+    box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (D,)))
+    dims = np.ascontiguousarray(X.shape, dtype=np.int32)
+    return X, np.ascontiguousarray(edges, dtype=np.float64), box, dims
+
+
+def grid_alm(lmax, edges, box, X):
+    """a^b_l(s) of eq. alm-bin-def at every node of a periodic grid field X (a D-dimensional
+    array over a box of sides `box`), as the direct sum over node offsets (Sec. "Application to
+    Gridded Data", reading R16).  Returns complex (ncell, nbins, nstates), nodes in row-major
+    order, states in the order of states()."""
+    lib = _load()
+    X, edges, box, dims = _prep_grid(X, edges, box)
+    D, nbins = X.ndim, len(edges) - 1
+    ns = lib.npcf_oracle_nstates(D, lmax)
+    out = np.zeros((X.size, nbins, ns, 2))
+    rc = lib.npcf_oracle_grid_alm(D, lmax, nbins, _dp(edges), _dp(box), _ip(dims), _dp(X), _dp(out))
+    if rc < 0:
+        raise ValueError(f"oracle failed ({rc})")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def estimate_grid(N, lmax, edges, box, X, *, bin_lt=False):
+    """The isotropic NPCF coefficients of a periodic grid field X (eq. NPCF-mult-estimator with the
+    spatial integral as a sum over nodes, Sec. "Application to Gridded Data"): keys as in keys(),
+    coefficients complex."""
+    lib = _load()
+    X, edges, box, dims = _prep_grid(X, edges, box)
+    D, nbins = X.ndim, len(edges) - 1
+    k = keys(D, N, lmax, nbins, bin_lt)
+    out = np.zeros((k.shape[0], 2))
+    rc = lib.npcf_oracle_grid_estimate(D, N, lmax, nbins, int(bin_lt), _dp(edges), _dp(box), _ip(dims), _dp(X),
+                                       _dp(out))
+    if rc < 0:
+        raise ValueError(f"oracle failed ({rc})")
+    return k, out[:, 0] + 1j * out[:, 1]

@@ -20,6 +20,9 @@
  *                                                               with eq. B-hypersph)
  *   - the N=3 estimator through the addition theorem, with its analytic
  *     gradient in positions and weights                        (Sec. "Derivation", eq. zeta-basis-decomp)
+ *   - the estimator of a field on a periodic grid, by direct sums over node
+ *     offsets                                                  (Sec. "Application to Gridded Data",
+ *                                                               eq. alm-bin-def, eq. NPCF-mult-estimator)
  *
  * Readings of the paper that this file takes where the text is silent or
  * garbled (every one is also listed in the design notes):
@@ -40,7 +43,14 @@
  *   R15 the D=3 5PCF (eq. D=3-NPCF, intermediate label l12) keeps the even-parity labels
  *      (l1+l2+l3+l4 even), which give the 585 angular components the paper counts for
  *      lmax=4; its printed coefficient sqrt(2 l12 - 1) is read as sqrt(2 l12 + 1), the
- *      value the CG chain of eq. Coupling-C gives.
+ *      value the CG chain of eq. Coupling-C gives;
+ *   R16 gridded data: the integrals over space and over the separation become
+ *      sums over grid nodes times the node volume; a^b_l keeps the 1/v_b of
+ *      eq. alm-bin-def (the FFT form printed for grids drops it) with v_b the
+ *      shell volume of R4; the separation o = 0 is skipped as in R1.  The FFT
+ *      form's kernel is read as Y*_l Theta^b: relabelling r -> -r in
+ *      eq. alm-bin-def moves the parity sign (-1)^{l_{D-1}} out but leaves the
+ *      conjugate on Y (the kernel printed as Y_l Theta^b gives other values).
  *
  * Floating point: compile with -ffp-contract=off so that no multiply-add is
  * fused; r^2 is formed as ((dx*dx + dy*dy) + dz*dz) + ... left to right.
@@ -989,3 +999,178 @@ int npcf_oracle_n3_closed(int D, int lmax, int nbins, int bin_lt, const double *
     return nk;
 }
 
+/* ------------------------------------------------------------------ */
+/* Gridded data (Sec. "Application to Gridded Data").                   */
+/*
+ * The field X is given at the nodes of a periodic grid with dims[a] nodes
+ * along axis a of a box of sides box[a] (spacing h_a = box[a]/dims[a], node
+ * volume dV = prod_a h_a; row-major storage, last axis fastest).  The
+ * integrals of eq. alm-bin-def and eq. NPCF-mult-estimator become sums over
+ * nodes times dV (reading R16):
+ *   a^b_l(s) = (1/v_b) sum_{o != 0} dV X(s + o h) Y*_l(unit(o h)) Theta^b(|o h|),
+ *   zeta     = (1/V_D) sum_s dV X(s) sum_[l] C prod_i a^{b_i}_{l^i}(s),
+ * o running over integer offset vectors, node indices taken modulo dims, v_b
+ * the shell volume of R4, the offset o = 0 skipped as R1 skips r = 0.  This
+ * direct sum over offsets is the plain definition; the FFT form of the paper
+ * evaluates the same circular convolution.  Every offset within r_max must
+ * reach a distinct node: 2 floor(r_max/h_a) < dims[a].
+ */
+typedef struct {
+    int64_t o[OR_MAXD];
+    int b;
+} goff_t;
+
+/* offsets within the bins and the conjugate harmonics there; returns the count or < 0 */
+static int64_t grid_offsets(int D, int lmax, int nbins, const double *edges, const double *box,
+                            const int *dims, goff_t **offs_out, cplx **yc_out)
+{
+    double h[OR_MAXD];
+    int64_t K[OR_MAXD], span = 1;
+    double rmax = edges[nbins];
+    for (int a = 0; a < D; ++a) {
+        if (dims[a] < 1 || !(box[a] > 0.0)) return -1;
+        h[a] = box[a] / dims[a];
+        K[a] = (int64_t)floor(rmax / h[a]);
+        if (2 * K[a] >= dims[a]) return -2;
+        span *= 2 * K[a] + 1;
+    }
+    int ns = enum_states(D, lmax, NULL);
+    state_t *st = (state_t *)malloc(sizeof(state_t) * ns);
+    enum_states(D, lmax, st);
+    goff_t *offs = (goff_t *)malloc(sizeof(goff_t) * span);
+    cplx *yc = (cplx *)malloc(sizeof(cplx) * span * ns);
+    int64_t nof = 0;
+    double d[OR_MAXD];
+    for (int64_t t = 0; t < span; ++t) {
+        int64_t rem = t;
+        goff_t g;
+        for (int a = D - 1; a >= 0; --a) {
+            g.o[a] = rem % (2 * K[a] + 1) - K[a];
+            rem /= 2 * K[a] + 1;
+            d[a] = (double)g.o[a] * h[a];
+        }
+        double r2 = norm2(D, d);
+        if (r2 == 0.0) continue;
+        g.b = bin_of(r2, nbins, edges);
+        if (g.b < 0) continue;
+        offs[nof] = g;
+        for (int s = 0; s < ns; ++s) yc[nof * ns + s] = conj(harmonic(D, &st[s], d));
+        ++nof;
+    }
+    free(st);
+    *offs_out = offs;
+    *yc_out = yc;
+    return nof;
+}
+
+/* a^b_l at every node: out is ncell x nbins x nstates complex (re, im interleaved) */
+static int grid_alm(int D, int lmax, int nbins, const double *edges, const double *box, const int *dims,
+                    const double *X, cplx *a)
+{
+    goff_t *offs;
+    cplx *yc;
+    int64_t nof = grid_offsets(D, lmax, nbins, edges, box, dims, &offs, &yc);
+    if (nof < 0) return (int)nof;
+    int ns = enum_states(D, lmax, NULL);
+    int64_t ncell = 1;
+    double dV = 1.0;
+    for (int a = 0; a < D; ++a) {
+        ncell *= dims[a];
+        dV *= box[a] / dims[a];
+    }
+    double vb[OR_MAXB];
+    for (int b = 0; b < nbins; ++b)
+        vb[b] = sphere_area(D) / D * (pow(edges[b + 1], (double)D) - pow(edges[b], (double)D));
+    int64_t c[OR_MAXD];
+    for (int64_t cell = 0; cell < ncell; ++cell) {
+        int64_t rem = cell;
+        for (int a = D - 1; a >= 0; --a) {
+            c[a] = rem % dims[a];
+            rem /= dims[a];
+        }
+        cplx *ac = a + cell * nbins * ns;
+        for (int i = 0; i < nbins * ns; ++i) ac[i] = 0.0;
+        for (int64_t q = 0; q < nof; ++q) {
+            int64_t idx = 0;
+            for (int a = 0; a < D; ++a) {
+                int64_t x = (c[a] + offs[q].o[a]) % dims[a];
+                if (x < 0) x += dims[a];
+                idx = idx * dims[a] + x;
+            }
+            double f = dV * X[idx];
+            for (int s = 0; s < ns; ++s) ac[offs[q].b * ns + s] += f * yc[q * ns + s];
+        }
+        for (int b = 0; b < nbins; ++b)
+            for (int s = 0; s < ns; ++s) ac[b * ns + s] /= vb[b];
+    }
+    free(offs);
+    free(yc);
+    return 0;
+}
+
+int npcf_oracle_grid_alm(int D, int lmax, int nbins, const double *edges, const double *box, const int *dims,
+                         const double *X, double *out)
+{
+    if (D < 2 || D > 4 || !supported(D, 3, lmax, nbins)) return -1;
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b + 1] > edges[b]) || edges[b] < 0.0) return -3;
+    return grid_alm(D, lmax, nbins, edges, box, dims, X, (cplx *)out);
+}
+
+int npcf_oracle_grid_estimate(int D, int N, int lmax, int nbins, int bin_lt, const double *edges,
+                              const double *box, const int *dims, const double *X, double *out)
+{
+    if (!supported(D, N, lmax, nbins)) return -1;
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b + 1] > edges[b]) || edges[b] < 0.0) return -3;
+    int ns = enum_states(D, lmax, NULL);
+    int64_t ncell = 1;
+    double dV = 1.0, V = 1.0;
+    for (int a = 0; a < D; ++a) {
+        if (dims[a] < 1) return -2;
+        ncell *= dims[a];
+        dV *= box[a] / dims[a];
+        V *= box[a];
+    }
+    cplx *a = (cplx *)malloc(sizeof(cplx) * ncell * nbins * ns);
+    int rc = grid_alm(D, lmax, nbins, edges, box, dims, X, a);
+    if (rc < 0) {
+        free(a);
+        return rc - 10;
+    }
+    int nl = enum_lambdas(D, N, lmax, NULL);
+    lam_t *lam = (lam_t *)malloc(sizeof(lam_t) * nl);
+    enum_lambdas(D, N, lmax, lam);
+    int *tstart = (int *)malloc(sizeof(int) * (nl + 1));
+    tstart[0] = 0;
+    for (int i = 0; i < nl; ++i) tstart[i + 1] = tstart[i] + lambda_terms(D, N, lmax, &lam[i], NULL);
+    term_t *terms = (term_t *)malloc(sizeof(term_t) * (tstart[nl] > 0 ? tstart[nl] : 1));
+    for (int i = 0; i < nl; ++i) lambda_terms(D, N, lmax, &lam[i], terms + tstart[i]);
+    int nk = enum_keys(D, N, lmax, nbins, bin_lt, NULL);
+    okey_t *keys = (okey_t *)malloc(sizeof(okey_t) * nk);
+    enum_keys(D, N, lmax, nbins, bin_lt, keys);
+    int *klam = (int *)malloc(sizeof(int) * nk);
+    for (int i = 0; i < nk; ++i) klam[i] = key_lambda(&keys[i], lam, nl);
+
+    cplx *zeta = (cplx *)calloc(nk, sizeof(cplx));
+    for (int64_t cell = 0; cell < ncell; ++cell) {
+        const cplx *ac = a + cell * nbins * ns;
+        for (int i = 0; i < nk; ++i) {
+            const okey_t *kk = &keys[i];
+            cplx acc = 0.0;
+            for (int t = tstart[klam[i]]; t < tstart[klam[i] + 1]; ++t) {
+                cplx p = terms[t].c * ac[kk->b[0] * ns + terms[t].s[0]] * ac[kk->b[1] * ns + terms[t].s[1]];
+                if (N >= 4) p *= ac[kk->b[2] * ns + terms[t].s[2]];
+                if (N == 5) p *= ac[kk->b[3] * ns + terms[t].s[3]];
+                acc += p;
+            }
+            zeta[i] += dV * X[cell] * acc;
+        }
+    }
+    for (int i = 0; i < nk; ++i) {
+        out[2 * i] = creal(zeta[i]) / V;
+        out[2 * i + 1] = cimag(zeta[i]) / V;
+    }
+    free(a); free(zeta); free(keys); free(klam); free(terms); free(tstart); free(lam);
+    return nk;
+}
