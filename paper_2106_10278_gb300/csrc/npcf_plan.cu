@@ -1208,7 +1208,11 @@ npcf_status npcf_compute_host(npcf_plan_t P, const void* pos, const void* w, int
                               int64_t pb, int64_t pe, npcf_stream_t stream)
 {
     if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
-    if (n < 0 || !coeffs || (n > 0 && (!pos || !w))) return fail(NPCF_ERR_ARG, "bad arguments");
+    if (n < 0 || n > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)n);
+    if (!coeffs || (n > 0 && (!pos || !w))) return fail(NPCF_ERR_ARG, "bad arguments");
+    if (pb == 0 && pe == 0) pe = n;
+    if (pb < 0 || pe > n || pb > pe) return fail(NPCF_ERR_ARG, "primary range [%lld, %lld) outside [0, %lld)",
+                                                 (long long)pb, (long long)pe, (long long)n);
     npcf_status st = ensure_device(P);
     if (st != NPCF_OK) return st;
     const size_t tb = P->fp64 ? 8 : 4;
@@ -1221,8 +1225,6 @@ npcf_status npcf_compute_host(npcf_plan_t P, const void* pos, const void* w, int
         CUDA_TRY(cudaMemcpyAsync(P->w_hpos.p, pos, tb * P->D * n, cudaMemcpyHostToDevice, s));
         CUDA_TRY(cudaMemcpyAsync(P->w_hw.p, w, tb * n, cudaMemcpyHostToDevice, s));
     }
-    if (pb == 0 && pe == 0) pe = n;
-    if (pb < 0 || pe > n || pb > pe) return fail(NPCF_ERR_ARG, "bad primary range");
     st = run(P, P->w_hpos.p, P->w_hw.p, n, P->w_hout.as<double>(), pb, pe, s);
     if (st != NPCF_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(coeffs, P->w_hout.p, sizeof(double) * 2 * P->ncoeff, cudaMemcpyDeviceToHost, s));
