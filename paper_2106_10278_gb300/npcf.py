@@ -106,6 +106,8 @@ class Plan:
 
     def __init__(self, D, N, lmax, edges, box, *, precision="fp32", periodic=True, bin_lt=False, sync_check=True,
                  timing=False):
+        if precision not in ("fp32", "fp64"):
+            raise ValueError(f"precision must be 'fp32' or 'fp64', not {precision!r}")
         lib = load_library()
         self.D, self.N, self.lmax = int(D), int(N), int(lmax)
         self.edges = np.ascontiguousarray(edges, dtype=np.float64)

@@ -111,3 +111,10 @@ def test_null_arguments(lib):
     assert lib.npcf_last_counters(None, None, 0) == -1
     assert b"NULL" in lib.npcf_last_error()
     lib.npcf_plan_destroy(None)  # a no-op
+
+
+def test_binding_rejects_unknown_precision():
+    from paper_2106_10278_gb300.npcf import Plan
+
+    with pytest.raises(ValueError):
+        Plan(3, 3, 2, [0.1, 0.2], 1.0, precision="bf16")
