@@ -69,6 +69,8 @@ def _load():
                                                 _i64, _i64, _i32, _i32, _pd]
         lib.npcf_oracle_n3_closed.argtypes = [_i32, _i32, _i32, _i32, _pd, _pd, _i32, _pd, _pd, _i64, _i64,
                                               _i64, _pd, _pd, _pd, _pd]
+        lib.npcf_oracle_sphere_estimate.argtypes = [_i32, _i32, _i32, _i32, _pd, _pd, _pd, _i64, _i64, _i64, _i32,
+                                                    _pd]
         lib.npcf_oracle_grid_alm.argtypes = [_i32, _i32, _i32, _pd, _pd, _pi, _pd, _pd]
         lib.npcf_oracle_grid_estimate.argtypes = [_i32, _i32, _i32, _i32, _i32, _pd, _pd, _pi, _pd, _pd]
         _lib = lib
@@ -253,6 +255,27 @@ def estimate_grid(N, lmax, edges, box, X, *, bin_lt=False):
     out = np.zeros((k.shape[0], 2))
     rc = lib.npcf_oracle_grid_estimate(D, N, lmax, nbins, int(bin_lt), _dp(edges), _dp(box), _ip(dims), _dp(X),
                                        _dp(out))
+    if rc < 0:
+        raise ValueError(f"oracle failed ({rc})")
+    return k, out[:, 0] + 1j * out[:, 1]
+
+
+def estimate_sphere(N, lmax, cos_edges, pos, w, *, primaries=None, brute=False, bin_lt=False):
+    """The isotropic NPCF of points on the unit 2-sphere (Sec. "Cosmic Microwave Background"):
+    the D = 2 basis about every primary, radial bins [c_b, c_{b+1}) in cos(theta) (reading R17),
+    1/(4 pi) in place of 1/V.  pos: (n, 3) directions (normalised by the oracle).  Keys as in
+    keys(2, N, ...); N = 3 or 4."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    cos_edges = np.ascontiguousarray(cos_edges, dtype=np.float64)
+    n = pos.shape[0]
+    pb, pe = (0, n) if primaries is None else primaries
+    nbins = len(cos_edges) - 1
+    k = keys(2, N, lmax, nbins, bin_lt)
+    out = np.zeros((k.shape[0], 2))
+    rc = lib.npcf_oracle_sphere_estimate(N, lmax, nbins, int(bin_lt), _dp(cos_edges), _dp(pos), _dp(w), n, pb, pe,
+                                         int(brute), _dp(out))
     if rc < 0:
         raise ValueError(f"oracle failed ({rc})")
     return k, out[:, 0] + 1j * out[:, 1]

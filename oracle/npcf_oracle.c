@@ -23,6 +23,8 @@
  *   - the estimator of a field on a periodic grid, by direct sums over node
  *     offsets                                                  (Sec. "Application to Gridded Data",
  *                                                               eq. alm-bin-def, eq. NPCF-mult-estimator)
+ *   - the estimator of points on the 2-sphere with the D = 2 basis about each
+ *     point                                                    (Sec. "Cosmic Microwave Background")
  *
  * Readings of the paper that this file takes where the text is silent or
  * garbled (every one is also listed in the design notes):
@@ -51,6 +53,13 @@
  *      form's kernel is read as Y*_l Theta^b: relabelling r -> -r in
  *      eq. alm-bin-def moves the parity sign (-1)^{l_{D-1}} out but leaves the
  *      conjugate on Y (the kernel printed as Y_l Theta^b gives other values).
+ *   R17 the 2-sphere: the radial coordinate is the great-circle angle theta,
+ *      binned in half-open intervals of cos theta (the paper states its bins as
+ *      a range of cos theta); v_b is the area 2 pi (c_{b+1} - c_b) of the
+ *      annulus and 1/(4 pi) replaces 1/V; the azimuth is counter-clockwise
+ *      seen from outside the sphere (the flat D = 2 orientation at the north
+ *      pole); a^b_l uses Y*_l as in eq. NPCF-estimator-discrete (the section
+ *      prints e^{+il phi}, which would conjugate every coefficient).
  *
  * Floating point: compile with -ffp-contract=off so that no multiply-add is
  * fused; r^2 is formed as ((dx*dx + dy*dy) + dz*dz) + ... left to right.
@@ -536,6 +545,74 @@ static int bin_of(double r2, int nbins, const double *edges)
     return -1;
 }
 
+/*
+ * The geometry of one pair (j, k): the bin of the separation (-1 outside the
+ * bins, or at r = 0) and the direction handed to the harmonics.
+ *   - Euclidean box (D = 2..4): the minimum-image separation y_k - y_j, binned
+ *     on its squared length (readings R3, R7);
+ *   - the 2-sphere (Sec. "Cosmic Microwave Background", reading R17): the
+ *     radial coordinate is the great-circle angle theta between the unit
+ *     vectors n_j and n_k, binned on cos theta = n_j . n_k in half-open
+ *     intervals [c_b, c_{b+1}); the direction is the tangent vector
+ *     n_k - (n_j . n_k) n_j in a right-handed frame (e1, e2, n_j) at the
+ *     primary, so the D = 2 harmonics see the azimuth phi about n_j.  With
+ *     sum l = 0 the isotropic keys do not depend on the choice of e1.
+ */
+typedef struct {
+    int sphere;          /* 0: Euclidean box, 1: unit 2-sphere */
+    int Dp;              /* components of a position: D, or 3 on the sphere */
+    int Dh;              /* dimension of the harmonics: D, or 2 on the sphere */
+    int nbins;
+    const double *edges; /* radial edges (box) or cos(theta) edges (sphere) */
+    const double *box;
+    int periodic;
+    double e1[3], e2[3]; /* tangent frame at the current primary (sphere) */
+} geom_t;
+
+static void geom_primary(geom_t *g, const double *yj)
+{
+    if (!g->sphere) return;
+    /* e1: the coordinate axis least aligned with n_j, projected on the tangent plane */
+    int a0 = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(yj[a]) < fabs(yj[a0])) a0 = a;
+    double u[3] = {0.0, 0.0, 0.0};
+    u[a0] = 1.0;
+    double c = yj[a0], nu = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        u[a] -= c * yj[a];
+        nu += u[a] * u[a];
+    }
+    nu = sqrt(nu);
+    for (int a = 0; a < 3; ++a) g->e1[a] = u[a] / nu;
+    /* e2 = n_j x e1 */
+    g->e2[0] = yj[1] * g->e1[2] - yj[2] * g->e1[1];
+    g->e2[1] = yj[2] * g->e1[0] - yj[0] * g->e1[2];
+    g->e2[2] = yj[0] * g->e1[1] - yj[1] * g->e1[0];
+}
+
+static int geom_pair(const geom_t *g, const double *yk, const double *yj, double *d)
+{
+    if (!g->sphere) {
+        separation(g->Dp, yk, yj, g->box, g->periodic, d);
+        return bin_of(norm2(g->Dp, d), g->nbins, g->edges);
+    }
+    double c = (yk[0] * yj[0] + yk[1] * yj[1]) + yk[2] * yj[2];
+    if (c < g->edges[0]) return -1;
+    int b = -1;
+    for (int i = 0; i < g->nbins; ++i)
+        if (c < g->edges[i + 1]) {
+            b = i;
+            break;
+        }
+    if (b < 0) return -1;
+    double t[3];
+    for (int a = 0; a < 3; ++a) t[a] = yk[a] - c * yj[a];
+    d[0] = (t[0] * g->e1[0] + t[1] * g->e1[1]) + t[2] * g->e1[2];
+    d[1] = (t[0] * g->e2[0] + t[1] * g->e2[1]) + t[2] * g->e2[2];
+    return b;
+}
+
 /* ------------------------------------------------------------------ */
 /* Public entry points (C ABI, called from Python through ctypes).     */
 
@@ -663,6 +740,10 @@ int npcf_oracle_estimate(int D, int N, int lmax, int nbins, int bin_lt, const do
  * the separable form subtracts, per primary, sum_{k in b} w_k^2 sum_terms C Y*_s1 Y*_s2 / v_b^2;
  * the naive form skips k = k'.
  */
+static int estimate_core(const geom_t *g, int N, int lmax, int bin_lt, const double *pos, const double *w,
+                         int64_t n, int64_t pb, int64_t pe, int brute, int remove_self, const double *vb, double V,
+                         double *out);
+
 int npcf_oracle_estimate_ex(int D, int N, int lmax, int nbins, int bin_lt, const double *edges,
                             const double *box, int periodic, const double *pos, const double *w, int64_t n,
                             int64_t pb, int64_t pe, int brute, int remove_self, double *out)
@@ -671,7 +752,57 @@ int npcf_oracle_estimate_ex(int D, int N, int lmax, int nbins, int bin_lt, const
     if (pb < 0 || pe > n || pb > pe) return -2;
     for (int b = 0; b < nbins; ++b)
         if (!(edges[b + 1] > edges[b]) || edges[b] < 0.0) return -3;
+    double vb[OR_MAXB];
+    for (int b = 0; b < nbins; ++b)
+        vb[b] = sphere_area(D) / D * (pow(edges[b + 1], (double)D) - pow(edges[b], (double)D));
+    double V = 1.0;
+    for (int a = 0; a < D; ++a) V *= box[a];
+    geom_t g = {0, D, D, nbins, edges, box, periodic, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    return estimate_core(&g, N, lmax, bin_lt, pos, w, n, pb, pe, brute, remove_self, vb, V, out);
+}
 
+/*
+ * The isotropic NPCF of points on the unit 2-sphere (Sec. "Cosmic Microwave
+ * Background"): the D = 2 basis about every primary, radial bins in cos theta
+ * (reading R17),
+ *   zeta = (1/4pi) sum_j w_j sum_[l] C prod_i a^{b_i}_{l^i}(n_j),
+ *   a^b_l(n_j) = (1/v_b) sum_k w_k Y*_l(phi_jk) Theta^b(cos theta_jk),
+ * v_b = 2 pi (c_{b+1} - c_b) the area of the annulus, C the D = 2 coupling.
+ * pos: n x 3 directions (normalised here); cos_edges: nbins+1 ascending values
+ * with -1 < c_0 (the azimuth of an antipodal point is undefined) and c_nb <= 1.
+ */
+int npcf_oracle_sphere_estimate(int N, int lmax, int nbins, int bin_lt, const double *cos_edges,
+                                const double *pos, const double *w, int64_t n, int64_t pb, int64_t pe,
+                                int brute, double *out)
+{
+    if (N > 4 || !supported(2, N, lmax, nbins)) return -1;
+    if (pb < 0 || pe > n || pb > pe) return -2;
+    if (!(cos_edges[0] > -1.0) || cos_edges[nbins] > 1.0) return -3;
+    for (int b = 0; b < nbins; ++b)
+        if (!(cos_edges[b + 1] > cos_edges[b])) return -3;
+    double *u = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; ++k) {
+        double r = sqrt((pos[3 * k] * pos[3 * k] + pos[3 * k + 1] * pos[3 * k + 1]) + pos[3 * k + 2] * pos[3 * k + 2]);
+        if (!(r > 0.0)) {
+            free(u);
+            return -4;
+        }
+        for (int a = 0; a < 3; ++a) u[3 * k + a] = pos[3 * k + a] / r;
+    }
+    double vb[OR_MAXB];
+    for (int b = 0; b < nbins; ++b) vb[b] = 2.0 * M_PI * (cos_edges[b + 1] - cos_edges[b]);
+    geom_t g = {1, 3, 2, nbins, cos_edges, NULL, 0, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    int rc = estimate_core(&g, N, lmax, bin_lt, u, w, n, pb, pe, brute, 0, vb, 4.0 * M_PI, out);
+    free(u);
+    return rc;
+}
+
+static int estimate_core(const geom_t *g, int N, int lmax, int bin_lt, const double *pos, const double *w,
+                         int64_t n, int64_t pb, int64_t pe, int brute, int remove_self, const double *vb, double V,
+                         double *out)
+{
+    const int D = g->Dh, Dp = g->Dp, nbins = g->nbins;
+    geom_t gg = *g;
     int ns = enum_states(D, lmax, NULL);
     state_t *st = (state_t *)malloc(sizeof(state_t) * ns);
     enum_states(D, lmax, st);
@@ -691,12 +822,6 @@ int npcf_oracle_estimate_ex(int D, int N, int lmax, int nbins, int bin_lt, const
     int *klam = (int *)malloc(sizeof(int) * nk);
     for (int i = 0; i < nk; ++i) klam[i] = key_lambda(&keys[i], lam, nl);
 
-    double vb[OR_MAXB];
-    for (int b = 0; b < nbins; ++b)
-        vb[b] = sphere_area(D) / D * (pow(edges[b + 1], (double)D) - pow(edges[b], (double)D));
-    double V = 1.0;
-    for (int a = 0; a < D; ++a) V *= box[a];
-
     cplx *zeta = (cplx *)calloc(nk, sizeof(cplx));
     cplx *a = (cplx *)malloc(sizeof(cplx) * nbins * ns);
     cplx *self = (cplx *)malloc(sizeof(cplx) * nbins * (nl > 0 ? nl : 1)); /* N=3 coincident terms */
@@ -712,14 +837,14 @@ int npcf_oracle_estimate_ex(int D, int N, int lmax, int nbins, int bin_lt, const
 
     double d[OR_MAXD];
     for (int64_t j = pb; j < pe; ++j) {
-        const double *yj = pos + j * D;
+        const double *yj = pos + j * Dp;
+        geom_primary(&gg, yj);
         if (!brute) {
             for (int i = 0; i < nbins * ns; ++i) a[i] = 0.0;
             for (int i = 0; i < nbins * nl; ++i) self[i] = 0.0;
             for (int64_t k = 0; k < n; ++k) {
                 if (k == j) continue;
-                separation(D, pos + k * D, yj, box, periodic, d);
-                int b = bin_of(norm2(D, d), nbins, edges);
+                int b = geom_pair(&gg, pos + k * Dp, yj, d);
                 if (b < 0) continue;
                 for (int s = 0; s < ns; ++s) a[b * ns + s] += w[k] * conj(harmonic(D, &st[s], d));
                 if (remove_self && N == 3)
@@ -750,8 +875,7 @@ int npcf_oracle_estimate_ex(int D, int N, int lmax, int nbins, int bin_lt, const
             int64_t nn = 0;
             for (int64_t k = 0; k < n; ++k) {
                 if (k == j) continue;
-                separation(D, pos + k * D, yj, box, periodic, d);
-                int b = bin_of(norm2(D, d), nbins, edges);
+                int b = geom_pair(&gg, pos + k * Dp, yj, d);
                 if (b < 0) continue;
                 nb_idx[nn] = k;
                 nb_bin[nn] = b;

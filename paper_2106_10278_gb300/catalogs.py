@@ -52,6 +52,15 @@ def uniform(n: int, D: int, L, seed: int) -> np.ndarray:
     return _fp32_in_box(_rng(seed).random((n, D)) * L, L)
 
 
+def sphere_uniform(n: int, seed: int) -> np.ndarray:
+    """n directions uniform on the unit 2-sphere (normalised Gaussian 3-vectors), rounded to
+    FP32 so that an FP32 device copy holds the same vectors; their length is 1 up to FP32
+    rounding, and consumers normalise them."""
+    v = _rng(seed).normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v.astype(np.float32).astype(np.float64)
+
+
 def gaussian_blobs(n: int, D: int, L, n_centres: int, sigma: float, seed: int) -> np.ndarray:
     """n points in Gaussian blobs: centres uniform, membership multinomial, wrapped."""
     L = np.broadcast_to(np.asarray(L, dtype=np.float64), (D,))

@@ -25,6 +25,14 @@ def test_generators_fp32_in_box_and_reproducible():
     assert np.array_equal(w.astype(np.float32).astype(np.float64), w)
 
 
+def test_sphere_directions_fp32_and_unit():
+    v = catalogs.sphere_uniform(4000, 5)
+    assert np.array_equal(v.astype(np.float32).astype(np.float64), v)
+    np.testing.assert_allclose(np.linalg.norm(v, axis=1), 1.0, rtol=1e-6)
+    assert np.all(np.abs(v.mean(axis=0)) < 0.05)  # isotropic: no preferred direction
+    assert np.array_equal(v, catalogs.sphere_uniform(4000, 5))
+
+
 def test_named_workloads():
     wl = catalogs.workload("d3n5", scale=0.1)
     assert (wl.D, wl.N, wl.lmax) == (3, 5, 4)
