@@ -71,6 +71,10 @@ def _load():
                                               _i64, _pd, _pd, _pd, _pd]
         lib.npcf_oracle_sphere_estimate.argtypes = [_i32, _i32, _i32, _i32, _pd, _pd, _pd, _i64, _i64, _i64, _i32,
                                                     _pd]
+        lib.npcf_oracle_aniso_nkeys.argtypes = [_i32, _i32, _i32, _i32]
+        lib.npcf_oracle_aniso_keys.argtypes = [_i32, _i32, _i32, _i32, _pi]
+        lib.npcf_oracle_aniso_estimate.argtypes = [_i32, _i32, _i32, _i32, _pd, _pd, _i32, _pd, _pd, _i64, _i64, _i64,
+                                                   _i32, _pd]
         lib.npcf_oracle_grid_alm.argtypes = [_i32, _i32, _i32, _pd, _pd, _pi, _pd, _pd]
         lib.npcf_oracle_grid_estimate.argtypes = [_i32, _i32, _i32, _i32, _i32, _pd, _pd, _pi, _pd, _pd]
         _lib = lib
@@ -276,6 +280,38 @@ def estimate_sphere(N, lmax, cos_edges, pos, w, *, primaries=None, brute=False, 
     out = np.zeros((k.shape[0], 2))
     rc = lib.npcf_oracle_sphere_estimate(N, lmax, nbins, int(bin_lt), _dp(cos_edges), _dp(pos), _dp(w), n, pb, pe,
                                          int(brute), _dp(out))
+    if rc < 0:
+        raise ValueError(f"oracle failed ({rc})")
+    return k, out[:, 0] + 1j * out[:, 1]
+
+
+def aniso_keys(N: int, lmax: int, nbins: int, bin_lt: bool = False) -> np.ndarray:
+    """Labels of the anisotropic basis about the x_3 line of sight (reading R18), one row per
+    coefficient: (b1, b2, b3, l1, l2, L, 0, 0) for N = 3 (b3 = -1) and
+    (b1, b2, b3, l1, l2, l12, l3, L) for N = 4."""
+    lib = _load()
+    nk = lib.npcf_oracle_aniso_nkeys(N, lmax, nbins, int(bin_lt))
+    if nk < 0:
+        raise ValueError("unsupported anisotropic configuration")
+    out = np.zeros((nk, 8), dtype=np.int32)
+    lib.npcf_oracle_aniso_keys(N, lmax, nbins, int(bin_lt), _ip(out))
+    return out
+
+
+def estimate_aniso(N, lmax, edges, box, pos, w, *, periodic=True, primaries=None, brute=False, bin_lt=False):
+    """The D = 3 NPCF coefficients zeta^{0L}_Lambda of the basis invariant under rotations about the
+    x_3 axis (Sec. "Large-Scale Structure": the redshift-space 3PCF and its extension to N = 4),
+    keys as in aniso_keys()."""
+    lib = _load()
+    pos, w, edges, box = _prep(pos, w, edges, box)
+    box = np.ascontiguousarray(np.broadcast_to(box, (3,)))
+    n = pos.shape[0]
+    pb, pe = (0, n) if primaries is None else primaries
+    nbins = len(edges) - 1
+    k = aniso_keys(N, lmax, nbins, bin_lt)
+    out = np.zeros((k.shape[0], 2))
+    rc = lib.npcf_oracle_aniso_estimate(N, lmax, nbins, int(bin_lt), _dp(edges), _dp(box), int(periodic), _dp(pos),
+                                        _dp(w), n, pb, pe, int(brute), _dp(out))
     if rc < 0:
         raise ValueError(f"oracle failed ({rc})")
     return k, out[:, 0] + 1j * out[:, 1]

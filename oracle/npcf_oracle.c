@@ -25,6 +25,8 @@
  *                                                               eq. alm-bin-def, eq. NPCF-mult-estimator)
  *   - the estimator of points on the 2-sphere with the D = 2 basis about each
  *     point                                                    (Sec. "Cosmic Microwave Background")
+ *   - the D = 3 anisotropic basis about a fixed line of sight, N = 3, 4
+ *                                                              (Sec. "Large-Scale Structure")
  *
  * Readings of the paper that this file takes where the text is silent or
  * garbled (every one is also listed in the design notes):
@@ -60,6 +62,12 @@
  *      seen from outside the sphere (the flat D = 2 orientation at the north
  *      pole); a^b_l uses Y*_l as in eq. NPCF-estimator-discrete (the section
  *      prints e^{+il phi}, which would conjugate every coefficient).
+ *   R18 the anisotropic basis: the line of sight is the fixed x_3 axis (as
+ *      the paper sets it); N=3 labels (l1, l2, L) with every l1, l2 <= lmax
+ *      and every L of the triangle rule, coupled as printed for the
+ *      redshift-space 3PCF; N=4 labels (l1, l2, l12, l3, L) through
+ *      eq. Coupling-C with the final state (L, 0), l12 and L unbounded but for
+ *      the triangle rules; a uses Y* and 1/v_b as in the isotropic estimator.
  *
  * Floating point: compile with -ffp-contract=off so that no multiply-add is
  * fused; r^2 is formed as ((dx*dx + dy*dy) + dz*dz) + ... left to right.
@@ -1296,5 +1304,211 @@ int npcf_oracle_grid_estimate(int D, int N, int lmax, int nbins, int bin_lt, con
         out[2 * i + 1] = cimag(zeta[i]) / V;
     }
     free(a); free(zeta); free(keys); free(klam); free(terms); free(tstart); free(lam);
+    return nk;
+}
+
+/* ------------------------------------------------------------------ */
+/* Anisotropic basis about a fixed line of sight (Sec. "Large-Scale     */
+/* Structure"): D = 3, invariance under rotations about x_3 keeps the   */
+/* states of combined angular momentum (L_1, L_2) = (0, L) (reading R18) */
+/*
+ * Labels:  N=3: (l1, l2, L), l1, l2 <= lmax, |l1 - l2| <= L <= l1 + l2;
+ *          N=4: (l1, l2, l12, l3, L), l1, l2, l3 <= lmax, l12 and L by the
+ *               triangle rules of eq. addition-triangle-conditions.
+ * Coupling: N=3 as printed for the redshift-space 3PCF,
+ *               C = (-1)^{l2-l1} sqrt(2L+1) (l1 l2 L; m -m 0),
+ *           which is the CG <l1 m l2 -m|L 0>; N=4 by eq. Coupling-C with the
+ *           final state (L, 0): <l1 m1 l2 m2|l12 m12><l12 m12 l3 m3|L 0>.
+ * Bins as the isotropic keys: b1 <= b2 (or <) for N=3, b1 < b2 < b3 for N=4.
+ */
+typedef struct { int b[3]; int l[5]; } akey_t;
+
+static int enum_aniso_keys(int N, int lmax, int nbins, int bin_lt, akey_t *out)
+{
+    int c = 0;
+    if (N == 3) {
+        for (int b1 = 0; b1 < nbins; ++b1)
+            for (int b2 = b1 + (bin_lt ? 1 : 0); b2 < nbins; ++b2)
+                for (int l1 = 0; l1 <= lmax; ++l1)
+                    for (int l2 = 0; l2 <= lmax; ++l2)
+                        for (int L = abs(l1 - l2); L <= l1 + l2; ++L) {
+                            if (out) {
+                                akey_t k = {{b1, b2, -1}, {l1, l2, L, 0, 0}};
+                                out[c] = k;
+                            }
+                            ++c;
+                        }
+    } else {
+        for (int b1 = 0; b1 < nbins; ++b1)
+            for (int b2 = b1 + 1; b2 < nbins; ++b2)
+                for (int b3 = b2 + 1; b3 < nbins; ++b3)
+                    for (int l1 = 0; l1 <= lmax; ++l1)
+                        for (int l2 = 0; l2 <= lmax; ++l2)
+                            for (int l12 = abs(l1 - l2); l12 <= l1 + l2; ++l12)
+                                for (int l3 = 0; l3 <= lmax; ++l3)
+                                    for (int L = abs(l12 - l3); L <= l12 + l3; ++L) {
+                                        if (out) {
+                                            akey_t k = {{b1, b2, b3}, {l1, l2, l12, l3, L}};
+                                            out[c] = k;
+                                        }
+                                        ++c;
+                                    }
+    }
+    return c;
+}
+
+static int d3_state(int l, int m) { return l * l + l + m; }
+
+/* the non-zero terms (state indices s[0..N-2], C) of one anisotropic label set */
+static int aniso_terms(int N, const akey_t *k, term_t *out)
+{
+    int c = 0;
+    if (N == 3) {
+        int l1 = k->l[0], l2 = k->l[1], L = k->l[2];
+        for (int m = -l1; m <= l1; ++m) {
+            if (abs(m) > l2) continue;
+            double v = sgn_pow(abs(l2 - l1)) * sqrt(2.0 * L + 1.0) * wigner3j(l1, l2, L, m, -m, 0);
+            if (v == 0.0) continue;
+            if (out) {
+                term_t t = {{d3_state(l1, m), d3_state(l2, -m), 0, 0}, v};
+                out[c] = t;
+            }
+            ++c;
+        }
+    } else {
+        int l1 = k->l[0], l2 = k->l[1], l12 = k->l[2], l3 = k->l[3], L = k->l[4];
+        for (int m1 = -l1; m1 <= l1; ++m1)
+            for (int m2 = -l2; m2 <= l2; ++m2) {
+                int m12 = m1 + m2, m3 = -m12;
+                if (abs(m12) > l12 || abs(m3) > l3) continue;
+                double v = cg_d3(l1, m1, l2, m2, l12, m12) * cg_d3(l12, m12, l3, m3, L, 0);
+                if (v == 0.0) continue;
+                if (out) {
+                    term_t t = {{d3_state(l1, m1), d3_state(l2, m2), d3_state(l3, m3), 0}, v};
+                    out[c] = t;
+                }
+                ++c;
+            }
+    }
+    return c;
+}
+
+int npcf_oracle_aniso_nkeys(int N, int lmax, int nbins, int bin_lt)
+{
+    if ((N != 3 && N != 4) || lmax < 0 || lmax > OR_MAXL || nbins < 1 || nbins > OR_MAXB) return -1;
+    return enum_aniso_keys(N, lmax, nbins, bin_lt, NULL);
+}
+
+/* keys: nkeys x 8 ints (b1, b2, b3, l1, l2, l3, l4, l5) with the labels of the akey_t layout */
+int npcf_oracle_aniso_keys(int N, int lmax, int nbins, int bin_lt, int *keys)
+{
+    int nk = npcf_oracle_aniso_nkeys(N, lmax, nbins, bin_lt);
+    if (nk < 0) return nk;
+    akey_t *k = (akey_t *)malloc(sizeof(akey_t) * (nk > 0 ? nk : 1));
+    enum_aniso_keys(N, lmax, nbins, bin_lt, k);
+    for (int i = 0; i < nk; ++i) {
+        for (int a = 0; a < 3; ++a) keys[8 * i + a] = k[i].b[a];
+        for (int a = 0; a < 5; ++a) keys[8 * i + 3 + a] = k[i].l[a];
+    }
+    free(k);
+    return nk;
+}
+
+/*
+ * zeta^{0L}_Lambda(b) = (1/V) sum_j w_j sum_terms C prod_i a^{b_i}_{l^i m^i}(y_j),
+ * a from eq. NPCF-estimator-discrete (Y*, 1/v_b); brute = 1 sums the basis over
+ * every tuple of secondaries instead (eq. NPCF-intro-discrete with eq. B-hypersph).
+ */
+int npcf_oracle_aniso_estimate(int N, int lmax, int nbins, int bin_lt, const double *edges, const double *box,
+                               int periodic, const double *pos, const double *w, int64_t n, int64_t pb, int64_t pe,
+                               int brute, double *out)
+{
+    const int D = 3;
+    int nk = npcf_oracle_aniso_nkeys(N, lmax, nbins, bin_lt);
+    if (nk < 0) return -1;
+    if (pb < 0 || pe > n || pb > pe) return -2;
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b + 1] > edges[b]) || edges[b] < 0.0) return -3;
+    int ns = enum_states(D, lmax, NULL);
+    state_t *st = (state_t *)malloc(sizeof(state_t) * ns);
+    enum_states(D, lmax, st);
+    akey_t *keys = (akey_t *)malloc(sizeof(akey_t) * (nk > 0 ? nk : 1));
+    enum_aniso_keys(N, lmax, nbins, bin_lt, keys);
+    int *tstart = (int *)malloc(sizeof(int) * (nk + 1));
+    tstart[0] = 0;
+    for (int i = 0; i < nk; ++i) tstart[i + 1] = tstart[i] + aniso_terms(N, &keys[i], NULL);
+    term_t *terms = (term_t *)malloc(sizeof(term_t) * (tstart[nk] > 0 ? tstart[nk] : 1));
+    for (int i = 0; i < nk; ++i) aniso_terms(N, &keys[i], terms + tstart[i]);
+    double vb[OR_MAXB];
+    for (int b = 0; b < nbins; ++b)
+        vb[b] = sphere_area(D) / D * (pow(edges[b + 1], (double)D) - pow(edges[b], (double)D));
+    double V = box[0] * box[1] * box[2];
+
+    cplx *zeta = (cplx *)calloc(nk > 0 ? nk : 1, sizeof(cplx));
+    cplx *a = (cplx *)malloc(sizeof(cplx) * nbins * ns);
+    int64_t *nb_idx = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int *nb_bin = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+    cplx *nb_y = (cplx *)malloc(sizeof(cplx) * (n > 0 ? n : 1) * ns);
+    double d[OR_MAXD];
+    for (int64_t j = pb; j < pe; ++j) {
+        const double *yj = pos + j * D;
+        int64_t nn = 0;
+        for (int i = 0; i < nbins * ns; ++i) a[i] = 0.0;
+        for (int64_t k = 0; k < n; ++k) {
+            if (k == j) continue;
+            separation(D, pos + k * D, yj, box, periodic, d);
+            int b = bin_of(norm2(D, d), nbins, edges);
+            if (b < 0) continue;
+            nb_idx[nn] = k;
+            nb_bin[nn] = b;
+            for (int s = 0; s < ns; ++s) {
+                nb_y[nn * ns + s] = harmonic(D, &st[s], d);
+                a[b * ns + s] += w[k] * conj(nb_y[nn * ns + s]);
+            }
+            ++nn;
+        }
+        for (int b = 0; b < nbins; ++b)
+            for (int s = 0; s < ns; ++s) a[b * ns + s] /= vb[b];
+        for (int i = 0; i < nk; ++i) {
+            const akey_t *kk = &keys[i];
+            cplx acc = 0.0;
+            if (!brute) {
+                for (int t = tstart[i]; t < tstart[i + 1]; ++t) {
+                    cplx p = terms[t].c * a[kk->b[0] * ns + terms[t].s[0]] * a[kk->b[1] * ns + terms[t].s[1]];
+                    if (N == 4) p *= a[kk->b[2] * ns + terms[t].s[2]];
+                    acc += p;
+                }
+            } else {
+                for (int64_t p1 = 0; p1 < nn; ++p1) {
+                    if (nb_bin[p1] != kk->b[0]) continue;
+                    for (int64_t p2 = 0; p2 < nn; ++p2) {
+                        if (nb_bin[p2] != kk->b[1]) continue;
+                        if (N == 3) {
+                            cplx P = 0.0;
+                            for (int t = tstart[i]; t < tstart[i + 1]; ++t)
+                                P += terms[t].c * nb_y[p1 * ns + terms[t].s[0]] * nb_y[p2 * ns + terms[t].s[1]];
+                            acc += w[nb_idx[p1]] * w[nb_idx[p2]] * conj(P) / (vb[kk->b[0]] * vb[kk->b[1]]);
+                            continue;
+                        }
+                        for (int64_t p3 = 0; p3 < nn; ++p3) {
+                            if (nb_bin[p3] != kk->b[2]) continue;
+                            cplx P = 0.0;
+                            for (int t = tstart[i]; t < tstart[i + 1]; ++t)
+                                P += terms[t].c * nb_y[p1 * ns + terms[t].s[0]] * nb_y[p2 * ns + terms[t].s[1]] *
+                                     nb_y[p3 * ns + terms[t].s[2]];
+                            acc += w[nb_idx[p1]] * w[nb_idx[p2]] * w[nb_idx[p3]] * conj(P) /
+                                   (vb[kk->b[0]] * vb[kk->b[1]] * vb[kk->b[2]]);
+                        }
+                    }
+                }
+            }
+            zeta[i] += w[j] * acc;
+        }
+    }
+    for (int i = 0; i < nk; ++i) {
+        out[2 * i] = creal(zeta[i]) / V;
+        out[2 * i + 1] = cimag(zeta[i]) / V;
+    }
+    free(zeta); free(a); free(nb_idx); free(nb_bin); free(nb_y); free(keys); free(tstart); free(terms); free(st);
     return nk;
 }
