@@ -224,3 +224,32 @@ def test_full_size_launch_equals_sum_of_ranges(name):
         plan.compute(pos, w, primaries=(half, wl.n)).cpu().numpy()
     err, scale = np.linalg.norm(full - parts), np.linalg.norm(full)
     assert scale > 0 and err <= TOL32 * scale, f"rel err {err / scale:.3e}"
+
+
+# --------------------------- a field on a periodic grid, through the particle path
+GRID_FIELDS = [
+    # D, N, lmax, nodes per axis, edges
+    (2, 3, 6, 32, [0.07, 0.13, 0.2, 0.27, 0.33]),
+    (3, 4, 2, 16, [0.07, 0.13, 0.2, 0.27, 0.33]),
+    (4, 3, 3, 8, [0.13, 0.2, 0.3, 0.37]),
+    (3, 5, 2, 16, [0.09, 0.15, 0.22, 0.29, 0.36]),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("D,N,lmax,M,edges", GRID_FIELDS)
+def test_grid_field_as_lattice_particles(D, N, lmax, M, edges, precision):
+    """The gridded estimator's direct sums (Sec. "Application to Gridded Data") are the discrete
+    estimator of one particle per node with weight X dV.  The nodes put separations on the axes
+    (directions such as (0, 0, 0, 1)) and repeat every distance many times; the spacing is a power
+    of two, so positions and weights are exact in FP32, and no lattice distance lies on an edge."""
+    h = 1.0 / M
+    dV = h ** D
+    X = np.random.default_rng(40 + D + N).normal(size=(M,) * D)
+    w = (X * dV).astype(np.float32).astype(np.float64).reshape(-1)
+    pos = np.stack(np.indices((M,) * D), -1).reshape(-1, D) * h
+    edges = np.asarray(edges)
+    plan = _plan(D, N, lmax, edges, np.ones(D), precision)
+    got = _run(plan, pos, w)
+    keys, ref = oracle.estimate_grid(N, lmax, edges, 1.0, (w / dV).reshape((M,) * D))
+    _check(plan, got, _aligned_oracle(plan, keys, ref))
