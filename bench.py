@@ -37,6 +37,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "pairs/s and NPCF coeffs/s, 3D iso 4PCF n=1M, mixed vs FP32 at stated rel err"
+BATCH_METRIC = "pairs/s, batched D=3 3PCF (lmax 10) + 4PCF (lmax 4) of 64 catalogues"
+GRAD_METRIC = "pairs/s, D=4 3PCF gradient step (forward + chi^2 + backward)"
+GRAD_WORKLOAD = ("d4n3-grad: D=4 3PCF, n=100k (50k uniform + 50k in 200 Gaussian blobs, sigma 0.01) in the "
+                 "periodic unit 4-cube, 8 bins over [0.01,0.12], lmax 4; chi^2 loss against the seed-104 catalogue")
+
+
+def batch_workload(ncat, n):
+    return (f"batch64: {ncat} catalogues, n={n}, boxes 500-1000, 8 bins over [10,120]; 3PCF lmax 10 and 4PCF "
+            "lmax 4 (two batched calls, pairs counted once)")
 WORKLOAD = ("d3n4: D=3 isotropic 4PCF, ~1M lognormal-Poisson data (w=+1) + 1M uniform randoms (w=-1), "
             "periodic box 1000, 10 linear bins over [20,160], lmax=5")
 SM_COUNT_NOMINAL = 152
@@ -224,25 +233,109 @@ def _cpu_baseline(wl, target_s):
                       f"{pairs} pairs in {dt:.2f} s (FP64 C oracle, single thread)"}
 
 
+def _reference_per_step(args, t_one):
+    """Primaries per reference step: about min(20 s, 150 s / (steps + warmup)) of oracle time, so that the
+    whole run ends within a few minutes."""
+    return max(1, int(round(min(20.0, 150.0 / max(args.steps + args.warmup, 1)) / max(t_one, 1e-3))))
+
+
+def _reference_line(args, metric, workload, n, v, total_t, sample):
+    return {
+        "impl": "reference", "metric": metric, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "n": n},
+        "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def _reference_batch64(args):
+    """The oracle on the batched workload: every step runs the 3PCF (lmax 10) and the 4PCF (lmax 4) on a
+    block of primaries of one catalogue (catalogue k mod 64 at step k); pairs are counted once, as in the
+    GPU arm."""
+    from paper_2106_10278_gb300 import catalogs
+    import oracle
+
+    bw = catalogs.batch64()
+
+    def one(i, a, m):
+        p, w, box = bw.catalogue(i)
+        t0 = time.perf_counter()
+        oracle.estimate(3, 3, 10, bw.edges, box, p, w, primaries=(a, a + m))
+        oracle.estimate(3, 4, 4, bw.edges, box, p, w, primaries=(a, a + m))
+        return time.perf_counter() - t0
+
+    per_step = _reference_per_step(args, one(0, 0, 1))
+    for k in range(args.warmup):
+        one(k % bw.ncat, 0, 1)
+    total_pairs, total_t, sizes = 0, 0.0, []
+    for k in range(args.steps):
+        i = k % bw.ncat
+        p, w, box = bw.catalogue(i)
+        m = min(per_step, len(p))
+        a = (k * m) % max(len(p) - m + 1, 1)
+        total_t += one(i, a, m)
+        total_pairs += count_pairs_numpy(p, bw.edges, box, (a, a + m))
+        sizes.append(m)
+    v = total_pairs / total_t
+    sample = (f"{max(sizes)} primaries per step (catalogue k mod {bw.ncat} at step k, all its secondaries), "
+              "3PCF lmax 10 + 4PCF lmax 4")
+    print(json.dumps(_reference_line(args, BATCH_METRIC, batch_workload(bw.ncat, len(bw.pos)), len(bw.pos), v,
+                                     total_t, sample)), flush=True)
+
+
+def _reference_grad(args):
+    """The oracle on the gradient workload: every step runs the forward estimate and the analytic gradient
+    (the addition-theorem form, bins held fixed) on a block of primaries, with the chi^2 upstream gradient
+    2 (zeta - t); t is the seed-104 catalogue's estimate on the same block, computed once outside the
+    timing (its values do not change the work)."""
+    from paper_2106_10278_gb300 import catalogs
+    import oracle
+
+    wl = catalogs.workload("d4n3", seed=4)
+    tgt = catalogs.workload("d4n3", seed=104)
+
+    def one(a, m, t):
+        t0 = time.perf_counter()
+        _, z = oracle.estimate(4, 3, 4, wl.edges, wl.box, wl.pos, wl.w, primaries=(a, a + m))
+        oracle.estimate_n3_closed(4, 4, wl.edges, wl.box, wl.pos, wl.w, primaries=(a, a + m),
+                                  grad_coeffs=2.0 * (z - t))
+        return time.perf_counter() - t0
+
+    _, t1 = oracle.estimate(4, 3, 4, tgt.edges, tgt.box, tgt.pos, tgt.w, primaries=(0, 1))
+    per_step = min(_reference_per_step(args, one(0, 1, t1)), wl.n)
+    _, t = oracle.estimate(4, 3, 4, tgt.edges, tgt.box, tgt.pos, tgt.w, primaries=(0, per_step))
+    for k in range(args.warmup):
+        one(k, 1, t1)
+    total_pairs, total_t = 0, 0.0
+    for k in range(args.steps):
+        a = (k * per_step) % max(wl.n - per_step + 1, 1)
+        total_t += one(a, per_step, t)
+        total_pairs += count_pairs_numpy(wl.pos, wl.edges, wl.box, (a, a + per_step))
+    v = total_pairs / total_t
+    sample = f"{per_step} primaries per step of the {wl.n}-particle catalogue: forward + analytic gradient"
+    print(json.dumps(_reference_line(args, GRAD_METRIC, GRAD_WORKLOAD, wl.n, v, total_t, sample)), flush=True)
+
+
 def run_reference(args, rank, world):
     from paper_2106_10278_gb300 import catalogs
 
     if rank != 0:
         return
-    if args.workload in ("batch64", "d4n3-grad"):
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-catalogue workloads "
-                          "(d3n4, d3n3_fp64, d2n3, d2n4, d4n3, d3n5)"}), flush=True)
-        return
-    wl = catalogs.workload(args.workload)
     import oracle
 
     oracle.build()
+    if args.workload == "batch64":
+        return _reference_batch64(args)
+    if args.workload == "d4n3-grad":
+        return _reference_grad(args)
+    wl = catalogs.workload(args.workload)
     # size one step at ~ (a few minutes / steps) of CPU time
     t0 = time.perf_counter()
     oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, 1))
     t1 = time.perf_counter() - t0
-    per_step = max(1, int(round(min(20.0, 150.0 / max(args.steps + args.warmup, 1)) / max(t1, 1e-3))))
-    per_step = min(per_step, wl.n)
+    per_step = min(_reference_per_step(args, t1), wl.n)
     for k in range(args.warmup):
         oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(k, k + 1))
     total_pairs, total_t = 0, 0.0
@@ -254,15 +347,9 @@ def run_reference(args, rank, world):
         total_pairs += count_pairs_numpy(wl.pos, wl.edges, wl.box, (a, a + per_step))
     v = total_pairs / total_t
     sample = f"{per_step} primaries per step of the {wl.n}-particle workload, all secondaries"
-    print(json.dumps({
-        "impl": "reference", "metric": METRIC if args.workload == "d3n4" else f"pairs/s and coupling terms/s, {args.workload}",
-        "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "d3n4" else args.workload, "n": wl.n},
-        "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }), flush=True)
+    metric = METRIC if args.workload == "d3n4" else f"pairs/s and coupling terms/s, {args.workload}"
+    workload = WORKLOAD if args.workload == "d3n4" else args.workload
+    print(json.dumps(_reference_line(args, metric, workload, wl.n, v, total_t, sample)), flush=True)
 
 
 def run_ours(args, rank, world):
@@ -485,12 +572,11 @@ def run_batch64(args, rank, world):
     achieved = fpp * pairs / (pair_ms[0] / 1e3) / 1e12
     value = world * pairs * args.steps / t_max
     line = {
-        "metric": "pairs/s, batched D=3 3PCF (lmax 10) + 4PCF (lmax 4) of 64 catalogues", "value": value,
+        "metric": BATCH_METRIC, "value": value,
         "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch64: {bw.ncat} catalogues, n={len(bw.pos)}, boxes 500-1000, 8 bins over "
-                               "[10,120]; 3PCF lmax 10 and 4PCF lmax 4 (two batched calls, pairs counted once)",
+        "config": {"workload": batch_workload(bw.ncat, len(bw.pos)),
                    "pairs_per_step": pairs, "ncoeff": [p.ncoeff for p in plans],
                    "l2": "256 MB buffer written before every timed step (outside the events)"},
         "stages_ms": {"pairs_3pcf_l10": pair_ms[0], "couple_3pcf": couple_ms[0], "pairs_4pcf_l4": pair_ms[1],
@@ -560,12 +646,10 @@ def run_grad(args, rank, world):
     bwd_ms = float(np.mean(bwd_ms))
     value = world * pairs * args.steps / t_max
     line = {
-        "metric": "pairs/s, D=4 3PCF gradient step (forward + chi^2 + backward)", "value": value, "unit": "pairs/s",
+        "metric": GRAD_METRIC, "value": value, "unit": "pairs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "d4n3-grad: D=4 3PCF, n=100k (50k uniform + 50k in 200 Gaussian blobs, sigma 0.01) "
-                               "in the periodic unit 4-cube, 8 bins over [0.01,0.12], lmax 4; chi^2 loss against "
-                               "the seed-104 catalogue", "n": wl.n, "pairs_per_step": pairs,
+        "config": {"workload": GRAD_WORKLOAD, "n": wl.n, "pairs_per_step": pairs,
                    "l2": "256 MB buffer written before every timed step (outside the events)"},
         "stages_ms": {"forward_pairs": fwd["pairs_ms"], "forward_couple": fwd["couple_ms"], "backward": bwd_ms,
                       "backward_stages": dict(zip(("cells", "pair_recompute", "couple_adjoint", "pair_adjoint"),
