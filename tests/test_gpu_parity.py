@@ -253,3 +253,18 @@ def test_grid_field_as_lattice_particles(D, N, lmax, M, edges, precision):
     got = _run(plan, pos, w)
     keys, ref = oracle.estimate_grid(N, lmax, edges, 1.0, (w / dV).reshape((M,) * D))
     _check(plan, got, _aligned_oracle(plan, keys, ref))
+
+
+def test_host_entry_point_rejects_bad_ranges_before_copying():
+    """npcf_compute_host validates n and the primary range on the host, before any copy; the plan
+    stays usable afterwards."""
+    from paper_2106_10278_gb300.npcf import NpcfError
+
+    plan = _plan(3, 3, 2, np.linspace(0.1, 0.3, 3), np.ones(3), "fp32")
+    pos = catalogs.uniform(10, 3, 1.0, 3)
+    w = np.ones(10)
+    for prims in ((5, 11), (6, 2), (-1, 3)):
+        with pytest.raises(NpcfError, match="ERR_ARG"):
+            plan.compute_host(pos, w, primaries=prims)
+    keys, ref = oracle.estimate(3, 3, 2, np.linspace(0.1, 0.3, 3), np.ones(3), pos, w)
+    _check(plan, plan.compute_host(pos, w), _aligned_oracle(plan, keys, ref))
