@@ -60,7 +60,9 @@ typedef enum {
     NPCF_ERR_UNSUPPORTED = -2,    /* (D, N, lmax, nbins) or an option this build does not provide */
     NPCF_ERR_CUDA = -3,           /* a CUDA runtime call failed */
     NPCF_ERR_WORKSPACE = -4,      /* device allocation failed */
-    NPCF_ERR_DEVICE_TIMEOUT = -5, /* a bounded device wait ran out */
+    NPCF_ERR_DEVICE_TIMEOUT = -5, /* a bounded device wait ran out (the tensor-core coupling's
+                                     waits on its MMA completion barriers; the kernel
+                                     then stops and the context stays usable) */
     NPCF_ERR_NONFINITE = -6,      /* a position or weight was NaN/Inf, or a position left the box */
 } npcf_status;
 
@@ -196,20 +198,24 @@ NPCF_API npcf_status npcf_last_profile(npcf_plan_t plan, double* stage_ms, int* 
  * an operational entry point).  Same arguments, same results.  For callers
  * that must not allocate device memory while running -- cudaMalloc
  * synchronises the device and can fail under memory pressure, which real-time
- * loops, processes whose caching allocator already holds the free memory, and
- * work recorded into CUDA graphs cannot accept.  Create the plan during set-up
- * (that allocates its tables once); this call then uses no cudaMalloc,
- * cudaFree or allocating library routine: all of its device workspace comes
- * from one static array of 16 MiB inside libnpcf (held by every GPU that loads
- * the library until the process exits).
+ * loops and processes whose caching allocator already holds the free memory
+ * cannot accept.  Create the plan during set-up (that allocates its tables
+ * once); this call then uses no cudaMalloc, cudaFree or allocating library
+ * routine: all of its device workspace comes from one static array of 16 MiB
+ * inside libnpcf (held by every GPU that loads the library until the process
+ * exits).
  *   - Sizes whose workspace exceeds the array return NPCF_ERR_WORKSPACE with
  *     the bytes needed (about n*(44 + nbins*nq*4) bytes for FP32, nq = 36 at
  *     D=3, lmax=5, plus one row of partial sums; e.g. the D=3 4PCF with
  *     lmax=5 and 10 bins fits n up to about 10,000).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Each call copies the cell grid's stencil and geometry (a few KB) from
+ *     host memory into the array before its kernels.
  *   - Every call shares the one array and clears what must start at zero;
  *     calls whose GPU work overlaps (two streams, two threads) race on it.
+ *   - Stage timings are not recorded (npcf_last_profile reports -1 after it);
+ *     the pair statistics and counters are.
  */
 NPCF_API npcf_status npcf_compute_noalloc(npcf_plan_t plan, const void* positions, const void* weights, int64_t n,
                                           double* coeffs, int64_t primary_begin, int64_t primary_end,

@@ -2,17 +2,19 @@
 
 This module only draws inputs (positions, weights, bin edges); it holds none of
 the estimator's arithmetic, so both the CUDA path and the FP64 oracle may use
-it.  Every position it returns is exactly representable in FP32 and lies in
-[0, L) on every axis, so an FP32 device copy and an FP64 host copy describe the
-same points.
+it.  Every position lies in [0, L) on every axis.  By default positions and
+weights are rounded to FP32, so that an FP32 device copy and the FP64 host copy
+describe the same points; ``fp32=False`` keeps the full FP64 mantissa, the
+inputs that FP64 plans are tested on (a stage that silently narrowed them to
+float would then show).
 
 Workloads (all periodic boxes, linear radial bins):
 
 =========  =====================================================================
 name       recipe
 =========  =====================================================================
-d3n3_fp64  D=3, N=3, lmax=5, FP64. n=2000 uniform in a cube of side 250,
-           w=1, 10 bins over [0, 100].
+d3n3_fp64  D=3, N=3, lmax=5, FP64. n=2000 uniform in a cube of side 250
+           (full FP64 mantissa), w=1, 10 bins over [0, 100].
 d2         D=2, N=3 and N=4, lmax=10. n=200k in the unit square: 100k uniform
            plus 100k in 400 Gaussian blobs (centres uniform, members
            multinomial, sigma=0.005, wrapped), w ~ N(1, 0.1), 16 bins over
@@ -37,19 +39,19 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def _fp32_in_box(x: np.ndarray, L: np.ndarray) -> np.ndarray:
-    """Wrap into [0, L), round to FP32, and re-wrap values that rounded up to L."""
+def _fp32_in_box(x: np.ndarray, L: np.ndarray, fp32: bool = True) -> np.ndarray:
+    """Wrap into [0, L), round to FP32 (unless fp32 is False), and re-wrap values that rounded up to L."""
     x = np.mod(x, L)
-    x32 = x.astype(np.float32).astype(np.float64)
-    L32 = np.asarray(L, dtype=np.float64)
-    x32 = np.where(x32 >= L32, 0.0, x32)
-    return x32
+    L64 = np.asarray(L, dtype=np.float64)
+    if fp32:
+        x = x.astype(np.float32).astype(np.float64)
+    return np.where(x >= L64, 0.0, x)
 
 
-def uniform(n: int, D: int, L, seed: int) -> np.ndarray:
-    """n points uniform in the periodic box [0, L)^D."""
+def uniform(n: int, D: int, L, seed: int, fp32: bool = True) -> np.ndarray:
+    """n points uniform in the periodic box [0, L)^D (FP32-representable unless fp32 is False)."""
     L = np.broadcast_to(np.asarray(L, dtype=np.float64), (D,))
-    return _fp32_in_box(_rng(seed).random((n, D)) * L, L)
+    return _fp32_in_box(_rng(seed).random((n, D)) * L, L, fp32)
 
 
 def sphere_uniform(n: int, seed: int) -> np.ndarray:
@@ -61,15 +63,16 @@ def sphere_uniform(n: int, seed: int) -> np.ndarray:
     return v.astype(np.float32).astype(np.float64)
 
 
-def gaussian_blobs(n: int, D: int, L, n_centres: int, sigma: float, seed: int) -> np.ndarray:
-    """n points in Gaussian blobs: centres uniform, membership multinomial, wrapped."""
+def gaussian_blobs(n: int, D: int, L, n_centres: int, sigma: float, seed: int, fp32: bool = True) -> np.ndarray:
+    """n points in Gaussian blobs: centres uniform, membership multinomial, wrapped (FP32-representable
+    unless fp32 is False)."""
     L = np.broadcast_to(np.asarray(L, dtype=np.float64), (D,))
     g = _rng(seed)
     centres = g.random((n_centres, D)) * L
     counts = g.multinomial(n, np.full(n_centres, 1.0 / n_centres))
     members = np.repeat(np.arange(n_centres), counts)
     x = centres[members] + g.normal(0.0, sigma, (n, D))
-    return _fp32_in_box(x, L)
+    return _fp32_in_box(x, L, fp32)
 
 
 def _rfftn(x):
@@ -118,8 +121,10 @@ def lognormal_poisson(n_mean: float, L: float, seed: int, grid: int = 256, slope
     return _fp32_in_box(x, np.full(3, float(L)))
 
 
-def normal_weights(n: int, mean: float, sd: float, seed: int) -> np.ndarray:
-    return _rng(seed).normal(mean, sd, n).astype(np.float32).astype(np.float64)
+def normal_weights(n: int, mean: float, sd: float, seed: int, fp32: bool = True) -> np.ndarray:
+    """n weights drawn from N(mean, sd^2) (FP32-representable unless fp32 is False)."""
+    w = _rng(seed).normal(mean, sd, n)
+    return w.astype(np.float32).astype(np.float64) if fp32 else w
 
 
 def linear_edges(lo: float, hi: float, nbins: int) -> np.ndarray:
@@ -193,7 +198,7 @@ def workload(name: str, seed: int | None = None, scale: float = 1.0) -> Workload
     if name == "d3n3_fp64":
         s = 0 if seed is None else seed
         n = max(8, int(round(2000 * scale)))
-        pos = uniform(n, 3, 250.0, s)
+        pos = uniform(n, 3, 250.0, s, fp32=False)
         return Workload(name, 3, 3, 5, linear_edges(0.0, 100.0, 10), np.full(3, 250.0), pos, np.ones(n), "fp64")
     if name in ("d2", "d2n3", "d2n4"):
         s = 1 if seed is None else seed

@@ -843,6 +843,21 @@ npcf_status run_pairs(npcf_plan_s* P, const GridView& gv, const void* pos, const
     return NPCF_OK;
 }
 
+// Persistent rows (CTAs along x) of the coupling launch for nprim primaries: about two CTAs per
+// SM over the key blocks; one per SM for the FP32 D=2 4PCF register kernel; for N=5 groups of
+// d3n5_group primaries with up to three CTAs per SM.  Never more rows than there is work.
+int couple_rows(const npcf_plan_s* P, int64_t nprim, int chunk)
+{
+    if (P->N == 5) {
+        const int G = d3n5_group(P->nbins, P->lmax, P->fp64);
+        return (int)std::min<int64_t>(3 * P->nsm, std::max<int64_t>(1, (nprim + G - 1) / G));
+    }
+    const int nkb = (int)P->kblocks.size();
+    int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
+    if (d2n4_registers(P)) rows = P->nsm;
+    return (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim + chunk - 1) / chunk));
+}
+
 npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, double* coeffs, int64_t pb, int64_t pe,
                 cudaStream_t s)
 {
@@ -851,14 +866,7 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     if ((st = prepare_grid(P, n)) != NPCF_OK) return st;
     const int64_t nprim_max = pe - pb;
     const int chunk = 128;
-    const int nkb = (int)P->kblocks.size();
-    int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
-    if (d2n4_registers(P)) rows = P->nsm;
-    if (P->N == 5) {  // groups of d3n5_group primaries (up to 3 CTAs per SM); a partial row holds every coefficient
-        const int G = d3n5_group(P->nbins, P->lmax, P->fp64);
-        rows = (int)std::min<int64_t>(3 * P->nsm, std::max<int64_t>(1, (nprim_max + G - 1) / G));
-    }
-    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, P->N == 5 ? rows : (nprim_max + chunk - 1) / chunk));
+    const int rows = couple_rows(P, nprim_max, chunk);
     if ((st = reserve_workspace(P, n, nprim_max, rows, P->ncells)) != NPCF_OK) return st;
     PairStage ps;
     if ((st = run_pairs(P, single_view(P), pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
@@ -1344,10 +1352,12 @@ void npcf_plan_destroy(npcf_plan_t P)
 // needs at compute time carved out of one file-scope __device__ array instead
 // of plan workspace.  It exists for callers that must not allocate device
 // memory once they are running: cudaMalloc synchronises the whole device and
-// may fail under memory pressure, which real-time loops, code that shares the
-// GPU with a caching allocator that owns all free memory, and code recorded
-// into a CUDA graph cannot accept.  Such callers create the plan (which
-// allocates its small tables once) during set-up and then call this.
+// may fail under memory pressure, which real-time loops and code that shares
+// the GPU with a caching allocator that owns all free memory cannot accept.
+// Such callers create the plan (which allocates its small tables once) during
+// set-up and then call this.  Each call copies the cell grid's stencil and
+// geometry (a few KB) from host memory into the array before its kernels, and
+// records no stage timings.
 //
 // The array below is part of the module: every GPU that loads libnpcf holds
 // its kNoallocBytes until the process exits.  Host code must not use the
@@ -1407,7 +1417,6 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     const int nc = g.ncells;
     const int64_t nprim_max = pe - pb;
     const int chunk = 128;
-    const int nkb = (int)P->kblocks.size();
     const int rb = rec_bytes(P->D, P->fp64), tb = P->fp64 ? 8 : 4;
 
     Carve cv{base};
@@ -1423,8 +1432,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     int* small = static_cast<int*>(cv.take(128));
     const size_t row_bytes = sizeof(double) * 2 * P->ncoeff;
     size_t left = cv.used <= kNoallocBytes ? kNoallocBytes - ((cv.used + 255) & ~size_t(255)) : 0;
-    int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
-    rows = (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim_max + chunk - 1) / chunk));
+    int rows = couple_rows(P, nprim_max, chunk);  // as npcf_compute, bounded by the scratch left
     rows = (int)std::min<size_t>((size_t)rows, left / row_bytes);
     if (cv.used > kNoallocBytes || rows < 1) {
         size_t need = ((cv.need + 255) & ~size_t(255)) + row_bytes;
@@ -1496,37 +1504,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     else e = launch_pairs_d4(pp, P->fp64, P->Lc, P->nsm, P->pair_smem, s);
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "pair kernel launch: %s", cudaGetErrorString(e));
 
-    CoupleParams kp{};
-    kp.D = P->D;
-    kp.N = P->N;
-    kp.nbins = P->nbins;
-    kp.lmax = P->lmax;
-    kp.nq = P->nq;
-    kp.nlam = P->nlam;
-    kp.a = a;
-    kp.wprim = wprim;
-    kp.nprim = ib.nprim;
-    kp.chunk = chunk;
-    kp.ncoeff = (int)P->ncoeff;
-    kp.partial = partial;
-    kp.pairs = P->d_pairs.as<int2>();
-    kp.pair_key = P->d_pair_key.as<int>();
-    kp.kblocks = P->d_kblocks.as<int4>();
-    kp.nkb = nkb;
-    kp.max_block_keys = P->max_block_keys;
-    kp.max_block_pairs = P->max_block_pairs;
-    kp.task_pairs = P->d_task.as<int>();
-    kp.lam2 = P->d_lam2.as<int2>();
-    kp.lam_odd = P->d_lamodd.as<signed char>();
-    kp.pref = P->d_pref.p;
-    kp.group = P->N == 5 ? d3n5_group(P->nbins, P->lmax, P->fp64) : d2n4_group(P->nbins, P->lmax);
-    kp.ntriple = (int)P->triples.size();
-    kp.triples = P->d_triples.as<int4>();
-    kp.lam5 = P->d_lam5.as<int4>();
-    kp.terms5 = P->d_terms5.as<int>();
-    kp.coef5 = P->d_coef5.as<double>();
-    kp.coef5f = P->d_coef5f.as<float>();
-    kp.ncat = 1;
+    CoupleParams kp = couple_params(P, a, wprim, ib.nprim, chunk, partial);
     CUDA_TRY(cudaMemsetAsync(partial, 0, row_bytes * rows, s));
     e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));

@@ -25,6 +25,24 @@ def test_generators_fp32_in_box_and_reproducible():
     assert np.array_equal(w.astype(np.float32).astype(np.float64), w)
 
 
+def test_full_mantissa_generators_for_fp64_plans():
+    """fp32=False keeps the FP64 mantissa (the inputs of FP64 plans), inside the same box and with the
+    same underlying draws (the FP32 variant is their rounding)."""
+    u = catalogs.uniform(5000, 3, [1.0, 2.0, 0.5], 7, fp32=False)
+    assert np.all(u >= 0.0) and np.all(u < [1.0, 2.0, 0.5])
+    assert not np.array_equal(u.astype(np.float32).astype(np.float64), u)
+    u32 = catalogs.uniform(5000, 3, [1.0, 2.0, 0.5], 7)
+    assert np.max(np.abs(u - u32)) <= 2.0 ** -23
+    b = catalogs.gaussian_blobs(5000, 4, 1.0, 20, 0.05, 8, fp32=False)
+    assert np.all(b >= 0.0) and np.all(b < 1.0)
+    assert not np.array_equal(b.astype(np.float32).astype(np.float64), b)
+    w = catalogs.normal_weights(1000, 1.0, 0.1, 3, fp32=False)
+    assert not np.array_equal(w.astype(np.float32).astype(np.float64), w)
+    np.testing.assert_allclose(w, catalogs.normal_weights(1000, 1.0, 0.1, 3), rtol=1e-7)
+    wl = catalogs.workload("d3n3_fp64", scale=0.1)
+    assert wl.precision == "fp64" and not np.array_equal(wl.pos.astype(np.float32).astype(np.float64), wl.pos)
+
+
 def test_sphere_directions_fp32_and_unit():
     v = catalogs.sphere_uniform(4000, 5)
     assert np.array_equal(v.astype(np.float32).astype(np.float64), v)

@@ -55,8 +55,10 @@ def _compare(lmax, edges, box, pos, w, precision, primaries=None):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("lmax,nbins", [(2, 5), (3, 6)])
 def test_5pcf_small_parity(lmax, nbins, precision):
-    pos = np.concatenate([catalogs.uniform(500, 3, 1.0, 51), catalogs.gaussian_blobs(500, 3, 1.0, 6, 0.05, 52)])
-    w = catalogs.normal_weights(1000, 1.0, 0.3, 53)
+    f32 = precision == "fp32"
+    pos = np.concatenate([catalogs.uniform(500, 3, 1.0, 51, fp32=f32),
+                          catalogs.gaussian_blobs(500, 3, 1.0, 6, 0.05, 52, fp32=f32)])
+    w = catalogs.normal_weights(1000, 1.0, 0.3, 53, fp32=f32)
     edges = np.linspace(0.05, 0.35, nbins + 1)
     _compare(lmax, edges, np.ones(3), pos, w, precision, primaries=(100, 260))
 

@@ -37,10 +37,11 @@ def _plan(D, lmax, edges, box, precision, **kw):
     return Plan(D, 3, lmax, edges, box, precision=precision, **kw)
 
 
-def _catalog(D, n, seed):
-    pos = np.concatenate([catalogs.uniform(n // 2, D, 1.0, seed),
-                          catalogs.gaussian_blobs(n - n // 2, D, 1.0, 5, 0.04, seed + 1)])
-    w = catalogs.normal_weights(n, 1.0, 0.3, seed + 2).astype(np.float32).astype(np.float64)
+def _catalog(D, n, seed, fp32=True):
+    """Half uniform, half in Gaussian blobs; FP32-representable, or with a full FP64 mantissa for FP64 plans."""
+    pos = np.concatenate([catalogs.uniform(n // 2, D, 1.0, seed, fp32=fp32),
+                          catalogs.gaussian_blobs(n - n // 2, D, 1.0, 5, 0.04, seed + 1, fp32=fp32)])
+    w = catalogs.normal_weights(n, 1.0, 0.3, seed + 2, fp32=fp32)
     return pos, w
 
 
@@ -104,16 +105,17 @@ CASES = [
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("D,lmax,nbins,n,rmax", CASES)
 def test_backward_small(D, lmax, nbins, n, rmax, precision):
-    pos, w = _catalog(D, n, 10 * D + lmax)
+    pos, w = _catalog(D, n, 10 * D + lmax, fp32=precision == "fp32")
     edges = np.linspace(0.02, rmax, nbins + 1)
     _compare(D, lmax, edges, np.ones(D), pos, w, precision, seed=D + lmax)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_backward_primary_range_and_open_box(precision):
-    pos, w = _catalog(3, 1500, 77)
+    pos, w = _catalog(3, 1500, 77, fp32=precision == "fp32")
     pos = pos * 0.96 + 0.02
-    pos = pos.astype(np.float32).astype(np.float64)
+    if precision == "fp32":
+        pos = pos.astype(np.float32).astype(np.float64)
     edges = np.linspace(0.03, 0.22, 7)
     _compare(3, 4, edges, np.ones(3), pos, w, precision, primaries=(200, 900), seed=5)
     _compare(3, 4, edges, np.ones(3), pos, w, precision, periodic=False, seed=6)
@@ -186,7 +188,7 @@ def test_backward_identities_at_scale(D):
     """Properties that hold at any size: sum_i dL/dy_i = 0 (translation invariance of a periodic
     catalogue) and sum_i w_i dL/dw_i = 3 L (zeta is cubic in the weights), with L from the forward."""
     n = {2: 60000, 3: 60000, 4: 40000}[D]
-    pos, w = _catalog(D, n, 300 + D)
+    pos, w = _catalog(D, n, 300 + D, fp32=False)
     lmax = {2: 8, 3: 5, 4: 3}[D]
     edges = np.linspace(0.005, {2: 0.03, 3: 0.06, 4: 0.12}[D], 9)
     plan = _plan(D, lmax, edges, np.ones(D), "fp64")
@@ -204,7 +206,7 @@ def test_backward_identities_at_scale(D):
 
 
 def test_autograd_function_matches_backward():
-    pos, w = _catalog(3, 1200, 9)
+    pos, w = _catalog(3, 1200, 9, fp32=False)
     edges = np.linspace(0.02, 0.2, 6)
     plan = _plan(3, 4, edges, np.ones(3), "fp64")
     tp = torch.tensor(pos, dtype=torch.float64, device="cuda", requires_grad=True)

@@ -48,8 +48,9 @@ def _check(precision, got, ref):
     assert scale > 0
 
 
-def _small_batch(D, seed):
-    """Five catalogues of different sizes (one empty) in boxes of different, non-cubic shapes."""
+def _small_batch(D, seed, fp32=True):
+    """Five catalogues of different sizes (one empty) in boxes of different, non-cubic shapes
+    (FP32-representable values, or a full FP64 mantissa when fp32 is False)."""
     sizes = [700, 0, 1500, 300, 1100]
     shapes = [[1.0, 1.0, 1.0, 1.0], [0.9, 1.1, 1.0, 1.0], [1.2, 1.0, 0.8, 1.1], [1.0, 0.9, 1.0, 0.9],
               [0.8, 0.8, 0.9, 1.0]]
@@ -57,10 +58,10 @@ def _small_batch(D, seed):
     parts, ws = [], []
     for i, n in enumerate(sizes):
         half = n // 2
-        p = np.concatenate([catalogs.uniform(half, D, boxes[i], seed + 10 * i),
-                            catalogs.gaussian_blobs(n - half, D, boxes[i], 4, 0.03, seed + 10 * i + 1)])
+        p = np.concatenate([catalogs.uniform(half, D, boxes[i], seed + 10 * i, fp32=fp32),
+                            catalogs.gaussian_blobs(n - half, D, boxes[i], 4, 0.03, seed + 10 * i + 1, fp32=fp32)])
         parts.append(p)
-        ws.append(catalogs.normal_weights(n, 1.0, 0.3, seed + 10 * i + 2))
+        ws.append(catalogs.normal_weights(n, 1.0, 0.3, seed + 10 * i + 2, fp32=fp32))
     offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     return np.concatenate(parts), np.concatenate(ws), offsets, boxes
 
@@ -78,7 +79,7 @@ CASES = [
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("D,N,lmax,nbins,rmax", CASES)
 def test_batched_small_parity(D, N, lmax, nbins, rmax, precision):
-    pos, w, offsets, boxes = _small_batch(D, 40 + D + N)
+    pos, w, offsets, boxes = _small_batch(D, 40 + D + N, fp32=precision == "fp32")
     edges = np.linspace(0.02, rmax, nbins + 1)
     plan = _plan(D, N, lmax, edges, precision)
     dt = torch.float64 if precision == "fp64" else torch.float32

@@ -4,7 +4,9 @@ Tolerances (both stated by the target of this implementation):
   FP64 plans:  max |gpu - oracle| <= 1e-10 * max |oracle|
   FP32 plans:  ||gpu - oracle||_2 <= 1e-5 * ||oracle||_2
 Bin decisions are exact on both paths (pairs near an edge are re-decided in
-FP64 from the original coordinates), so the pair sets agree exactly.
+FP64 from the original coordinates), so the pair sets agree exactly.  FP64
+plans are tested on positions and weights with a full FP64 mantissa (the
+generators' fp32=False), FP32 plans on FP32-representable ones.
 """
 import numpy as np
 import pytest
@@ -88,25 +90,33 @@ CASES = [
 @pytest.mark.parametrize("D,N,lmax,nbins,n,prims", CASES)
 def test_parity_small(D, N, lmax, nbins, n, prims, precision):
     g = np.random.default_rng(D * 100 + N * 10 + lmax)
-    pos = np.concatenate([catalogs.uniform(n // 2, D, 1.0, D + 7),
-                          catalogs.gaussian_blobs(n - n // 2, D, 1.0, 7, 0.03, D + 8)])
-    w = catalogs.normal_weights(n, 1.0, 0.3, D + 9) * np.where(g.random(n) < 0.3, -1.0, 1.0)
+    f32 = precision == "fp32"
+    pos = np.concatenate([catalogs.uniform(n // 2, D, 1.0, D + 7, fp32=f32),
+                          catalogs.gaussian_blobs(n - n // 2, D, 1.0, 7, 0.03, D + 8, fp32=f32)])
+    w = catalogs.normal_weights(n, 1.0, 0.3, D + 9, fp32=f32) * np.where(g.random(n) < 0.3, -1.0, 1.0)
+    if not f32:  # the FP64 path must not narrow its inputs: they carry more than FP32's 24 bits
+        assert not np.array_equal(pos.astype(np.float32).astype(np.float64), pos)
+        assert not np.array_equal(w.astype(np.float32).astype(np.float64), w)
     edges = np.linspace(0.02, 0.3 if D < 4 else 0.4, nbins + 1)
     _compare(D, N, lmax, edges, np.ones(D), pos, w, precision, primaries=prims)
 
 
 def test_fp64_d3n3_workload_full():
-    """D=3 3PCF in FP64, n=2000 in a periodic cube of side 250, 10 bins over [0, 100], lmax=5."""
+    """D=3 3PCF in FP64, n=2000 in a periodic cube of side 250 (full-mantissa positions), 10 bins over
+    [0, 100], lmax=5; the weights get a full mantissa too."""
     wl = catalogs.workload("d3n3_fp64")
-    _compare(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, "fp64")
+    assert not np.array_equal(wl.pos.astype(np.float32).astype(np.float64), wl.pos)
+    w = catalogs.normal_weights(wl.n, 1.0, 0.3, 17, fp32=False)
+    _compare(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, w, "fp64")
 
 
 def test_fp64_d3n3_bruteforce_n200():
     """The GPU against the naive N-tuplet sum projected on the same basis (n=200)."""
     wl = catalogs.workload("d3n3_fp64", scale=0.1)
+    w = catalogs.normal_weights(wl.n, 1.0, 0.3, 18, fp32=False)
     plan = _plan(3, 3, 5, wl.edges, wl.box, "fp64")
-    got = _run(plan, wl.pos, wl.w)
-    keys, ref = oracle.estimate(3, 3, 5, wl.edges, wl.box, wl.pos, wl.w, brute=True)
+    got = _run(plan, wl.pos, w)
+    keys, ref = oracle.estimate(3, 3, 5, wl.edges, wl.box, wl.pos, w, brute=True)
     _check(plan, got, _aligned_oracle(plan, keys, ref))
 
 
