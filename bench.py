@@ -48,6 +48,9 @@ def batch_workload(ncat, n):
             "lmax 4 (two batched calls, pairs counted once)")
 WORKLOAD = ("d3n4: D=3 isotropic 4PCF, ~1M lognormal-Poisson data (w=+1) + 1M uniform randoms (w=-1), "
             "periodic box 1000, 10 linear bins over [20,160], lmax=5")
+# the arithmetic each precision runs the path in (pair stage / coupling)
+DTYPES = {"fp32": "f32", "fp64": "f64", "mixed_bf16x3": "f32 pairs, bf16x3 tensor-core coupling",
+          "mixed_tf32x3": "f32 pairs, tf32x3 tensor-core coupling"}
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 
@@ -63,6 +66,8 @@ def _args():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default=None,
+                    help="fp32 | fp64 | mixed_bf16x3 | mixed_tf32x3 (default: the workload's own, fp32 or fp64)")
     return ap.parse_args()
 
 
@@ -201,22 +206,66 @@ def _peaks():
         return {}
 
 
+def kernel_source_sha16() -> str:
+    """Hash of the pair kernel's sources (the kernel, its harmonics and shared structures): a
+    committed ncu traffic figure is used only while it matches."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("npcf_pairs.cuh", "npcf_device.cuh", "npcf_internal.h", "npcf_math.h"):
+        h.update(open(os.path.join(ROOT, "paper_2106_10278_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_from_profiles(workload: str):
-    """Per-launch DRAM bytes of the pair kernel from the committed ncu summary, if current."""
+    """Per-launch DRAM bytes of the pair kernel from the committed ncu summary, if it was taken on the
+    current kernel sources (its kernel_sha16 line matches); else None."""
     path = os.path.join(ROOT, "profiles", f"k_pairs_{workload}.md")
+    vals = {}
     try:
         for line in open(path):
-            if line.startswith("traffic_bytes_per_launch:"):
-                v = line.split(":", 1)[1].strip()
-                return None if v in ("", "null") else float(v)
+            for key in ("traffic_bytes_per_launch:", "kernel_sha16:"):
+                if line.startswith(key):
+                    vals[key] = line.split(":", 1)[1].strip()
     except OSError:
-        pass
-    return None
+        return None
+    v = vals.get("traffic_bytes_per_launch:")
+    if v in (None, "", "null") or vals.get("kernel_sha16:") != kernel_source_sha16():
+        return None
+    return float(v)
 
 
 # ---------------------------------------------------------------------- arms
-def _cpu_baseline(wl, target_s):
-    """The FP64 oracle (single thread, as it stands) on a bounded sample of primaries."""
+_ORACLE_INPUT = {}
+
+
+def _oracle_worker_init(path):
+    """Spawned worker: load the workload saved by the parent (memory-mapped) and build nothing."""
+    import oracle
+
+    oracle.build()
+    d = np.load(path, allow_pickle=True)
+    _ORACLE_INPUT.update({k: d[k] for k in d.files})
+
+
+def _oracle_worker_block(prims):
+    """The oracle, as it stands, on one block of primaries; returns (coefficients, seconds)."""
+    import oracle
+
+    x = _ORACLE_INPUT
+    t0 = time.perf_counter()
+    _, z = oracle.estimate(int(x["D"]), int(x["N"]), int(x["lmax"]), x["edges"], x["box"], x["pos"], x["w"],
+                           primaries=prims)
+    return z, time.perf_counter() - t0
+
+
+def _cpu_baseline(wl, target_s, gpu_range_fn=None):
+    """The FP64 oracle (as it stands) on a bounded sample of primaries: single-threaded, then the same
+    program in one spawned process per host core over disjoint primary blocks.  When gpu_range_fn is
+    given, the GPU's coefficients of the single-threaded sample's primaries are compared with the
+    oracle's (the per-result error of this run)."""
+    import multiprocessing as mp
+
     import oracle
 
     oracle.build()
@@ -225,12 +274,43 @@ def _cpu_baseline(wl, target_s):
     t1 = time.perf_counter() - t0
     nprim = int(max(1, min(256, round(target_s / max(t1, 1e-3)))))
     t0 = time.perf_counter()
-    oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, nprim))
+    keys, ref = oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, nprim))
     dt = time.perf_counter() - t0
     pairs = count_pairs_numpy(wl.pos, wl.edges, wl.box, (0, nprim))
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-            "sample": f"primaries [0,{nprim}) of the {wl.n}-particle workload, all secondaries, "
-                      f"{pairs} pairs in {dt:.2f} s (FP64 C oracle, single thread)"}
+    host = os.cpu_count() or 1
+    out = {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "host_cores": host, "kind": "oracle",
+           "sample": f"primaries [0,{nprim}) of the {wl.n}-particle workload, all secondaries, "
+                     f"{pairs} pairs in {dt:.2f} s (FP64 C oracle, single thread)"}
+    if gpu_range_fn is not None:
+        got, plan_keys = gpu_range_fn(0, nprim)
+        index = {tuple(int(v) for v in k): i for i, k in enumerate(keys)}
+        r = ref[np.array([index[tuple(int(v) for v in k)] for k in plan_keys])]
+        out["rel_err_vs_oracle"] = {"value": float(np.linalg.norm(got - r) / np.linalg.norm(r)),
+                                    "primaries": [0, nprim],
+                                    "measure": "||gpu - oracle||_2 / ||oracle||_2 over all coefficients"}
+    if host > 1:
+        # the same oracle in `host` spawned processes, each on its own block of m primaries
+        m = nprim
+        blocks = [(nprim + i * m, nprim + (i + 1) * m) for i in range(host)]
+        if blocks[-1][1] <= wl.n:
+            fd, path = tempfile.mkstemp(suffix=".npz")
+            os.close(fd)
+            try:
+                np.savez(path, D=wl.D, N=wl.N, lmax=wl.lmax, edges=wl.edges, box=wl.box, pos=wl.pos, w=wl.w)
+                ctx = mp.get_context("spawn")
+                with ctx.Pool(host, initializer=_oracle_worker_init, initargs=(path,)) as pool:
+                    pool.map(_oracle_worker_block, [(i, i + 1) for i in range(host)])  # warm every worker
+                    t0 = time.perf_counter()
+                    res = pool.map(_oracle_worker_block, blocks)
+                    wall = time.perf_counter() - t0
+                ppairs = sum(count_pairs_numpy(wl.pos, wl.edges, wl.box, b) for b in blocks)
+                out["all_cores"] = {"value": ppairs / wall, "unit": "pairs/s", "cores": host,
+                                    "sample": f"{host} processes x {m} primaries ([{nprim},{blocks[-1][1]})), "
+                                              f"{ppairs} pairs in {wall:.2f} s wall (the same oracle, one spawned "
+                                              "process per host core)"}
+            finally:
+                os.unlink(path)
+    return out
 
 
 def _reference_per_step(args, t_one):
@@ -331,25 +411,42 @@ def run_reference(args, rank, world):
     if args.workload == "d4n3-grad":
         return _reference_grad(args)
     wl = catalogs.workload(args.workload)
-    # size one step at ~ (a few minutes / steps) of CPU time
+    import multiprocessing as mp
+
+    # size one step at ~ (a few minutes / steps) of CPU time; every step runs the oracle, as it stands,
+    # in one spawned process per host core, each on its own block of primaries
+    host = os.cpu_count() or 1
     t0 = time.perf_counter()
     oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, 1))
     t1 = time.perf_counter() - t0
-    per_step = min(_reference_per_step(args, t1), wl.n)
-    for k in range(args.warmup):
-        oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(k, k + 1))
+    per_proc = max(1, min(_reference_per_step(args, t1), wl.n // max(host, 1)))
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
     total_pairs, total_t = 0, 0.0
-    for k in range(args.steps):
-        a = (k * per_step) % max(wl.n - per_step + 1, 1)
-        t0 = time.perf_counter()
-        oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(a, a + per_step))
-        total_t += time.perf_counter() - t0
-        total_pairs += count_pairs_numpy(wl.pos, wl.edges, wl.box, (a, a + per_step))
+    try:
+        np.savez(path, D=wl.D, N=wl.N, lmax=wl.lmax, edges=wl.edges, box=wl.box, pos=wl.pos, w=wl.w)
+        with mp.get_context("spawn").Pool(host, initializer=_oracle_worker_init, initargs=(path,)) as pool:
+            for k in range(args.warmup):
+                pool.map(_oracle_worker_block, [(i, i + 1) for i in range(host)])
+            span = per_proc * host
+            for k in range(args.steps):
+                a = (k * span) % max(wl.n - span + 1, 1)
+                blocks = [(a + i * per_proc, a + (i + 1) * per_proc) for i in range(host)]
+                t0 = time.perf_counter()
+                pool.map(_oracle_worker_block, blocks)
+                total_t += time.perf_counter() - t0
+                total_pairs += sum(count_pairs_numpy(wl.pos, wl.edges, wl.box, b) for b in blocks)
+    finally:
+        os.unlink(path)
     v = total_pairs / total_t
-    sample = f"{per_step} primaries per step of the {wl.n}-particle workload, all secondaries"
+    sample = (f"{host} processes x {per_proc} primaries per step of the {wl.n}-particle workload, all secondaries "
+              "(the FP64 oracle, one spawned process per host core)")
     metric = METRIC if args.workload == "d3n4" else f"pairs/s and coupling terms/s, {args.workload}"
     workload = WORKLOAD if args.workload == "d3n4" else args.workload
-    print(json.dumps(_reference_line(args, metric, workload, wl.n, v, total_t, sample)), flush=True)
+    line = _reference_line(args, metric, workload, wl.n, v, total_t, sample)
+    line["cpu_baseline"]["cores"] = host
+    line["host_cores"] = host
+    print(json.dumps(line), flush=True)
 
 
 def run_ours(args, rank, world):
@@ -368,7 +465,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     base_seed = {"d3n4": 2, "d2n3": 1, "d2n4": 1, "d4n3": 4, "d3n3_fp64": 0, "d3n5": 5}[args.workload]
     wl = catalogs.workload(args.workload, seed=base_seed + 1000 * rank, scale=args.scale)
-    prec = "fp64" if wl.precision == "fp64" else "fp32"
+    prec = args.precision or ("fp64" if wl.precision == "fp64" else "fp32")
     tdt = torch.float64 if prec == "fp64" else torch.float32
     plan = Plan(wl.D, wl.N, wl.lmax, wl.edges, wl.box, precision=prec, sync_check=False, timing=True)
     pos = torch.tensor(wl.pos, dtype=tdt, device=dev)
@@ -435,7 +532,10 @@ def run_ours(args, rank, world):
     if ck_s <= pk_s:
         achieved = fpp * pairs_per_step / pk_s / 1e12
         roofline = {"bound": "alu", "kernel": "k_pairs", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": _traffic_from_profiles(args.workload), "peak_note": note,
+                    "frac": achieved / peak, "traffic": _traffic_from_profiles(args.workload),
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, committed in "
+                                      f"profiles/k_pairs_{args.workload}.md for kernel sources {kernel_source_sha16()} "
+                                      "(null when that summary was taken on other sources)", "peak_note": note,
                     "flops_per_pair": fpp, "pairs_per_launch": pairs_per_step,
                     "pair_kernel_ms": float(np.mean(pair_ms))}
     else:
@@ -467,8 +567,8 @@ def run_ours(args, rank, world):
         "metric": METRIC if args.workload == "d3n4" else f"pairs/s and coupling terms/s, {args.workload}",
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "d3n4" else args.workload, "n": wl.n,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "d3n4" else args.workload, "n": wl.n, "precision": prec,
                    "primaries": nprim, "pairs_per_step": pairs_per_step, "candidates_per_step": cand_per_step,
                    "ncoeff": plan.ncoeff,
                    "l2": "256 MB buffer written before every timed step (outside the events)"},
@@ -481,7 +581,14 @@ def run_ours(args, rank, world):
     if args.scale != 1.0:
         line["config"]["scale"] = args.scale
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
+        def gpu_range(a, b):  # the GPU's coefficients of primaries [a, b), for the per-result error
+            z = plan.compute(pos, w, primaries=(a, b)).cpu().numpy()
+            return z, plan.keys()
+
+        cb = _cpu_baseline(wl, args.cpu_seconds, gpu_range)
+        line["rel_err_vs_oracle"] = cb.pop("rel_err_vs_oracle", None)
+        line["host_cores"] = cb["host_cores"]
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -66,12 +66,25 @@ typedef enum {
     NPCF_ERR_NONFINITE = -6,      /* a position or weight was NaN/Inf, or a position left the box */
 } npcf_status;
 
-enum { NPCF_FP64 = 0, NPCF_FP32 = 1 };          /* npcf_opts.precision */
+/* npcf_opts.precision.  The two split-precision modes run the pair stage as NPCF_FP32 and
+ * the coupling (the contraction over primaries of eq. NPCF-estimator-discrete) on the
+ * tensor cores: every FP32 operand x is split into hi + lo of BF16 (MIXED_BF16X3) or TF32
+ * (MIXED_TF32X3) and a product is kept as hi*hi + hi*lo + lo*hi with FP32 accumulation over
+ * spans of primaries and FP64 sums across spans.  Provided for the D=2 4PCF (at most 17
+ * bins); other plans return NPCF_ERR_UNSUPPORTED for them. */
+enum { NPCF_FP64 = 0, NPCF_FP32 = 1, NPCF_MIXED_BF16X3 = 2, NPCF_MIXED_TF32X3 = 3 };
 enum { NPCF_BINS_LE = 0, NPCF_BINS_LT = 1 };    /* npcf_opts.bin_order (N=3 only) */
+/* npcf_opts.parity: which components a plan returns, by their behaviour under r -> -r (the
+ * basis parity (-1)^(l1+l2+l3) of eq. B-hypersph; the odd ones are imaginary).  Only the D=3
+ * 4PCF has odd components: N=3 and the D=2 4PCF are even (in D=2, r -> -r is a rotation) and the
+ * 5PCF keys are the even label sets, so NPCF_PARITY_ODD is refused for them. */
+enum { NPCF_PARITY_ALL = 0, NPCF_PARITY_EVEN = 1, NPCF_PARITY_ODD = 2 };
 
 typedef struct {
     int precision;  /* NPCF_FP32 (positions/weights float, pair and coupling arithmetic FP32,
-                       cross-primary sums FP64) or NPCF_FP64 (double throughout) */
+                       cross-primary sums FP64), NPCF_FP64 (double throughout), or
+                       NPCF_MIXED_BF16X3 / NPCF_MIXED_TF32X3 (float inputs, FP32 pairs,
+                       split-precision tensor-core coupling; see above) */
     int periodic;   /* 1: minimum image in the box; 0: open boundaries */
     int bin_order;  /* NPCF_BINS_LE (default) or NPCF_BINS_LT, N=3 only */
     int sync_check; /* 1 (default): npcf_compute waits for the stream and reports
@@ -79,9 +92,19 @@ typedef struct {
                        them later with npcf_device_status */
     int timing;     /* 1: record CUDA events between the stages of every compute
                        (read with npcf_last_profile); 0 (default): none */
+    int remove_self; /* 0 (default): keep the tuples whose secondaries coincide, as the
+                       naive N-tuplet sum of eq. NPCF-estimator-intro-discrete does; 1:
+                       subtract them exactly.  Only N=3 keys with b1 = b2 have such tuples:
+                       per primary j, sum_{k in b} w_k^2 c_l / v_b^2 is removed, c_l the
+                       basis at coinciding directions ((-1)^l sqrt(dim_l)/|S^{D-1}| for
+                       D >= 3, 1/(2 pi) for D = 2).  npcf_backward refuses such plans. */
+    int parity;     /* NPCF_PARITY_ALL (default), NPCF_PARITY_EVEN or NPCF_PARITY_ODD: the
+                       keys the plan returns (npcf_num_coeffs / npcf_coeff_index count and
+                       label only those) */
 } npcf_opts;
 
-/* Default options: FP32, periodic, b1 <= b2, sync_check = 1, timing = 0. */
+/* Default options: FP32, periodic, b1 <= b2, sync_check = 1, timing = 0, remove_self = 0,
+ * parity = NPCF_PARITY_ALL. */
 NPCF_API void npcf_default_opts(npcf_opts* opts);
 
 /*
@@ -224,13 +247,25 @@ NPCF_API npcf_status npcf_compute_noalloc(npcf_plan_t plan, const void* position
 /*
  * Work counters of the pair kernel in the last call (host, waits for its
  * stream), for profiling: [0] pairs, [1] candidate secondaries examined,
- * [2] consumption rounds, [3] lanes that found work in those rounds,
- * [4] candidate iterations of a warp (64 candidates each), [5] rounds forced
- * by full queues, [6] iterations with a pair in an edge-flagged table bucket,
- * [7] iterations with a pair decided in FP64.  Writes min(n, 8) entries (the
- * rest zero).
+ * [2] accumulation rounds of the warps' pair batches (each lane adds one pair
+ * per round), [3] lane-rounds that added a pair (= pairs; [3] / (32 [2]) is the
+ * lane fill), [4] candidate iterations of a warp (32 candidates each),
+ * [5] pair batches, [6] iterations with a pair in an edge-flagged table
+ * bucket, [7] iterations with a pair decided in FP64.  Writes min(n, 8)
+ * entries (the rest zero).
  */
 NPCF_API npcf_status npcf_last_counters(npcf_plan_t plan, int64_t* counters, int n);
+
+/*
+ * Diagnostic (no counterpart in the paper): the split-precision tensor-core contraction
+ * that the mixed couplings use, on caller data: d = a b^T with a 128 x k and b n x k
+ * (row-major FP32, device), d 128 x n (FP32, device, overwritten).  tf32 = 0 splits into
+ * BF16 pairs, 1 into TF32 pairs.  n a multiple of 16 in [16, 256]; k a positive multiple of
+ * 64 (BF16) or 32 (TF32), at most 4096.  One CTA; waits for the stream.  Errors:
+ * NPCF_ERR_ARG, NPCF_ERR_DEVICE_TIMEOUT (a bounded wait on the MMA ran out), NPCF_ERR_CUDA.
+ */
+NPCF_API npcf_status npcf_selftest_tc(int tf32, int n, int k, const float* a, const float* b, float* d,
+                                      npcf_stream_t stream);
 
 /* Thread-local description of the most recent error on this thread. */
 NPCF_API const char* npcf_last_error(void);

@@ -220,24 +220,30 @@ __global__ void k_totals(int ncells, const int* cell_prims, const int* prim_star
     }
 }
 
-__global__ void k_reduce_rows(const double* partial, int rows, int ncols, double scale, double* out)
+// out[k] = scale * sum_r partial[r][col(k)], k < nout, rows of ncols; col = colmap (the plan's
+// selected keys, e.g. one parity) or the identity
+__global__ void k_reduce_rows(const double* partial, int rows, int ncols, const int* colmap, int nout, double scale,
+                              double* out)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ncols) return;
+    if (k >= nout) return;
+    const int col = colmap ? colmap[k] : k;
     double s = 0.0;
-    for (int r = 0; r < rows; ++r) s += partial[(size_t)r * ncols + k];
+    for (int r = 0; r < rows; ++r) s += partial[(size_t)r * ncols + col];
     out[k] = s * scale;
 }
 
-__global__ void k_reduce_cats(const double* partial, int rows, int ncols, const double* scales, double* out)
+__global__ void k_reduce_cats(const double* partial, int rows, int ncols, const int* colmap, int nout,
+                              const double* scales, double* out)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ncols) return;
+    if (k >= nout) return;
     const int c = blockIdx.y;
+    const int col = colmap ? colmap[k] : k;
     const double* pc = partial + (size_t)c * rows * ncols;
     double s = 0.0;
-    for (int r = 0; r < rows; ++r) s += pc[(size_t)r * ncols + k];
-    out[(size_t)c * ncols + k] = s * scales[c];
+    for (int r = 0; r < rows; ++r) s += pc[(size_t)r * ncols + col];
+    out[(size_t)c * nout + k] = s * scales[c];
 }
 
 inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -317,20 +323,23 @@ cudaError_t launch_make_items(const ItemBuffers& b, const int* cell_start, const
     return cudaMemsetAsync(b.ticket, 0, sizeof(int), s);
 }
 
-cudaError_t launch_reduce(const double* partial, int rows, int ncols, double scale, double* out, cudaStream_t s)
+cudaError_t launch_reduce(const double* partial, int rows, int ncols, const int* colmap, int nout, double scale,
+                          double* out, cudaStream_t s)
 {
-    if (ncols <= 0) return cudaSuccess;
+    if (nout <= 0) return cudaSuccess;
     const int t = 256;
-    k_reduce_rows<<<blocks_for(ncols, t), t, 0, s>>>(partial, rows, ncols, scale, out); ++launch_counter();
+    k_reduce_rows<<<blocks_for(nout, t), t, 0, s>>>(partial, rows, ncols, colmap, nout, scale, out);
+    ++launch_counter();
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, int ncat, const double* scales, double* out,
-                               cudaStream_t s)
+cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, const int* colmap, int nout, int ncat,
+                               const double* scales, double* out, cudaStream_t s)
 {
-    if (ncols <= 0 || ncat <= 0) return cudaSuccess;
+    if (nout <= 0 || ncat <= 0) return cudaSuccess;
     const int t = 256;
-    k_reduce_cats<<<dim3(blocks_for(ncols, t), ncat), t, 0, s>>>(partial, rows, ncols, scales, out); ++launch_counter();
+    k_reduce_cats<<<dim3(blocks_for(nout, t), ncat), t, 0, s>>>(partial, rows, ncols, colmap, nout, scales, out);
+    ++launch_counter();
     return cudaGetLastError();
 }
 

@@ -41,13 +41,17 @@ struct Cx {
 enum { MODE_N3 = 0, MODE_D2N4 = 1 };
 
 // ------------------------------------------------------------------ N = 3
+// `self` (NULL unless the remove_self option is on): the primary's sums of w_k^2 per bin; for
+// keys with b1 = b2 the tuples with coinciding secondaries, w_k^2 c_l / v_b^2 per secondary
+// (c_l the basis value at coinciding directions), are subtracted.
 template <int D, typename T, typename AccT>
-__device__ __forceinline__ void body_n3(const CoupleParams& p, const T* a, T w, AccT* acc, int4 blk)
+__device__ __forceinline__ void body_n3(const CoupleParams& p, const T* a, const T* self, T w, AccT* acc, int4 blk)
 {
     const int L1 = p.lmax + 1;
     const int nq = p.nq;
     const int nitems = (blk.y - blk.x) * L1;
     const T* pref = static_cast<const T*>(p.pref);
+    const T* selfc = static_cast<const T*>(p.selfc);
     for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
         const int pr = blk.x + i / L1;
         const int l = i - (i / L1) * L1;
@@ -55,6 +59,7 @@ __device__ __forceinline__ void body_n3(const CoupleParams& p, const T* a, T w, 
         const T* u = a + bb.x * nq;
         const T* v = a + bb.y * nq;
         const int key = p.pair_key[pr] + l - blk.z;
+        const T dself = (self && bb.x == bb.y) ? selfc[bb.x * L1 + l] * self[bb.x] : T(0);
         if constexpr (D == 2) {
             T re, im;
             if (l == 0) {
@@ -65,7 +70,7 @@ __device__ __forceinline__ void body_n3(const CoupleParams& p, const T* a, T w, 
                 re = fma(u[q], v[q], u[q + 1] * v[q + 1]);
                 im = fma(u[q + 1], v[q], -(u[q] * v[q + 1]));
             }
-            acc[2 * key] += w * re;
+            acc[2 * key] += w * (re - dself);
             acc[2 * key + 1] += w * im;
         } else if constexpr (D == 3) {
             const int b0 = l * l;
@@ -75,7 +80,7 @@ __device__ __forceinline__ void body_n3(const CoupleParams& p, const T* a, T w, 
                 const int q = b0 + 2 * m - 1;
                 s1 = fma(u[q], v[q], fma(u[q + 1], v[q + 1], s1));
             }
-            acc[key] += w * pref[l] * fma(T(2), s1, s0);
+            acc[key] += w * fma(pref[l], fma(T(2), s1, s0), -dself);
         } else {
             T s0 = T(0), s1 = T(0);
             for (int l2 = 0; l2 <= l; ++l2) {
@@ -86,7 +91,7 @@ __device__ __forceinline__ void body_n3(const CoupleParams& p, const T* a, T w, 
                     s1 = fma(u[q], v[q], fma(u[q + 1], v[q + 1], s1));
                 }
             }
-            acc[key] += w * pref[l] * fma(T(2), s1, s0);
+            acc[key] += w * fma(pref[l], fma(T(2), s1, s0), -dself);
         }
     }
 }
@@ -123,9 +128,9 @@ __global__ void __launch_bounds__(kCoupleThreads) k_couple(const CoupleParams p)
     extern __shared__ __align__(16) unsigned char smem[];
     const int4 blk = p.kblocks[blockIdx.y];
     const int comps = (MODE == MODE_N3 && D != 2) ? 1 : 2;
-    int a_elems;  // T elements of the per-primary copy
+    int a_elems;  // T elements of the per-primary copy (N=3: a-row, then the nbins sums of w^2)
     if constexpr (MODE == MODE_D2N4) a_elems = p.nbins * (2 * p.lmax + 1) * 2;
-    else a_elems = p.nbins * p.nq;
+    else a_elems = p.nbins * p.nq + p.nbins;
     T* A = reinterpret_cast<T*>(smem);
     AccT* acc = reinterpret_cast<AccT*>(smem + ((a_elems * (int)sizeof(T) + 15) / 16) * 16);
     const int nacc = (blk.w - blk.z) * comps;
@@ -140,6 +145,7 @@ __global__ void __launch_bounds__(kCoupleThreads) k_couple(const CoupleParams p)
     const int stride = p.nbins * p.nq;
     const T* aglob = static_cast<const T*>(p.a) + first * stride;
     const T* wglob = static_cast<const T*>(p.wprim) + first;
+    const T* sglob = p.self ? static_cast<const T*>(p.self) + first * p.nbins : nullptr;
 
     for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
         const int p0 = ch * p.chunk;
@@ -160,10 +166,12 @@ __global__ void __launch_bounds__(kCoupleThreads) k_couple(const CoupleParams p)
                 }
             } else {
                 for (int i = threadIdx.x; i < stride; i += blockDim.x) A[i] = ap[i];
+                if (sglob)
+                    for (int i = threadIdx.x; i < p.nbins; i += blockDim.x) A[stride + i] = sglob[(size_t)pi * p.nbins + i];
             }
             const T w = wglob[pi];
             __syncthreads();
-            if constexpr (MODE == MODE_N3) body_n3<D, T, AccT>(p, A, w, acc, blk);
+            if constexpr (MODE == MODE_N3) body_n3<D, T, AccT>(p, A, sglob ? A + stride : nullptr, w, acc, blk);
             else body_d2n4<T, AccT>(p, reinterpret_cast<const Cx<T>*>(A), w, acc, blk);
         }
         __syncthreads();
@@ -278,7 +286,6 @@ int d2n4_group(int nbins, int lmax)
 
 int couple_smem(const CoupleParams& p, int fp64)
 {
-    if (p.N == 5) return couple_d3n5_smem(p, fp64);
     if (p.N == 4 && p.D == 3) return couple_d3n4_smem(p, fp64);
     if (p.N == 4 && p.D == 2 && !fp64) {
         const int G = d2n4_group(p.nbins, p.lmax);
@@ -291,7 +298,7 @@ int couple_smem(const CoupleParams& p, int fp64)
         a_elems = p.nbins * (2 * p.lmax + 1) * 2;
         comps = 2;
     } else {
-        a_elems = p.nbins * p.nq;
+        a_elems = p.nbins * p.nq + p.nbins;
         comps = p.D == 2 ? 2 : 1;
     }
     return (a_elems * tb + 15) / 16 * 16 + p.max_block_keys * comps * tb;
@@ -299,7 +306,6 @@ int couple_smem(const CoupleParams& p, int fp64)
 
 cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s)
 {
-    if (p.N == 5) return launch_couple_d3n5(p, fp64, grid, smem, s);
     if (p.N == 3) {
         switch (p.D * 2 + (fp64 ? 1 : 0)) {
             case 4: return launch_t<MODE_N3, 2, 0, float>(p, grid, smem, s);

@@ -1,0 +1,221 @@
+// npcf_couple_d3n5f.cu -- the D=3 isotropic 5PCF coupling (eq. D=3-NPCF) factored
+// through the intermediate label l12.  The CG chain of eq. Coupling-C,
+//     <l1 m1 l2 m2|l12 m12><l12 m12 l3 m3|l4 M><l4 M l4 m4|0 0>,  M = m12 + m3 = -m4,
+// splits the sum over (m1, m2, m3, m4) of one primary into
+//     zeta^{b1 b2 b3 b4}_{l1 l2 l12 l3 l4} += w_j sum_{m12} X_j(b1 b2; l1 l2 l12; m12) Z_j(b3 b4; l12 l3 l4; m12),
+//     X_j = sum_{m1} <l1 m1 l2 m12-m1|l12 m12> a^{b1}_{l1 m1} a^{b2}_{l2, m12-m1},
+//     Z_j = sum_{m3} <l12 m12 l3 m3|l4 M><l4 M l4 -M|0 0> a^{b3}_{l3 m3} a^{b4}_{l4, -M}.
+// For one l12 the sum over (j, m12) is a matrix product: rows (b1 < b2, l1, l2), columns
+// (b3 < b4, l3, l4), K = (primary, m12).  Only blocks with b2 < b3 and l1 + l2 + l3 + l4 even
+// are keys, so rows are ordered by (parity, b2) and columns by (parity, b3), and only tiles that
+// hold keys are computed.
+//
+// Per chunk of primaries: k_d3n5_form writes X (times w_j) and Z of each primary into a scratch
+// laid out K-contiguous per row (the chunk's X and Z stay in L2 for the contraction);
+// k_d3n5_contract runs the tiles, a 64 x 64 complex block per CTA with 4 x 4 per thread (rows
+// ty + 16 a, columns tx + 16 b),
+// K staged through shared memory, FP32 (or FP64) sums over the CTA's primaries added into its
+// FP64 partial row.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "npcf_device.cuh"
+#include "npcf_internal.h"
+
+namespace npcf {
+
+namespace {
+
+template <typename T>
+struct C5 {
+    T r, i;
+};
+
+constexpr int kFormThreads = 256;
+constexpr int kTile = 64;   // rows and columns of a contraction tile
+constexpr int kKc = 16;     // K entries per shared-memory stage
+constexpr int kConThreads = 256;
+
+// One primary per CTA: its a^b for all signed m in shared memory, then every X and Z entry.
+template <typename T>
+__global__ void __launch_bounds__(kFormThreads) k_d3n5_form(const D3n5Params q, int chunk0, int nchunk_prim)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nb = q.nbins, S = (q.lmax + 1) * (q.lmax + 1);
+    C5<T>* A = reinterpret_cast<C5<T>*>(smem);  // [nb][S]
+    const int jj = blockIdx.x;
+    const int cat = blockIdx.y;
+    const int nprim = q.cat_count ? q.cat_count[cat] : *q.nprim;
+    const size_t first = q.cat_first ? (size_t)q.cat_first[cat] : 0;
+    const int j = chunk0 + jj;
+    const bool live = jj < nchunk_prim && j < nprim;
+    const T* ap = static_cast<const T*>(q.a) + (first + (live ? j : 0)) * (size_t)nb * q.nq;
+    const T w = live ? static_cast<const T*>(q.wprim)[first + j] : T(0);
+    for (int i = threadIdx.x; i < nb * S; i += blockDim.x) {
+        const int b = i / S, s = i - b * S;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= s) ++l;
+        const int m = s - l * l - l, am = m < 0 ? -m : m;
+        T re = T(0), im = T(0);
+        if (live) {
+            const T* x = ap + b * q.nq + q_index_d3(l, am);
+            re = x[0];
+            im = am > 0 ? x[1] : T(0);
+            if (m < 0) {  // a_{l,-m} = (-1)^m conj(a_{l m})
+                im = -im;
+                if (am & 1) {
+                    re = -re;
+                    im = -im;
+                }
+            }
+        }
+        A[i] = C5<T>{re, im};
+    }
+    __syncthreads();
+    C5<T>* X = static_cast<C5<T>*>(q.xs) + (size_t)cat * q.xs_cat;
+    C5<T>* Z = static_cast<C5<T>*>(q.zs) + (size_t)cat * q.zs_cat;
+    const T* coef = static_cast<const T*>(q.coef);
+    // X entries: (group, bin pair); group = (l12, (l1, l2), m12) with its term list
+    const int nx = q.ngx * q.np12;
+    for (int e = threadIdx.x; e < nx; e += blockDim.x) {
+        const int g = e / q.np12, pr = e - g * q.np12;
+        const int4 G = q.gx[g];  // term begin, term end, l12, row-in-pair (ix) | m12 index << 16
+        const int2 bb = q.p12[pr];
+        const C5<T>* u = A + bb.x * S;
+        const C5<T>* v = A + bb.y * S;
+        T sr = T(0), si = T(0);
+        for (int t = G.x; t < G.y; ++t) {
+            const int st = q.terms[t];
+            const C5<T> x = u[st & 0xff], y = v[(st >> 8) & 0xff];
+            const T pr_ = x.r * y.r - x.i * y.i, pi_ = x.r * y.i + x.i * y.r;
+            sr = fma(coef[t], pr_, sr);
+            si = fma(coef[t], pi_, si);
+        }
+        const int l12 = G.z, ix = G.w & 0xffff, mi = G.w >> 16, K = 2 * l12 + 1;
+        const int row = q.xrow[q.row0[l12] + pr * q.nlx[l12] + ix];  // position in the (parity, b2) order
+        X[(size_t)q.xoff[l12] * q.npc + ((size_t)row * q.npc + jj) * K + mi] = C5<T>{w * sr, w * si};
+    }
+    const int nz = q.ngz * q.np34;
+    for (int e = threadIdx.x; e < nz; e += blockDim.x) {
+        const int g = e / q.np34, pr = e - g * q.np34;
+        const int4 G = q.gz[g];
+        const int2 bb = q.p34[pr];
+        const C5<T>* u = A + bb.x * S;
+        const C5<T>* v = A + bb.y * S;
+        T sr = T(0), si = T(0);
+        for (int t = G.x; t < G.y; ++t) {
+            const int st = q.terms[t];
+            const C5<T> x = u[st & 0xff], y = v[(st >> 8) & 0xff];
+            const T pr_ = x.r * y.r - x.i * y.i, pi_ = x.r * y.i + x.i * y.r;
+            sr = fma(coef[t], pr_, sr);
+            si = fma(coef[t], pi_, si);
+        }
+        const int l12 = G.z, iz = G.w & 0xffff, mi = G.w >> 16, K = 2 * l12 + 1;
+        const int col = q.zcol[q.col0[l12] + pr * q.nlz[l12] + iz];  // position in the (parity, b3) order
+        Z[(size_t)q.zoff[l12] * q.npc + ((size_t)col * q.npc + jj) * K + mi] = C5<T>{sr, si};
+    }
+}
+
+// One tile (l12, 64 rows, 64 columns) per blockIdx.x, one slice of the chunk's primaries per
+// blockIdx.y (its own partial row), catalogue blockIdx.z.
+template <typename T>
+__global__ void __launch_bounds__(kConThreads) k_d3n5_contract(const D3n5Params q, int nchunk_prim)
+{
+    __shared__ C5<T> Xs[kKc][kTile + 1];
+    __shared__ C5<T> Zs[kKc][kTile + 1];
+    const int4 tile = q.tiles[blockIdx.x];  // l12, first row, first column, -
+    const int l12 = tile.x, K1 = 2 * l12 + 1;
+    const int nrows = min(kTile, q.nlx[l12] * q.np12 - tile.y);
+    const int ncols = min(kTile, q.nlz[l12] * q.np34 - tile.z);
+    // rows and columns are in (parity, b2) and (parity, b3) order: row r and column c meet in a key
+    // when b2 < b3 and the parities agree
+    const int cat = blockIdx.z;
+    const C5<T>* X = static_cast<const C5<T>*>(q.xs) + (size_t)cat * q.xs_cat + (size_t)q.xoff[l12] * q.npc;
+    const C5<T>* Z = static_cast<const C5<T>*>(q.zs) + (size_t)cat * q.zs_cat + (size_t)q.zoff[l12] * q.npc;
+    // this CTA's primaries of the chunk
+    const int per = (nchunk_prim + gridDim.y - 1) / gridDim.y;
+    const int j0 = blockIdx.y * per, j1 = min(nchunk_prim, j0 + per);
+    const int k0 = j0 * K1, k1 = max(k0, j1 * K1);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T ar[4][4], ai[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ar[a][b] = ai[a][b] = T(0);
+    for (int kb = k0; kb < k1; kb += kKc) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kKc * kTile; i += kConThreads) {
+            const int r = i / kKc, k = i - r * kKc;  // K fastest: coalesced along a row
+            const int kk = kb + k;
+            const bool ok = kk < k1;
+            Xs[k][r] = (ok && r < nrows) ? X[(size_t)(tile.y + r) * q.npc * K1 + kk] : C5<T>{T(0), T(0)};
+            Zs[k][r] = (ok && r < ncols) ? Z[(size_t)(tile.z + r) * q.npc * K1 + kk] : C5<T>{T(0), T(0)};
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kKc; ++k) {
+            C5<T> x[4], z[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {  // rows ty + 16 a, columns tx + 16 b: conflict-free reads
+                x[a] = Xs[k][ty + 16 * a];
+                z[a] = Zs[k][tx + 16 * a];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    ar[a][b] = fma(x[a].r, z[b].r, fma(-x[a].i, z[b].i, ar[a][b]));
+                    ai[a][b] = fma(x[a].r, z[b].i, fma(x[a].i, z[b].r, ai[a][b]));
+                }
+        }
+    }
+    double* prow = q.partial + ((size_t)cat * gridDim.y + blockIdx.y) * 2 * q.ncoeff;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = ty + 16 * a;
+        if (r >= nrows) continue;
+        const int4 R = q.rowinfo[q.row0[l12] + tile.y + r];  // b1, b2, parity, l1 | l2 << 8
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int c = tx + 16 * b;
+            if (c >= ncols) continue;
+            const int4 C = q.colinfo[q.col0[l12] + tile.z + c];  // b3, b4, parity, l3 | l4 << 8
+            if (R.y >= C.x || R.z != C.z) continue;
+            const int L1 = q.lmax + 1;
+            const int l1 = R.w & 0xff, l2 = R.w >> 8, l3 = C.w & 0xff, l4 = C.w >> 8;
+            const int lam = q.lamidx[(((l1 * L1 + l2) * (2 * L1 - 1) + l12) * L1 + l3) * L1 + l4];
+            const int key = q.trikey[(R.x * q.nbins + R.y) * q.nbins + C.x] + (C.y - C.x - 1) * q.nlam + lam;
+            prow[2 * key] += (double)ar[a][b];
+            prow[2 * key + 1] += (double)ai[a][b];
+        }
+    }
+}
+
+}  // namespace
+
+int d3n5f_form_smem(int nbins, int lmax, int fp64)
+{
+    return nbins * (lmax + 1) * (lmax + 1) * 2 * (fp64 ? 8 : 4);
+}
+
+cudaError_t launch_d3n5f(const D3n5Params& q, int fp64, int nchunk_prim, int chunk0, int ksplit, int ncat,
+                         cudaStream_t s)
+{
+    const int fs = d3n5f_form_smem(q.nbins, q.lmax, fp64);
+    const dim3 fgrid(q.npc, ncat > 1 ? ncat : 1);
+    const dim3 cgrid(q.ntiles, ksplit, ncat > 1 ? ncat : 1);
+    if (fp64) {
+        k_d3n5_form<double><<<fgrid, kFormThreads, fs, s>>>(q, chunk0, nchunk_prim);
+        ++launch_counter();
+        k_d3n5_contract<double><<<cgrid, kConThreads, 0, s>>>(q, nchunk_prim);
+    } else {
+        k_d3n5_form<float><<<fgrid, kFormThreads, fs, s>>>(q, chunk0, nchunk_prim);
+        ++launch_counter();
+        k_d3n5_contract<float><<<cgrid, kConThreads, 0, s>>>(q, nchunk_prim);
+    }
+    ++launch_counter();
+    return cudaGetLastError();
+}
+
+}  // namespace npcf

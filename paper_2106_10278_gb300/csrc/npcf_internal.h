@@ -7,7 +7,7 @@
 
 namespace npcf {
 
-constexpr int kMaxBins = 32;   // lanes own bins in the pair kernel: at most one warp's worth
+constexpr int kMaxBins = 32;   // the pair kernel shares a warp's 32 lanes out among the bins
 constexpr int kMaxD = 4;
 constexpr int kTab = 4096;     // radial lookup-table entries
 
@@ -59,13 +59,7 @@ struct PairParams {
     float edgef[kMaxBins + 1];
     double edge2[kMaxBins + 1];  // FP64 squares, the exact bin decision
     float tab_lo, tab_inv;       // radial table: bucket k covers [tab_lo + k/tab_inv, ...)
-    signed char lane_bin[32];
-    signed char lane_rank[32];
-    signed char bin_nlanes[kMaxBins];
-    signed char bin_first[kMaxBins];
     int warps;                   // primaries per item (= warps per CTA)
-    int busy_round;              // run a consumption round when this many lanes have work
-    int tot_round;               // ... or when this many pairs are staged in total
     int nstencil;
     const int* stencil;          // packed offsets, 8 bits per axis (signed)
     const unsigned char* tab;    // kTab entries
@@ -78,7 +72,8 @@ struct PairParams {
     const void* inv_vb;          // nbins (T)
     void* a_out;                 // nprim x nbins x nq (T)
     void* w_out;                 // nprim (T)
-    unsigned long long* stats;   // [0] pairs, [1] candidates, [2] rounds, [3] busy lanes, [4] chunks, [5] forced rounds, [6] flagged-bucket iterations, [7] exact-FP64 iterations
+    void* self_out;              // nprim x nbins (T): sum of w_k^2 per bin, or NULL
+    unsigned long long* stats;   // [0] pairs, [1] candidates, [2] accumulation rounds, [3] busy lane-rounds, [4] chunks, [5] batches, [6] flagged-bucket iterations, [7] exact-FP64 iterations
 };
 
 // ----------------------------------------------------------- coupling kernel
@@ -100,17 +95,61 @@ struct CoupleParams {
     const int2* lam2;          // D=2, N=4: (l1, l2) per Lambda index
     const signed char* lam_odd;// D=3, N=4: 1 if l1+l2+l3 is odd (coefficient imaginary)
     const void* pref;          // N=3: per-l factor of the zero coupling (T)
-    int group;                 // D=2 N=4 FP32 and N=5: primaries per shared-memory group
-    int ntriple;               // N=5: bin triples b1 < b2 < b3 < nbins - 1
-    const int4* triples;       // N=5: (b1, b2, b3, first key) per triple
-    const int4* lam5;          // N=5: (first term, end term, l4, 0) per label set
-    const int* terms5;         // N=5: state(l1,m1) | state(l2,m2) << 8 | state(l3,m3) << 16 | m4 << 24
-    const double* coef5;       // N=5: the coupling coefficient of each term
-    const float* coef5f;       // N=5: the same in FP32 (FP32 plans)
+    int group;                 // D=2 N=4 FP32: primaries per shared-memory group
     int ncat;                  // catalogues (blockIdx.z); 0 or 1 for a single one
     const int* cat_first;      // ncat: first primary of each catalogue in the a-array (NULL: one catalogue)
     const int* cat_count;      // ncat: its primaries
+    // split-precision tensor-core coupling (npcf_couple_tc.cu)
+    int tc_npairs;             // bin pairs = MMA rows (at most 128)
+    int tc_glam;               // label sets per CTA (their accumulators share the CTA's TMEM)
+    int tc_tmem_cols;          // TMEM columns each CTA allocates (a power of two, <= 512)
+    int tc_span;               // chunks of primaries summed in FP32 before each FP64 flush
+    int* err;                  // error word: bit 2 = a bounded wait on the tensor core ran out
+    const void* self;          // N=3 remove_self: nprim x nbins sums of w_k^2 (T), or NULL
+    const void* selfc;         // nbins x (lmax + 1): coincident-direction value c_l / v_b^2 (T)
 };
+
+// ------------------------------------------------- factored 5PCF coupling
+// Tables and scratch of npcf_couple_d3n5f.cu (D=3, N=5, through the intermediate label l12).
+struct D3n5Params {
+    int nbins, lmax, nq, nlam, ncoeff;
+    int npc;                     // primaries per chunk: K = npc (2 l12 + 1) per row and column
+    const void* a;               // nprim x nbins x nq (T)
+    const void* wprim;           // nprim (T)
+    const int* nprim;
+    const int* cat_first;        // NULL: one catalogue
+    const int* cat_count;
+    int np12, np34;              // bin pairs (b1 < b2) with b2 <= nbins - 3; (b3 < b4) with b3 >= 2
+    const int2* p12;
+    const int2* p34;
+    int ngx, ngz;                // term groups of X and Z
+    const int4* gx;              // (term begin, term end, l12, ix | m12 index << 16)
+    const int4* gz;              // (term begin, term end, l12, iz | m12 index << 16)
+    const int* terms;            // state of the first a | state of the second a << 8
+    const void* coef;            // CG product of each term (T)
+    const int* nlx;              // per l12: (l1, l2) label pairs
+    const int* nlz;              // per l12: (l3, l4) label pairs
+    const int* row0;             // per l12: first row (and X row map entry)
+    const int* col0;             // per l12: first column (and Z column map entry)
+    const int* xrow;             // [row0 + pair * nlx + ix]: row position in (parity, b2) order
+    const int* zcol;             // [col0 + pair * nlz + iz]: column position in (parity, b3) order
+    const int4* rowinfo;         // by position: b1, b2, parity, l1 | l2 << 8
+    const int4* colinfo;         // by position: b3, b4, parity, l3 | l4 << 8
+    const long long* xoff;       // per l12: first element of its X block in the scratch, per primary of a
+    const long long* zoff;       //   chunk (complex elements; the block starts at xoff[l12] * npc)
+    int ntiles;
+    const int4* tiles;           // (l12, first row, first column, 0): the 64 x 64 blocks that hold keys
+    const int* lamidx;           // [l1][l2][l12][l3][l4] -> label-set index (or -1)
+    const int* trikey;           // [b1][b2][b3] -> first key of the bin triple
+    void* xs;                    // scratch: X of the chunk (complex T)
+    void* zs;                    // scratch: Z of the chunk
+    size_t xs_cat, zs_cat;       // complex elements per catalogue
+    double* partial;             // (catalogue, ksplit) rows x 2 ncoeff
+};
+
+int d3n5f_form_smem(int nbins, int lmax, int fp64);
+cudaError_t launch_d3n5f(const D3n5Params& q, int fp64, int nchunk_prim, int chunk0, int ksplit, int ncat,
+                         cudaStream_t s);
 
 // ------------------------------------------------------------- launchers
 // Each returns cudaSuccess or the launch error, and adds the kernels it
@@ -142,12 +181,20 @@ cudaError_t launch_make_items(const ItemBuffers& b, const int* cell_start, const
 cudaError_t launch_couple(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
 int couple_smem(const CoupleParams& p, int fp64);
 int d2n4_group(int nbins, int lmax);
-int d3n5_group(int nbins, int lmax, int fp64);
-int couple_d3n5_smem(const CoupleParams& p, int fp64);
-cudaError_t launch_couple_d3n5(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
-cudaError_t launch_reduce(const double* partial, int rows, int ncols, double scale, double* out, cudaStream_t s);
-// per catalogue c: out[c][k] = scales[c] * sum_r partial[c][r][k]
-cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, int ncat, const double* scales, double* out,
+// out[k] = scale * sum_r partial[r][colmap[k]] (colmap NULL: the identity), k < nout
+cudaError_t launch_reduce(const double* partial, int rows, int ncols, const int* colmap, int nout, double scale,
+                          double* out, cudaStream_t s);
+// per catalogue c: out[c][k] = scales[c] * sum_r partial[c][r][colmap[k]]
+cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, const int* colmap, int nout, int ncat,
+                               const double* scales, double* out, cudaStream_t s);
+
+// split-precision tensor-core couplings (npcf_couple_tc.cu)
+int couple_tc_smem(int nbins, int nq, int tf32);
+int couple_tc_n(int nbins);
+int couple_tc_chunk(int tf32);
+cudaError_t launch_couple_d2n4_tc(const CoupleParams& p, int tf32, int rows, int groups, int smem, cudaStream_t s);
+int tc_selftest_smem();
+cudaError_t launch_tc_selftest(int tf32, const float* A, const float* B, float* D, int N, int K, int* err,
                                cudaStream_t s);
 
 // adjoint of the N=3 estimator (npcf_backward.cu)

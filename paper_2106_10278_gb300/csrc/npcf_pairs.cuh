@@ -11,12 +11,14 @@
 //    primary cannot reach, and streams the candidates from global memory
 //    (L1/L2 resident) with a two-deep register prefetch -- no block barriers
 //    while scanning.
-//  * Lanes own radial bins: lane l accumulates only bin lane_bin[l] (the host
-//    gives big shells more lanes).  A candidate that falls in bin b is
-//    appended to a per-(warp, bin) queue in shared memory; when enough are
-//    queued, every lane pops one pair of its own bin and adds w Y* for all
-//    (l, m) into registers.  No cross-lane reduction happens until the
-//    primary is finished.
+//  * Accepted pairs (unit separation, weight, bin) are compacted into a
+//    per-warp batch in shared memory.  A full batch is counting-sorted by bin
+//    (arrival order kept inside a bin), the 32 lanes are shared out among the
+//    bins in proportion to this batch's own counts (a lane accumulates pairs
+//    of one bin), every lane adds w Y* for all components of its pairs into
+//    registers, and the lanes' sums are merged into the warp's per-bin
+//    accumulators in shared memory.  Every sum runs in a fixed order, so the
+//    results are bitwise reproducible.
 //  * The bin of a pair is decided exactly as the FP64 definition decides it:
 //    FP32 distances pick the bin, and any pair within a few FP32 ulps of an
 //    edge is re-decided from the original coordinates in FP64.
@@ -35,32 +37,30 @@ struct PairCfg {
     static constexpr int kThreads = (sizeof(T) == 4) ? (NQ <= 64 ? 512 : 256) : (NQ <= 40 ? 256 : 128);
 };
 
-// staged pairs per warp (shared by all bins): 416 16-byte records (D <= 3, FP32) keep the
-// CTA within the 196 KB shared-memory carveout; larger records get 320
-__host__ __device__ constexpr int pool_slots(int rec_bytes) { return rec_bytes <= 16 ? 416 : 320; }
-constexpr int kQCap = 192;      // entries of one bin's index queue
+// Pairs per warp batch: 512 records of 16 bytes (FP32, D <= 3), 256 of the larger records.
+__host__ __device__ constexpr int pair_batch(int rec_bytes) { return rec_bytes <= 16 ? 512 : 256; }
 
 // Shared-memory carve-up of one CTA (host and device must agree):
-//   radial table + edges + lane map | job lists + scan scratch | the item's CatGeom
-//   | per warp: [fstack[slots] u16 | binq[nbins][kQCap] u16 | pool of `slots` records]
-// where the pool region also holds the final cross-lane reduction scratch.  Queue
-// lengths and the free-stack top live in registers (lane b keeps bin b's length).
-__host__ __device__ inline int pair_pool_bytes(int rec_bytes, int t_bytes, int nq_compiled)
+//   radial table + edges | job lists + scan scratch | the item's CatGeom
+//   | per warp: [records (also the merge scratch) | acc[nbins][nq] | bins u8 | idx u16 | 4 x 32 ints
+//                | sum of w^2 per bin (32)]
+__host__ __device__ inline int pair_rec_region(int rec_bytes, int t_bytes, int nq_compiled)
 {
-    const int pool = pool_slots(rec_bytes) * rec_bytes;
+    const int recs = pair_batch(rec_bytes) * rec_bytes;
     const int scratch = 32 * (nq_compiled + 1) * t_bytes;
-    return pool > scratch ? pool : scratch;
+    return ((recs > scratch ? recs : scratch) + 15) / 16 * 16;
 }
 
 __host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int nbins, int nq_compiled)
 {
-    const int head = pool_slots(rec_bytes) * 2 + nbins * kQCap * 2;
-    return ((head + 15) / 16) * 16 + ((pair_pool_bytes(rec_bytes, t_bytes, nq_compiled) + 15) / 16) * 16;
+    const int B = pair_batch(rec_bytes);
+    return pair_rec_region(rec_bytes, t_bytes, nq_compiled) + (nbins * nq_compiled * t_bytes + 15) / 16 * 16 +
+           (3 * B + 15) / 16 * 16 + 4 * 32 * 4 + 32 * t_bytes;
 }
 
 constexpr int kMaxJobs = 640;   // neighbour cells of one item (the largest stencil used: 613 cells, D=3 c=4)
 
-// fixed part: radial table | edges + lane map (576) | job lists + scan scratch | the item's CatGeom
+// fixed part: radial table | edges (576) | job lists + scan scratch | the item's CatGeom
 constexpr int kGeomOffset = kTab + 576 + (3 * kMaxJobs + 4 + 72) * 4;
 __host__ __device__ inline int pair_fixed_bytes(int rec_bytes, int threads)
 {
@@ -234,13 +234,126 @@ __device__ __forceinline__ Rec<D, T> ldg_rec(const Rec<D, T>* src, int i)
     return u.r;
 }
 
+// One batch of a warp's accepted pairs: sort by bin, share the lanes out, accumulate, merge.
+// recs/bins hold nbuf entries; acc_s[nbins][NQ] receives the sums of w Y* and w2_s[nbins] those
+// of w^2 (the coincident-secondary terms that the remove_self option subtracts); acc is the
+// lane's register accumulator (zero on entry and on exit).  hist, cursor, segf, segn, segbin:
+// 32 ints each.
+template <int D, int LMAX, typename T>
+__device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned char* bins, unsigned short* idx,
+                                                 T* acc_s, T* w2_s, int* hist, int* cursor, int* seg, int nbuf,
+                                                 int nbins, T* acc, unsigned& nrounds)
+{
+    constexpr int NQ = PairCfg<D, LMAX, T>::NQ;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int* segf = seg;        // first lane of bin b's segment
+    int* segn = seg + 32;   // its lanes (0: the bin has no pair in this batch)
+    int* segbin = hist;     // reused after the histogram: bin of the k-th segment
+    // 1. histogram of the batch's bins
+    hist[lane] = 0;
+    __syncwarp();
+    for (int i = lane; i < nbuf; i += 32) atomicAdd(&hist[bins[i]], 1);
+    __syncwarp();
+    const int cnt = lane < nbins ? hist[lane] : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int start = incl - cnt;
+    // 2. rounds R: the fewest with sum_b ceil(n_b / R) <= 32 lanes
+    int R = (nbuf + 31) >> 5, nl = 0;
+    for (;;) {
+        nl = cnt > 0 ? (cnt + R - 1) / R : 0;
+        if (__reduce_add_sync(full, nl) <= 32) break;
+        ++R;
+    }
+    nrounds += (unsigned)R;
+    int ninc = nl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(full, ninc, o);
+        if (lane >= o) ninc += v;
+    }
+    const int first = ninc - nl;
+    const unsigned E = __ballot_sync(full, nl > 0);
+    __syncwarp();
+    segf[lane] = first;
+    segn[lane] = nl;
+    if (nl > 0) segbin[__popc(E & lt_mask)] = lane;
+    cursor[lane] = start;
+    // 3. this lane's segment: the one that starts at or below it
+    const unsigned S = __reduce_or_sync(full, nl > 0 ? (1u << (first & 31)) : 0u);
+    const unsigned below = S & (0xffffffffu >> (31 - lane));
+    const int s0 = 31 - __clz(below);
+    __syncwarp();
+    const int my_bin = segbin[__popc(S & ((1u << s0) - 1u))];
+    const int my_rank = lane - s0;
+    const int my_nl = __shfl_sync(full, nl, my_bin);
+    const int my_start = __shfl_sync(full, start, my_bin);
+    const int my_cnt = __shfl_sync(full, cnt, my_bin);
+    // 4. indices sorted by bin, arrival order kept within a bin
+    for (int i0 = 0; i0 < nbuf; i0 += 32) {
+        const int i = i0 + lane;
+        const bool v = i < nbuf;
+        const int b = v ? (int)bins[i] : 64 + lane;
+        const unsigned peers = __match_any_sync(full, b);
+        const int rank = __popc(peers & lt_mask);
+        const int base = v ? cursor[b] : 0;
+        __syncwarp();
+        if (v) {
+            idx[base + rank] = (unsigned short)i;
+            if (rank == 0) cursor[b] = base + __popc(peers);
+        }
+        __syncwarp();
+    }
+    // 5. every lane accumulates the pairs of its bin, lanes of one bin taking every my_nl-th
+    T w2 = T(0);
+    if (my_rank < my_nl) {
+        for (int k = my_rank; k < my_cnt; k += my_nl) {
+            const Rec<D, T> e = recs[idx[my_start + k]];
+            if constexpr (D == 2) accum_d2<LMAX, T>(acc, e.x(0), e.x(1), e.w());
+            else if constexpr (D == 3) accum_d3<LMAX, T>(acc, e.x(0), e.x(1), e.x(2), e.w());
+            else accum_d4<LMAX, T>(acc, e.x(0), e.x(1), e.x(2), e.x(3), e.w());
+            w2 = fma(e.w(), e.w(), w2);
+        }
+    }
+    __syncwarp();
+    // 6. merge: the lanes' sums through the record space into acc_s (segments in lane order)
+    T* scr = reinterpret_cast<T*>(recs);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        scr[lane * (NQ + 1) + q] = acc[q];
+        acc[q] = T(0);
+    }
+    scr[lane * (NQ + 1) + NQ] = w2;
+    __syncwarp();
+    if (lane < nbins) {
+        const int f = segf[lane], n = segn[lane];
+        T sum = T(0);
+        for (int l = 0; l < n; ++l) sum += scr[(f + l) * (NQ + 1) + NQ];
+        w2_s[lane] += sum;
+    }
+    for (int o = lane; o < nbins * NQ; o += 32) {
+        const int b = o / NQ, q = o - b * NQ;
+        const int f = segf[b], n = segn[b];
+        T sum = T(0);
+        for (int l = 0; l < n; ++l) sum += scr[(f + l) * (NQ + 1) + q];
+        acc_s[o] += sum;
+    }
+    __syncwarp();
+}
+
 template <int D, int LMAX, typename T>
 __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(const PairParams p)
 {
     using R = Rec<D, T>;
     constexpr int NQ = PairCfg<D, LMAX, T>::NQ;
     constexpr bool kFP32 = sizeof(T) == 4;
-    constexpr int kPool = pool_slots((int)sizeof(R));
+    constexpr int kB = pair_batch((int)sizeof(R));
     const unsigned full = 0xffffffffu;
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -251,8 +364,6 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     unsigned char* tab = smem;
     float* s_edge = reinterpret_cast<float*>(tab + kTab);          // nbins + 1
     double* s_edge2 = reinterpret_cast<double*>(tab + kTab + 192);  // nbins + 1
-    signed char* s_first = reinterpret_cast<signed char*>(tab + kTab + 192 + 272);
-    signed char* s_nl = s_first + 32;
     int* job_a = reinterpret_cast<int*>(tab + kTab + 576);  // kMaxJobs: first slot of the cell
     int* job_pk = job_a + kMaxJobs;                          // kMaxJobs: packed stencil offset
     int* job_pre = job_pk + kMaxJobs;                        // kMaxJobs + 1: record prefix
@@ -260,10 +371,14 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     CatGeom* s_geo = reinterpret_cast<CatGeom*>(smem + kGeomOffset);
     unsigned char* wbase = smem + pair_fixed_bytes(sizeof(R), nthreads) +
                            warp * pair_warp_bytes(sizeof(R), sizeof(T), nbins, NQ);
-    unsigned short* fstack = reinterpret_cast<unsigned short*>(wbase);
-    unsigned short* binq = fstack + kPool;
-    R* pool = reinterpret_cast<R*>(wbase + ((kPool * 2 + nbins * kQCap * 2 + 15) / 16) * 16);  // as pair_warp_bytes
-    T* scratch = reinterpret_cast<T*>(pool);
+    R* recs = reinterpret_cast<R*>(wbase);
+    T* acc_s = reinterpret_cast<T*>(wbase + pair_rec_region(sizeof(R), sizeof(T), NQ));
+    unsigned char* bins = reinterpret_cast<unsigned char*>(acc_s) + (nbins * NQ * (int)sizeof(T) + 15) / 16 * 16;
+    unsigned short* idx = reinterpret_cast<unsigned short*>(bins + kB);
+    int* hist = reinterpret_cast<int*>(bins + (3 * kB + 15) / 16 * 16);
+    int* cursor = hist + 32;
+    int* seg = cursor + 32;  // 64 ints
+    T* w2_s = reinterpret_cast<T*>(seg + 64);  // 32
 
     for (int i = threadIdx.x; i < kTab / 4; i += nthreads)
         reinterpret_cast<int*>(tab)[i] = reinterpret_cast<const int*>(p.tab)[i];
@@ -271,19 +386,10 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         s_edge[threadIdx.x] = p.edgef[threadIdx.x];
         s_edge2[threadIdx.x] = p.edge2[threadIdx.x];
     }
-    if (threadIdx.x < nbins) {
-        s_first[threadIdx.x] = p.bin_first[threadIdx.x];
-        s_nl[threadIdx.x] = p.bin_nlanes[threadIdx.x];
-    }
-    const int mybin = p.lane_bin[lane];
-    const int myrank = p.lane_rank[lane];
-    const int mynl = p.bin_nlanes[mybin];
-    const int lane_nl = lane < nbins ? p.bin_nlanes[lane] : 0;
     const T* qnorm = static_cast<const T*>(p.qnorm);
     const T* inv_vb = static_cast<const T*>(p.inv_vb);
     const R* rec = static_cast<const R*>(p.rec);
     const int nq = p.nq;
-    const float tol = p.tol;
 
     __shared__ int s_item;
     for (;;) {
@@ -354,45 +460,13 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         T acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = T(0);
-        int qlen = 0;                   // lane b < nbins: length of bin b's queue
-        int ftop_r = kPool, tot_r = 0;  // warp-uniform: free-stack top, staged pairs
-        for (int i = lane; i < kPool; i += 32) fstack[i] = (unsigned short)i;
+        for (int i = lane; i < nbins * NQ; i += 32) acc_s[i] = T(0);
+        w2_s[lane] = T(0);
         __syncwarp();
+        int nbuf = 0;  // warp-uniform: staged pairs of the current batch
         unsigned npairs = 0;
         unsigned long long ncand = 0;
-        unsigned nrounds = 0, nbusy = 0, nchunks = 0, nforced = 0, nflag = 0, nexact = 0;
-
-        // one consumption round: every lane pops one staged pair of its own bin
-        auto round = [&]() {
-            const int q = __shfl_sync(full, qlen, mybin);
-            const bool has = myrank < q;
-            ++nrounds;
-            nbusy += has ? 1u : 0u;
-            int idx = 0;
-            if (has) {
-                idx = binq[mybin * kQCap + (q - 1 - myrank)];
-                const R e = pool[idx];
-                accum_pair<D, LMAX, T>(acc, e);
-            }
-            const unsigned fm = __ballot_sync(full, has);
-            if (has) fstack[ftop_r + __popc(fm & lt_mask)] = (unsigned short)idx;
-            ftop_r += __popc(fm);
-            tot_r -= __popc(fm);
-            qlen = qlen > lane_nl ? qlen - lane_nl : 0;
-            __syncwarp();
-        };
-        auto consume = [&](bool drain) {
-            for (;;) {
-                const int tot = tot_r;
-                if (tot == 0) break;
-                const int busy = __reduce_add_sync(full, qlen < lane_nl ? qlen : lane_nl);
-                const bool over = __any_sync(full, qlen > kQCap - 32) || tot > kPool - 32;
-                const bool want = busy >= p.busy_round || tot >= p.tot_round;
-                if (!drain && !want && !over) break;
-                if (!drain && !want) ++nforced;
-                round();
-            }
-        };
+        unsigned nrounds = 0, nbatch = 0, nchunks = 0, nflag = 0, nexact = 0;
 
         // every warp walks the item's cells on its own, streaming candidates from
         // global memory (L1/L2) with a two-deep register prefetch: no block barriers
@@ -428,70 +502,63 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                     ++nchunks;
                     nflag += __any_sync(full, anyflag) ? 1u : 0u;
                     nexact += __any_sync(full, anyexact) ? 1u : 0u;
-                    // stage the pair: a pool slot from the free stack, its index on the bin queue
+                    // compact the accepted pairs into the batch: unit separation, weight, bin
                     const bool take = bin >= 0;
                     const unsigned tm = __ballot_sync(full, take);
                     if (tm == 0u) continue;
-                    // lanes staging into the same bin: AND of the ballots of the bin's bits
-                    unsigned peers = tm, mine = tm;  // mine: lanes staging into bin `lane`
-#pragma unroll
-                    for (int kb = 0; kb < 5; ++kb) {
-                        const unsigned bk = __ballot_sync(full, (bin >> kb) & 1);
-                        peers &= ((bin >> kb) & 1) ? bk : ~bk;
-                        mine &= ((lane >> kb) & 1) ? bk : ~bk;
-                    }
-                    const int rank = __popc(peers & lt_mask);
-                    const int base = __shfl_sync(full, qlen, take ? bin : 0);
                     if (take) {
-                        const int slot = fstack[ftop_r - 1 - __popc(tm & lt_mask)];
+                        const int slot = nbuf + __popc(tm & lt_mask);
                         R e;
                         T* f = reinterpret_cast<T*>(e.v);
                         const T rinv = rsqrt_t(r2);
 #pragma unroll
                         for (int d = 0; d < D; ++d) f[d] = dx[d] * rinv;
                         f[D] = pk.w();
-                        pool[slot] = e;
-                        binq[bin * kQCap + base + rank] = (unsigned short)slot;
+                        recs[slot] = e;
+                        bins[slot] = (unsigned char)bin;
                         ++npairs;
                     }
-                    if (lane < nbins) qlen += __popc(mine);
-                    ftop_r -= __popc(tm);
-                    tot_r += __popc(tm);
-                    __syncwarp();
-                    consume(false);
+                    nbuf += __popc(tm);
+                    if (nbuf > kB - 32) {
+                        __syncwarp();
+                        pair_batch_flush<D, LMAX, T>(recs, bins, idx, acc_s, w2_s, hist, cursor, seg, nbuf,
+                                                     nbins, acc, nrounds);
+                        nbuf = 0;
+                        ++nbatch;
+                    }
                 }
             }
+            if (nbuf > 0) {
+                __syncwarp();
+                pair_batch_flush<D, LMAX, T>(recs, bins, idx, acc_s, w2_s, hist, cursor, seg, nbuf, nbins, acc,
+                                             nrounds);
+                ++nbatch;
+            }
         }
-        consume(true);
         // statistics
         {
             const unsigned tot = __reduce_add_sync(full, npairs);
-            const unsigned busy = __reduce_add_sync(full, nbusy);
             if (lane == 0 && active) {
                 atomicAdd(&p.stats[0], (unsigned long long)tot);
                 atomicAdd(&p.stats[1], ncand);
                 atomicAdd(&p.stats[2], (unsigned long long)nrounds);
-                atomicAdd(&p.stats[3], (unsigned long long)busy);
+                atomicAdd(&p.stats[3], (unsigned long long)tot);
                 atomicAdd(&p.stats[4], (unsigned long long)nchunks);
-                atomicAdd(&p.stats[5], (unsigned long long)nforced);
+                atomicAdd(&p.stats[5], (unsigned long long)nbatch);
                 atomicAdd(&p.stats[6], (unsigned long long)nflag);
                 atomicAdd(&p.stats[7], (unsigned long long)nexact);
             }
         }
-        // reduce the lanes of each bin and write a^b (normalised)
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) scratch[lane * (NQ + 1) + q] = acc[q];
+        // write a^b (normalised)
         __syncwarp();
         if (active) {
             T* aout = static_cast<T*>(p.a_out) + (size_t)pidx * nbins * nq;
             for (int i = lane; i < nbins * nq; i += 32) {
                 const int b = i / nq, q = i - b * nq;
-                const int f0 = s_first[b], nl = s_nl[b];
-                T sum = T(0);
-                for (int r = 0; r < nl; ++r) sum += scratch[(f0 + r) * (NQ + 1) + q];
-                aout[i] = sum * qnorm[q] * inv_vb[b];
+                aout[i] = acc_s[b * NQ + q] * qnorm[q] * inv_vb[b];
             }
             if (lane == 0) static_cast<T*>(p.w_out)[pidx] = wj;
+            if (p.self_out && lane < nbins) static_cast<T*>(p.self_out)[(size_t)pidx * nbins + lane] = w2_s[lane];
         }
         __syncwarp();
     }

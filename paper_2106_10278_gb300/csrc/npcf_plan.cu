@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <random>
 #include <string>
@@ -88,20 +89,23 @@ struct npcf_plan_s {
     int D = 3, N = 3, lmax = 0, nbins = 0;
     npcf_opts opts{};
     int fp64 = 0;
+    int mixed = 0;  // split-precision tensor-core coupling: 0 none, 1 BF16x3, 2 TF32x3
     std::vector<double> edges;
     double box[4] = {1, 1, 1, 1};
     double V = 1.0;
     // keys
     int nlam = 0;
     std::vector<int> lam;       // nlam x 3
-    int64_t ncoeff = 0;
-    std::vector<int> key_bins;  // ncoeff x 3
+    int64_t ncoeff = 0;         // keys the kernels compute
+    std::vector<int> key_bins;  // ncoeff x 4
     std::vector<int> key_lam;   // ncoeff
+    int64_t nvis = 0;           // keys the caller sees (the opts.parity selection of the computed keys)
+    std::vector<int64_t> vis;   // nvis: computed key of each visible key
     // coupling structure
     std::vector<int2> pairs;
     std::vector<int> pair_key;
     std::vector<int4> kblocks;
-    std::vector<int4> triples;  // N=5: (b1, b2, b3, first key)
+    std::vector<int4> triples;  // N=5: (b1, b2, b3, first key) of the bin triples that have a b4
     int max_block_keys = 0;
     int max_block_pairs = 0;
     std::vector<int> task_pairs;
@@ -113,7 +117,14 @@ struct npcf_plan_s {
     PairParams pp{};
     // device tables
     DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil, d_task;
-    DevBuf d_triples, d_lam5, d_terms5, d_coef5, d_coef5f;  // N=5 coupling tables
+    // N=5: the factored coupling's tables (npcf_couple_d3n5f.cu) and its per-chunk scratch
+    DevBuf d5_p12, d5_p34, d5_gx, d5_gz, d5_terms, d5_coef, d5_nlx, d5_nlz, d5_row0, d5_col0, d5_xrow, d5_zcol;
+    DevBuf d5_rowinfo, d5_colinfo, d5_xoff, d5_zoff, d5_tiles, d5_lamidx, d5_trikey, w_x5, w_z5;
+    D3n5Params d5{};           // host copy with the device table pointers (scratch set per call)
+    int64_t d5_unit_x = 0, d5_unit_z = 0;  // complex scratch elements per primary of a chunk
+    DevBuf d_colmap;  // 2*nvis computed columns of the visible outputs (when a parity is selected)
+    DevBuf d_selfc;   // remove_self (N=3): c_l / v_b^2 per (bin, l)
+    DevBuf w_self;    // remove_self (N=3): sum of w_k^2 per (primary, bin)
     // workspace
     DevBuf w_cid, w_perm, w_rec, w_cells, w_items, w_a, w_wprim, w_partial, w_small, w_hpos, w_hw, w_hout;
     // adjoint (npcf_backward)
@@ -219,6 +230,15 @@ void build_keys(npcf_plan_s* P)
             }
     }
     P->ncoeff = (int64_t)P->key_lam.size();
+    // the caller's keys: all, or one parity of (-1)^(l1+l2+l3) (only the D=3 4PCF has both)
+    P->vis.clear();
+    for (int64_t i = 0; i < P->ncoeff; ++i) {
+        const int* l = &P->lam[5 * P->key_lam[i]];
+        const int odd = (P->N == 4 && P->D == 3) ? ((l[0] + l[1] + l[2]) & 1) : 0;
+        if (P->opts.parity == NPCF_PARITY_ALL || odd == (P->opts.parity == NPCF_PARITY_ODD ? 1 : 0))
+            P->vis.push_back(i);
+    }
+    P->nvis = (int64_t)P->vis.size();
 }
 
 // Split the pair list into blocks whose keys fit the shared accumulators.
@@ -406,40 +426,6 @@ CatGeom make_geom(int D, const int* nc, const double* box, int base, int64_t fir
     return g;
 }
 
-// ------------------------------------------------------------ lane map
-void lane_map(npcf_plan_s* P)
-{
-    const int nb = P->nbins, D = P->D;
-    std::vector<double> share(nb);
-    double tot = 0.0;
-    for (int b = 0; b < nb; ++b) {
-        share[b] = std::pow(P->edges[b + 1], D) - std::pow(P->edges[b], D);
-        tot += share[b];
-    }
-    std::vector<int> lanes(nb, 1);
-    for (int k = nb; k < 32; ++k) {
-        int best = 0;
-        double bv = -1.0;
-        for (int b = 0; b < nb; ++b) {
-            const double v = share[b] / tot / lanes[b];
-            if (v > bv) {
-                bv = v;
-                best = b;
-            }
-        }
-        lanes[best]++;
-    }
-    int l = 0;
-    for (int b = 0; b < nb; ++b) {
-        P->pp.bin_first[b] = (signed char)l;
-        P->pp.bin_nlanes[b] = (signed char)lanes[b];
-        for (int r = 0; r < lanes[b]; ++r, ++l) {
-            P->pp.lane_bin[l] = (signed char)b;
-            P->pp.lane_rank[l] = (signed char)r;
-        }
-    }
-}
-
 int pair_compiled_lmax(int D, int fp64, int lmax)
 {
     if (D == 2) return pair_compiled_lmax_d2(fp64, lmax);
@@ -477,6 +463,252 @@ npcf_status ensure_device(npcf_plan_s* P)
 // (one CTA per SM: its group of a-rows fills shared memory).
 bool d2n4_registers(const npcf_plan_s* P) { return P->N == 4 && P->D == 2 && !P->fp64; }
 
+// Plans whose coupling runs on the tensor cores in split precision (BF16x3 or TF32x3).
+bool tc_coupling(const npcf_plan_s* P) { return P->mixed != 0 && P->D == 2 && P->N == 4; }
+
+// label sets per CTA of the tensor-core coupling: as many MMA accumulators (128 x N FP32) as
+// fit the 512 TMEM columns of an SM
+int tc_glam(const npcf_plan_s* P) { return std::max(1, 512 / couple_tc_n(P->nbins)); }
+int tc_groups(const npcf_plan_s* P) { return (P->nlam + tc_glam(P) - 1) / tc_glam(P); }
+
+// chunks of primaries summed in FP32 (in TMEM) before each FP64 flush; NPCF_TC_SPAN overrides
+int tc_span()
+{
+    if (const char* e = std::getenv("NPCF_TC_SPAN")) {
+        const int v = std::atoi(e);
+        if (v > 0 && v <= 1024) return v;
+    }
+    return 8;
+}
+
+// ----------------------------------------------------- factored 5PCF tables
+// The tables of the 5PCF coupling through the intermediate label (npcf_couple_d3n5f.cu): bin
+// pairs, the (l1, l2) and (l3, l4) label pairs of every l12, the CG terms of X and Z, the rows
+// (columns) of every l12 in (parity, b2) ((parity, b3)) order, the tiles that hold keys, and
+// the key maps.  The CG chain is the one of eq. Coupling-C with the CGs of eq. CG-examples.
+npcf_status build_d3n5f_tables(npcf_plan_s* P)
+{
+    const int L = P->lmax, nb = P->nbins, NL = 2 * L + 1;
+    auto cg = [](int j1, int m1, int j2, int m2, int J, int M) {
+        return cx::neg1_pow(j1 - j2 + M) * std::sqrt(2.0 * J + 1.0) * cx::wigner3j(j1, j2, J, m1, m2, -M);
+    };
+    auto st = [](int l, int m) { return l * l + l + m; };
+    std::vector<int2> p12, p34;
+    for (int b2 = 1; b2 <= nb - 3; ++b2)
+        for (int b1 = 0; b1 < b2; ++b1) p12.push_back(make_int2(b1, b2));
+    for (int b3 = 2; b3 <= nb - 2; ++b3)
+        for (int b4 = b3 + 1; b4 < nb; ++b4) p34.push_back(make_int2(b3, b4));
+    std::vector<std::vector<int2>> lx(NL), lz(NL);
+    for (int l12 = 0; l12 < NL; ++l12)
+        for (int a = 0; a <= L; ++a)
+            for (int b = 0; b <= L; ++b) {
+                if (std::abs(a - b) <= l12 && l12 <= a + b) lx[l12].push_back(make_int2(a, b));
+                if (std::abs(l12 - a) <= b && b <= l12 + a) lz[l12].push_back(make_int2(a, b));
+            }
+    std::vector<int4> gx, gz;
+    std::vector<int> terms;
+    std::vector<double> coef;
+    for (int l12 = 0; l12 < NL; ++l12) {
+        for (int ix = 0; ix < (int)lx[l12].size(); ++ix) {
+            const int l1 = lx[l12][ix].x, l2 = lx[l12][ix].y;
+            for (int m12 = -l12; m12 <= l12; ++m12) {
+                const int t0 = (int)terms.size();
+                for (int m1 = -l1; m1 <= l1; ++m1) {
+                    const int m2 = m12 - m1;
+                    if (std::abs(m2) > l2) continue;
+                    const double c = cg(l1, m1, l2, m2, l12, m12);
+                    if (c == 0.0) continue;
+                    terms.push_back(st(l1, m1) | (st(l2, m2) << 8));
+                    coef.push_back(c);
+                }
+                gx.push_back(make_int4(t0, (int)terms.size(), l12, ix | ((m12 + l12) << 16)));
+            }
+        }
+        for (int iz = 0; iz < (int)lz[l12].size(); ++iz) {
+            const int l3 = lz[l12][iz].x, l4 = lz[l12][iz].y;
+            for (int m12 = -l12; m12 <= l12; ++m12) {
+                const int t0 = (int)terms.size();
+                for (int m3 = -l3; m3 <= l3; ++m3) {
+                    const int M = m12 + m3;
+                    if (std::abs(M) > l4) continue;
+                    const double c = cg(l12, m12, l3, m3, l4, M) * cg(l4, M, l4, -M, 0, 0);
+                    if (c == 0.0) continue;
+                    terms.push_back(st(l3, m3) | (st(l4, -M) << 8));
+                    coef.push_back(c);
+                }
+                gz.push_back(make_int4(t0, (int)terms.size(), l12, iz | ((m12 + l12) << 16)));
+            }
+        }
+    }
+    // rows (columns) of each l12 in (parity, b2, b1, ix) ((parity, b3, b4, iz)) order
+    std::vector<int> nlx(NL), nlz(NL), row0(NL + 1), col0(NL + 1), xrow, zcol;
+    std::vector<int4> rowinfo, colinfo, tiles;
+    std::vector<long long> xoff(NL), zoff(NL);
+    long long ux = 0, uz = 0;
+    for (int l12 = 0; l12 < NL; ++l12) {
+        nlx[l12] = (int)lx[l12].size();
+        nlz[l12] = (int)lz[l12].size();
+        row0[l12] = (int)rowinfo.size();
+        col0[l12] = (int)colinfo.size();
+        const int nr = (int)p12.size() * nlx[l12], nc = (int)p34.size() * nlz[l12];
+        std::vector<int> ro(nr), co(nc);
+        for (int i = 0; i < nr; ++i) ro[i] = i;
+        for (int i = 0; i < nc; ++i) co[i] = i;
+        auto rkey = [&](int i) {
+            const int pr = i / nlx[l12], ix = i % nlx[l12];
+            const int par = (lx[l12][ix].x + lx[l12][ix].y) & 1;
+            return std::make_tuple(par, p12[pr].y, p12[pr].x, ix);
+        };
+        auto ckey = [&](int i) {
+            const int pr = i / nlz[l12], iz = i % nlz[l12];
+            const int par = (lz[l12][iz].x + lz[l12][iz].y) & 1;
+            return std::make_tuple(par, p34[pr].x, p34[pr].y, iz);
+        };
+        std::stable_sort(ro.begin(), ro.end(), [&](int a, int b) { return rkey(a) < rkey(b); });
+        std::stable_sort(co.begin(), co.end(), [&](int a, int b) { return ckey(a) < ckey(b); });
+        std::vector<int> rpos(nr), cpos(nc);
+        for (int k = 0; k < nr; ++k) {
+            rpos[ro[k]] = k;
+            const int pr = ro[k] / nlx[l12], ix = ro[k] % nlx[l12];
+            const int2 l = lx[l12][ix];
+            rowinfo.push_back(make_int4(p12[pr].x, p12[pr].y, (l.x + l.y) & 1, l.x | (l.y << 8)));
+        }
+        for (int k = 0; k < nc; ++k) {
+            cpos[co[k]] = k;
+            const int pr = co[k] / nlz[l12], iz = co[k] % nlz[l12];
+            const int2 l = lz[l12][iz];
+            colinfo.push_back(make_int4(p34[pr].x, p34[pr].y, (l.x + l.y) & 1, l.x | (l.y << 8)));
+        }
+        xrow.insert(xrow.end(), rpos.begin(), rpos.end());
+        zcol.insert(zcol.end(), cpos.begin(), cpos.end());
+        xoff[l12] = ux;
+        zoff[l12] = uz;
+        ux += (long long)nr * (2 * l12 + 1);
+        uz += (long long)nc * (2 * l12 + 1);
+        // 64 x 64 tiles that hold a key: some row and column of one parity with b2 < b3
+        for (int r0 = 0; r0 < nr; r0 += 64)
+            for (int c0 = 0; c0 < nc; c0 += 64) {
+                int minb2[2] = {1 << 30, 1 << 30}, maxb3[2] = {-1, -1};
+                for (int k = r0; k < std::min(nr, r0 + 64); ++k) {
+                    const int4 R = rowinfo[row0[l12] + k];
+                    minb2[R.z] = std::min(minb2[R.z], R.y);
+                }
+                for (int k = c0; k < std::min(nc, c0 + 64); ++k) {
+                    const int4 C = colinfo[col0[l12] + k];
+                    maxb3[C.z] = std::max(maxb3[C.z], C.x);
+                }
+                if (minb2[0] < maxb3[0] || minb2[1] < maxb3[1]) tiles.push_back(make_int4(l12, r0, c0, 0));
+            }
+    }
+    row0[NL] = (int)rowinfo.size();
+    col0[NL] = (int)colinfo.size();
+    const int L1 = L + 1;
+    std::vector<int> lamidx((size_t)L1 * L1 * NL * L1 * L1, -1);
+    for (int i = 0; i < P->nlam; ++i) {
+        const int* l = &P->lam[5 * i];
+        lamidx[((((size_t)l[0] * L1 + l[1]) * NL + l[2]) * L1 + l[3]) * L1 + l[4]] = i;
+    }
+    std::vector<int> trikey((size_t)nb * nb * nb, -1);
+    for (const int4& t : P->triples) trikey[((size_t)t.x * nb + t.y) * nb + t.z] = t.w;
+    CUDA_TRY(upload(P->d5_p12, p12));
+    CUDA_TRY(upload(P->d5_p34, p34));
+    CUDA_TRY(upload(P->d5_gx, gx));
+    CUDA_TRY(upload(P->d5_gz, gz));
+    CUDA_TRY(upload(P->d5_terms, terms));
+    if (P->fp64) CUDA_TRY(upload(P->d5_coef, coef));
+    else CUDA_TRY(upload(P->d5_coef, cast_vec<float>(coef)));
+    CUDA_TRY(upload(P->d5_nlx, nlx));
+    CUDA_TRY(upload(P->d5_nlz, nlz));
+    CUDA_TRY(upload(P->d5_row0, row0));
+    CUDA_TRY(upload(P->d5_col0, col0));
+    CUDA_TRY(upload(P->d5_xrow, xrow));
+    CUDA_TRY(upload(P->d5_zcol, zcol));
+    CUDA_TRY(upload(P->d5_rowinfo, rowinfo));
+    CUDA_TRY(upload(P->d5_colinfo, colinfo));
+    CUDA_TRY(upload(P->d5_xoff, xoff));
+    CUDA_TRY(upload(P->d5_zoff, zoff));
+    CUDA_TRY(upload(P->d5_tiles, tiles));
+    CUDA_TRY(upload(P->d5_lamidx, lamidx));
+    CUDA_TRY(upload(P->d5_trikey, trikey));
+    D3n5Params& q = P->d5;
+    q = D3n5Params{};
+    q.nbins = nb;
+    q.lmax = L;
+    q.nq = P->nq;
+    q.nlam = P->nlam;
+    q.ncoeff = (int)P->ncoeff;
+    q.np12 = (int)p12.size();
+    q.np34 = (int)p34.size();
+    q.p12 = P->d5_p12.as<int2>();
+    q.p34 = P->d5_p34.as<int2>();
+    q.ngx = (int)gx.size();
+    q.ngz = (int)gz.size();
+    q.gx = P->d5_gx.as<int4>();
+    q.gz = P->d5_gz.as<int4>();
+    q.terms = P->d5_terms.as<int>();
+    q.coef = P->d5_coef.p;
+    q.nlx = P->d5_nlx.as<int>();
+    q.nlz = P->d5_nlz.as<int>();
+    q.row0 = P->d5_row0.as<int>();
+    q.col0 = P->d5_col0.as<int>();
+    q.xrow = P->d5_xrow.as<int>();
+    q.zcol = P->d5_zcol.as<int>();
+    q.rowinfo = P->d5_rowinfo.as<int4>();
+    q.colinfo = P->d5_colinfo.as<int4>();
+    q.xoff = P->d5_xoff.as<long long>();
+    q.zoff = P->d5_zoff.as<long long>();
+    q.ntiles = (int)tiles.size();
+    q.tiles = P->d5_tiles.as<int4>();
+    q.lamidx = P->d5_lamidx.as<int>();
+    q.trikey = P->d5_trikey.as<int>();
+    P->d5_unit_x = ux;
+    P->d5_unit_z = uz;
+    if (d3n5f_form_smem(nb, L, P->fp64) > P->smem_optin)
+        return fail(NPCF_ERR_UNSUPPORTED, "the 5PCF coupling needs more shared memory than available");
+    return NPCF_OK;
+}
+
+// Primaries per chunk of the factored 5PCF coupling: its X and Z scratch near 64 MB (it stays in
+// L2 between the two kernels), a multiple of 16 in [16, 512].
+int d3n5f_chunk(const npcf_plan_s* P, size_t budget = size_t(64) << 20)
+{
+    const size_t per = (size_t)(P->d5_unit_x + P->d5_unit_z) * 2 * (P->fp64 ? 8 : 4);
+    const size_t c = budget / std::max<size_t>(per, 1);
+    return (int)std::max<size_t>(16, std::min<size_t>(512, c / 16 * 16));
+}
+
+// The partial rows (K slices) of the factored 5PCF coupling: about two CTAs per SM over its tiles.
+int d3n5f_ksplit(const npcf_plan_s* P, int npc)
+{
+    return std::max(1, std::min(npc / 8, (2 * P->nsm + P->d5.ntiles - 1) / std::max(P->d5.ntiles, 1)));
+}
+
+// The factored 5PCF coupling of ncat catalogues (a-array rows cat_first[c] ..): per chunk of npc
+// primaries the formation and the contraction kernels; partial rows [cat][ksplit].
+npcf_status run_d3n5f(npcf_plan_s* P, const void* a, const void* wprim, const int* nprim_dev, int64_t nprim_max,
+                      const int* cat_first, const int* cat_count, int ncat, void* xs, void* zs, int npc, int ksplit,
+                      double* partial, cudaStream_t s)
+{
+    D3n5Params q = P->d5;
+    q.npc = npc;
+    q.a = a;
+    q.wprim = wprim;
+    q.nprim = nprim_dev;
+    q.cat_first = cat_first;
+    q.cat_count = cat_count;
+    q.xs = xs;
+    q.zs = zs;
+    q.xs_cat = (size_t)P->d5_unit_x * npc;
+    q.zs_cat = (size_t)P->d5_unit_z * npc;
+    q.partial = partial;
+    for (int64_t c0 = 0; c0 < std::max<int64_t>(nprim_max, 1); c0 += npc) {
+        const int nc = (int)std::min<int64_t>(npc, std::max<int64_t>(nprim_max - c0, 0));
+        cudaError_t e = launch_d3n5f(q, P->fp64, nc, (int)c0, ksplit, ncat, s);
+        if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "5PCF coupling launch: %s", cudaGetErrorString(e));
+    }
+    return NPCF_OK;
+}
+
 npcf_status setup_tables(npcf_plan_s* P)
 {
     const int D = P->D, nb = P->nbins;
@@ -506,16 +738,6 @@ npcf_status setup_tables(npcf_plan_s* P)
     pp.nq = P->nq;
     pp.periodic = P->opts.periodic;
     pp.warps = warps;
-    // consumption policy of the pair kernel's bin queues; NPCF_PAIR_POLICY="busy,total" overrides
-    pp.busy_round = 28;
-    pp.tot_round = 1 << 30;
-    if (const char* pol = std::getenv("NPCF_PAIR_POLICY")) {
-        int b = 0, t = 0;
-        if (std::sscanf(pol, "%d,%d", &b, &t) == 2 && b > 0 && t > 0) {
-            pp.busy_round = b;
-            pp.tot_round = t;
-        }
-    }
     double maxL = 0.0;
     for (int d = 0; d < D; ++d) maxL = std::max(maxL, P->box[d]);
     const double rmax = P->edges[nb], rmin = P->edges[0];
@@ -551,7 +773,6 @@ npcf_status setup_tables(npcf_plan_s* P)
             if (P->edges[e] >= ra && P->edges[e] <= rb) near = true;
         tab[k] = (unsigned char)((b < 0 ? 63 : b) | (near ? 64 : 0));
     }
-    lane_map(P);
     CUDA_TRY(upload(P->d_tab, tab));
     std::vector<double> qn = component_norms(D, P->lmax);
     std::vector<double> ivb(nb);
@@ -567,6 +788,30 @@ npcf_status setup_tables(npcf_plan_s* P)
     pp.tab = P->d_tab.as<unsigned char>();
     pp.qnorm = P->d_qnorm.p;
     pp.inv_vb = P->d_invvb.p;
+
+    // the visible outputs' columns, when a parity selection drops keys
+    if (P->nvis != P->ncoeff) {
+        std::vector<int> cm(2 * P->nvis);
+        for (int64_t i = 0; i < P->nvis; ++i) {
+            cm[2 * i] = (int)(2 * P->vis[i]);
+            cm[2 * i + 1] = (int)(2 * P->vis[i] + 1);
+        }
+        CUDA_TRY(upload(P->d_colmap, cm));
+    }
+    // remove_self: the basis at coinciding directions, summed over the coupled states of label l
+    // (addition theorem): (-1)^l sqrt(dim_l) / |S^{D-1}| for D >= 3, 1 / (2 pi) for D = 2; over v_b^2
+    if (P->opts.remove_self && P->N == 3) {
+        std::vector<double> sc((size_t)nb * (P->lmax + 1));
+        for (int b = 0; b < nb; ++b)
+            for (int l = 0; l <= P->lmax; ++l) {
+                double c = 1.0 / (2.0 * M_PI);
+                if (D == 3) c = cx::neg1_pow(l) * std::sqrt(2.0 * l + 1.0) / sphere_area(3);
+                if (D == 4) c = cx::neg1_pow(l) * (l + 1.0) / sphere_area(4);
+                sc[(size_t)b * (P->lmax + 1) + l] = c * ivb[b] * ivb[b];
+            }
+        if (P->fp64) CUDA_TRY(upload(P->d_selfc, sc));
+        else CUDA_TRY(upload(P->d_selfc, cast_vec<float>(sc)));
+    }
 
     // coupling tables
     std::vector<double> pref(P->lmax + 1, 1.0);
@@ -584,48 +829,7 @@ npcf_status setup_tables(npcf_plan_s* P)
     }
     CUDA_TRY(upload(P->d_lam2, lam2));
     CUDA_TRY(upload(P->d_lamodd, lamodd));
-    if (P->N == 5) {
-        // the coupling terms of every label set, from the CG chain of eq. Coupling-C
-        // <l1 m1 l2 m2|l12 m12><l12 m12 l3 m3|l4 M><l4 M l4 m4|0 0>, M = -m4, sorted by m4
-        auto cg = [](int j1, int m1, int j2, int m2, int J, int M) {
-            return cx::neg1_pow(j1 - j2 + M) * std::sqrt(2.0 * J + 1.0) * cx::wigner3j(j1, j2, J, m1, m2, -M);
-        };
-        std::vector<int4> lam5;
-        std::vector<int> terms;
-        std::vector<double> coef;
-        for (int i = 0; i < P->nlam; ++i) {
-            const int* l = &P->lam[5 * i];
-            const int l1 = l[0], l2 = l[1], l12 = l[2], l3 = l[3], l4 = l[4];
-            const int t0 = (int)terms.size();
-            for (int m4 = -l4; m4 <= l4; ++m4)
-                for (int m1 = -l1; m1 <= l1; ++m1)
-                    for (int m2 = -l2; m2 <= l2; ++m2) {
-                        const int m12 = m1 + m2, m3 = -m4 - m12;
-                        if (std::abs(m12) > l12 || std::abs(m3) > l3) continue;
-                        const double c = cg(l1, m1, l2, m2, l12, m12) * cg(l12, m12, l3, m3, l4, -m4) *
-                                         cg(l4, -m4, l4, m4, 0, 0);
-                        if (c == 0.0) continue;
-                        const int s1 = l1 * l1 + l1 + m1, s2 = l2 * l2 + l2 + m2, s3 = l3 * l3 + l3 + m3;
-                        terms.push_back((int)((unsigned)s1 | ((unsigned)s2 << 8) | ((unsigned)s3 << 16) |
-                                              ((unsigned)(m4 & 0xff) << 24)));
-                        coef.push_back(c);
-                    }
-            lam5.push_back(make_int4(t0, (int)terms.size(), l4, 0));
-        }
-        CUDA_TRY(upload(P->d_lam5, lam5));
-        CUDA_TRY(upload(P->d_terms5, terms));
-        CUDA_TRY(upload(P->d_coef5, coef));
-        CUDA_TRY(upload(P->d_coef5f, cast_vec<float>(coef)));
-        CUDA_TRY(upload(P->d_triples, P->triples));
-        CoupleParams cp{};
-        cp.N = 5;
-        cp.nbins = nb;
-        cp.lmax = P->lmax;
-        cp.group = d3n5_group(nb, P->lmax, P->fp64);
-        if (couple_d3n5_smem(cp, P->fp64) > P->smem_optin)
-            return fail(NPCF_ERR_UNSUPPORTED, "the 5PCF coupling needs more shared memory than available");
-        return NPCF_OK;
-    }
+    if (P->N == 5) return build_d3n5f_tables(P);
     // key blocks: accumulators get what shared memory the per-primary copy leaves
     CoupleParams cp{};
     cp.D = D;
@@ -637,6 +841,9 @@ npcf_status setup_tables(npcf_plan_s* P)
     const int base = couple_smem(cp, P->fp64);
     const int comps = (P->N == 3 && D != 2) || (P->N == 4 && D == 3) ? 1 : 2;
     const int budget = std::min(P->smem_optin, 160 * 1024) - base;
+    if (tc_coupling(P) && couple_tc_smem(nb, P->nq, P->mixed == 2) > P->smem_optin)
+        return fail(NPCF_ERR_UNSUPPORTED, "the tensor-core coupling needs %d bytes of shared memory",
+                    couple_tc_smem(nb, P->nq, P->mixed == 2));
     if (d2n4_registers(P)) {
         // the register kernel walks every (bin pair, label) item itself: one block of all keys
         if (base > P->smem_optin) return fail(NPCF_ERR_UNSUPPORTED, "D=2 4PCF coupling needs %d bytes of shared memory", base);
@@ -686,6 +893,9 @@ npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int 
     if ((st = R(P->w_items, sizeof(int4) * (n + nc + 1))) != NPCF_OK) return st;
     if ((st = R(P->w_a, (size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins * P->nq)) != NPCF_OK) return st;
     if ((st = R(P->w_wprim, (size_t)tb * std::max<int64_t>(nprim_max, 1))) != NPCF_OK) return st;
+    if (P->opts.remove_self && P->N == 3 &&
+        (st = R(P->w_self, (size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins)) != NPCF_OK)
+        return st;
     if ((st = R(P->w_partial, sizeof(double) * rows * 2 * P->ncoeff)) != NPCF_OK) return st;
     if ((st = R(P->w_small, 128)) != NPCF_OK) return st;
     return NPCF_OK;
@@ -739,15 +949,45 @@ CoupleParams couple_params(const npcf_plan_s* P, const void* a, const void* wpri
     kp.lam2 = P->d_lam2.as<int2>();
     kp.lam_odd = P->d_lamodd.as<signed char>();
     kp.pref = P->d_pref.p;
-    kp.group = P->N == 5 ? d3n5_group(P->nbins, P->lmax, P->fp64) : d2n4_group(P->nbins, P->lmax);
-    kp.ntriple = (int)P->triples.size();
-    kp.triples = P->d_triples.as<int4>();
-    kp.lam5 = P->d_lam5.as<int4>();
-    kp.terms5 = P->d_terms5.as<int>();
-    kp.coef5 = P->d_coef5.as<double>();
-    kp.coef5f = P->d_coef5f.as<float>();
+    kp.group = d2n4_group(P->nbins, P->lmax);
     kp.ncat = 1;
+    kp.tc_npairs = (int)P->pairs.size();
+    kp.tc_glam = tc_glam(P);
+    int cols = 32;
+    while (cols < kp.tc_glam * couple_tc_n(P->nbins)) cols *= 2;
+    kp.tc_tmem_cols = cols;
+    kp.tc_span = tc_span();
+    kp.self = (P->opts.remove_self && P->N == 3) ? P->w_self.p : nullptr;
+    kp.selfc = P->d_selfc.p;
     return kp;
+}
+
+const int* plan_colmap(const npcf_plan_s* P) { return P->nvis != P->ncoeff ? P->d_colmap.as<int>() : nullptr; }
+
+// The coupling stage of a plan: the tensor-core kernel for split-precision plans, the factored
+// 5PCF kernels (per chunk of primaries, xs/zs their scratch), the CUDA-core kernels otherwise.
+// rows: the partial rows per catalogue (the 5PCF's K slices).
+npcf_status plan_coupling(npcf_plan_s* P, CoupleParams kp, int* err, int rows, int64_t nprim_max, void* xs, void* zs,
+                          int npc, cudaStream_t s)
+{
+    kp.err = err;
+    cudaError_t e;
+    if (P->N == 5)
+        return run_d3n5f(P, kp.a, kp.wprim, kp.nprim, nprim_max, kp.cat_first, kp.cat_count, kp.ncat, xs, zs, npc,
+                         rows, kp.partial, s);
+    if (tc_coupling(P))
+        e = launch_couple_d2n4_tc(kp, P->mixed == 2, rows, tc_groups(P),
+                                  couple_tc_smem(P->nbins, P->nq, P->mixed == 2), s);
+    else
+        e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
+    return NPCF_OK;
+}
+
+// bytes of the factored 5PCF scratch (X and Z) for npc primaries per chunk and ncat catalogues
+size_t d3n5f_scratch_bytes(const npcf_plan_s* P, int npc, int ncat)
+{
+    return (size_t)(P->d5_unit_x + P->d5_unit_z) * npc * ncat * 2 * (P->fp64 ? 8 : 4);
 }
 
 // What the cell-list and pair stages leave for the stages after them.
@@ -828,6 +1068,7 @@ npcf_status run_pairs(npcf_plan_s* P, const GridView& gv, const void* pos, const
     pp.ticket = ib.ticket;
     pp.a_out = P->w_a.p;
     pp.w_out = P->w_wprim.p;
+    pp.self_out = (P->opts.remove_self && P->N == 3) ? P->w_self.p : nullptr;
     pp.stats = stats;
     const int grid = P->nsm;
     cudaError_t e;
@@ -844,14 +1085,16 @@ npcf_status run_pairs(npcf_plan_s* P, const GridView& gv, const void* pos, const
 }
 
 // Persistent rows (CTAs along x) of the coupling launch for nprim primaries: about two CTAs per
-// SM over the key blocks; one per SM for the FP32 D=2 4PCF register kernel; for N=5 groups of
-// d3n5_group primaries with up to three CTAs per SM.  Never more rows than there is work.
+// SM over the key blocks; one per SM for the FP32 D=2 4PCF register kernel; for N=5 the K
+// slices of the factored coupling.  Never more rows than there is work.
 int couple_rows(const npcf_plan_s* P, int64_t nprim, int chunk)
 {
-    if (P->N == 5) {
-        const int G = d3n5_group(P->nbins, P->lmax, P->fp64);
-        return (int)std::min<int64_t>(3 * P->nsm, std::max<int64_t>(1, (nprim + G - 1) / G));
+    if (tc_coupling(P)) {  // one CTA per SM over (rows x label-set groups)
+        const int64_t KP = couple_tc_chunk(P->mixed == 2);
+        const int r = std::max(1, P->nsm / tc_groups(P));
+        return (int)std::min<int64_t>(r, std::max<int64_t>(1, (nprim + KP - 1) / KP));
     }
+    if (P->N == 5) return d3n5f_ksplit(P, d3n5f_chunk(P));
     const int nkb = (int)P->kblocks.size();
     int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
     if (d2n4_registers(P)) rows = P->nsm;
@@ -868,6 +1111,9 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
     const int chunk = 128;
     const int rows = couple_rows(P, nprim_max, chunk);
     if ((st = reserve_workspace(P, n, nprim_max, rows, P->ncells)) != NPCF_OK) return st;
+    const int npc = P->N == 5 ? d3n5f_chunk(P) : 0;
+    if (P->N == 5 && (P->w_x5.reserve(d3n5f_scratch_bytes(P, npc, 1)) != cudaSuccess))
+        return fail(NPCF_ERR_WORKSPACE, "device allocation of the 5PCF scratch failed");
     PairStage ps;
     if ((st = run_pairs(P, single_view(P), pos, w, n, pb, pe, s, &ps)) != NPCF_OK) return st;
     const ItemBuffers& ib = ps.ib;
@@ -877,11 +1123,13 @@ npcf_status run(npcf_plan_s* P, const void* pos, const void* w, int64_t n, doubl
 
     CoupleParams kp = couple_params(P, P->w_a.p, P->w_wprim.p, ib.nprim, chunk, P->w_partial.as<double>());
     CUDA_TRY(cudaMemsetAsync(kp.partial, 0, sizeof(double) * rows * 2 * P->ncoeff, s));
-    const int csm = couple_smem(kp, P->fp64);
-    e = launch_couple(kp, P->fp64, rows, csm, s);
-    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
+    if ((st = plan_coupling(P, kp, small + S_ERR, rows, nprim_max, P->w_x5.p,
+                            P->w_x5.as<unsigned char>() + (size_t)P->d5_unit_x * npc * 2 * (P->fp64 ? 8 : 4), npc, s)) !=
+        NPCF_OK)
+        return st;
     if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[3], s));
-    CUDA_TRY(launch_reduce(kp.partial, rows, (int)(2 * P->ncoeff), 1.0 / P->V, coeffs, s));
+    CUDA_TRY(launch_reduce(kp.partial, rows, (int)(2 * P->ncoeff), plan_colmap(P), (int)(2 * P->nvis), 1.0 / P->V,
+                           coeffs, s));
     if (P->opts.timing) {
         CUDA_TRY(cudaEventRecord(P->ev[4], s));
         P->timed = 1;
@@ -1064,7 +1312,16 @@ npcf_status run_batched(npcf_plan_s* P, const void* pos, const void* w, const in
     const int64_t row_bytes = (int64_t)sizeof(double) * 2 * P->ncoeff * ncat;
     r64 = std::min<int64_t>(r64, std::max<int64_t>(1, (int64_t(512) << 20) / std::max<int64_t>(row_bytes, 1)));
     int rows = (int)std::min<int64_t>(r64, std::max<int64_t>(1, max_chunks));
+    if (tc_coupling(P)) {  // one CTA per SM over (rows x label-set groups x catalogues)
+        const int64_t KP = couple_tc_chunk(P->mixed == 2);
+        rows = (int)std::min<int64_t>(std::max(1, P->nsm / (tc_groups(P) * ncat)),
+                                      std::max<int64_t>(1, (nmax + KP - 1) / KP));
+    }
+    const int npc = P->N == 5 ? d3n5f_chunk(P) : 0;
+    if (P->N == 5) rows = couple_rows(P, nmax, chunk);
     if ((st = reserve_workspace(P, n, n, rows * ncat, P->b_ncells)) != NPCF_OK) return st;
+    if (P->N == 5 && (P->w_x5.reserve(d3n5f_scratch_bytes(P, npc, ncat)) != cudaSuccess))
+        return fail(NPCF_ERR_WORKSPACE, "device allocation of the 5PCF scratch failed");
     GridView gv;
     gv.ncells = P->b_ncells;
     gv.ncat = ncat;
@@ -1080,10 +1337,14 @@ npcf_status run_batched(npcf_plan_s* P, const void* pos, const void* w, const in
     kp.cat_first = P->b_first.as<int>();
     kp.cat_count = P->b_count.as<int>();
     CUDA_TRY(cudaMemsetAsync(kp.partial, 0, sizeof(double) * rows * ncat * 2 * P->ncoeff, s));
-    cudaError_t e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
-    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
+    if ((st = plan_coupling(P, kp, ps.small + S_ERR, rows, nmax, P->w_x5.p,
+                            P->w_x5.as<unsigned char>() +
+                                (size_t)P->d5_unit_x * npc * ncat * 2 * (P->fp64 ? 8 : 4),
+                            npc, s)) != NPCF_OK)
+        return st;
     if (P->opts.timing) CUDA_TRY(cudaEventRecord(P->ev[3], s));
-    CUDA_TRY(launch_reduce_cats(kp.partial, rows, (int)(2 * P->ncoeff), ncat, P->b_scales.as<double>(), coeffs, s));
+    CUDA_TRY(launch_reduce_cats(kp.partial, rows, (int)(2 * P->ncoeff), plan_colmap(P), (int)(2 * P->nvis), ncat,
+                                P->b_scales.as<double>(), coeffs, s));
     if (P->opts.timing) {
         CUDA_TRY(cudaEventRecord(P->ev[4], s));
         P->timed = 1;
@@ -1100,6 +1361,8 @@ npcf_status check_flags(npcf_plan_s* P)
 {
     if (P->h_small[S_ERR] & 1) return fail(NPCF_ERR_NONFINITE, "a position or weight is NaN or infinite");
     if (P->h_small[S_ERR] & 2) return fail(NPCF_ERR_NONFINITE, "a position lies outside [0, box)");
+    if (P->h_small[S_ERR] & 4)
+        return fail(NPCF_ERR_DEVICE_TIMEOUT, "a bounded wait of the tensor-core coupling ran out; the call stopped");
     return NPCF_OK;
 }
 
@@ -1116,6 +1379,8 @@ void npcf_default_opts(npcf_opts* o)
     o->bin_order = NPCF_BINS_LE;
     o->sync_check = 1;
     o->timing = 0;
+    o->remove_self = 0;
+    o->parity = NPCF_PARITY_ALL;
 }
 
 npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const double* edges, int nbins,
@@ -1142,8 +1407,20 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
     npcf_opts o;
     npcf_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != NPCF_FP32 && o.precision != NPCF_FP64) return fail(NPCF_ERR_ARG, "bad precision");
+    if (o.precision != NPCF_FP32 && o.precision != NPCF_FP64 && o.precision != NPCF_MIXED_BF16X3 &&
+        o.precision != NPCF_MIXED_TF32X3)
+        return fail(NPCF_ERR_ARG, "bad precision");
+    const bool mixed = o.precision == NPCF_MIXED_BF16X3 || o.precision == NPCF_MIXED_TF32X3;
+    if (mixed && !(D == 2 && N == 4))
+        return fail(NPCF_ERR_UNSUPPORTED, "the split-precision tensor-core coupling is provided for the D=2 4PCF");
+    if (mixed && (nbins - 1) * (nbins - 2) / 2 > 128)
+        return fail(NPCF_ERR_UNSUPPORTED, "the tensor-core D=2 4PCF coupling takes at most 17 bins");
     if (o.bin_order != NPCF_BINS_LE && o.bin_order != NPCF_BINS_LT) return fail(NPCF_ERR_ARG, "bad bin_order");
+    if (o.remove_self != 0 && o.remove_self != 1) return fail(NPCF_ERR_ARG, "remove_self must be 0 or 1");
+    if (o.parity != NPCF_PARITY_ALL && o.parity != NPCF_PARITY_EVEN && o.parity != NPCF_PARITY_ODD)
+        return fail(NPCF_ERR_ARG, "bad parity");
+    if (o.parity == NPCF_PARITY_ODD && !(N == 4 && D == 3))
+        return fail(NPCF_ERR_UNSUPPORTED, "this plan has no odd-parity components (only the D=3 4PCF has them)");
     for (int d = 0; d < D; ++d) {
         if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(NPCF_ERR_ARG, "box sides must be > 0");
         if (o.periodic && !(edges[nbins] < 0.5 * box[d]))
@@ -1157,6 +1434,7 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
     P->nbins = nbins;
     P->opts = o;
     P->fp64 = o.precision == NPCF_FP64;
+    P->mixed = o.precision == NPCF_MIXED_BF16X3 ? 1 : (o.precision == NPCF_MIXED_TF32X3 ? 2 : 0);
     P->edges.assign(edges, edges + nbins + 1);
     P->V = 1.0;
     for (int d = 0; d < D; ++d) {
@@ -1177,16 +1455,17 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
 npcf_status npcf_num_coeffs(npcf_plan_t P, int64_t* n)
 {
     if (!P || !n) return fail(NPCF_ERR_ARG, "NULL argument");
-    *n = P->ncoeff;
+    *n = P->nvis;
     return NPCF_OK;
 }
 
 npcf_status npcf_coeff_index(npcf_plan_t P, int64_t i, int* bins, int* ells)
 {
     if (!P || !bins || !ells) return fail(NPCF_ERR_ARG, "NULL argument");
-    if (i < 0 || i >= P->ncoeff) return fail(NPCF_ERR_ARG, "index %lld out of range", (long long)i);
-    for (int k = 0; k < P->N - 1; ++k) bins[k] = P->key_bins[4 * i + k];
-    const int il = P->key_lam[i];
+    if (i < 0 || i >= P->nvis) return fail(NPCF_ERR_ARG, "index %lld out of range", (long long)i);
+    const int64_t ki = P->vis[i];
+    for (int k = 0; k < P->N - 1; ++k) bins[k] = P->key_bins[4 * ki + k];
+    const int il = P->key_lam[ki];
     const int ne = P->N == 3 ? 1 : (P->N == 4 ? 3 : 5);
     for (int k = 0; k < ne; ++k) ells[k] = P->lam[5 * il + k];
     return NPCF_OK;
@@ -1226,7 +1505,7 @@ npcf_status npcf_compute_host(npcf_plan_t P, const void* pos, const void* w, int
     const size_t tb = P->fp64 ? 8 : 4;
     if (P->w_hpos.reserve(tb * P->D * std::max<int64_t>(n, 1)) != cudaSuccess ||
         P->w_hw.reserve(tb * std::max<int64_t>(n, 1)) != cudaSuccess ||
-        P->w_hout.reserve(sizeof(double) * 2 * P->ncoeff + 16) != cudaSuccess)
+        P->w_hout.reserve(sizeof(double) * 2 * P->nvis + 16) != cudaSuccess)
         return fail(NPCF_ERR_WORKSPACE, "device staging allocation failed");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n > 0) {
@@ -1235,7 +1514,7 @@ npcf_status npcf_compute_host(npcf_plan_t P, const void* pos, const void* w, int
     }
     st = run(P, P->w_hpos.p, P->w_hw.p, n, P->w_hout.as<double>(), pb, pe, s);
     if (st != NPCF_OK) return st;
-    CUDA_TRY(cudaMemcpyAsync(coeffs, P->w_hout.p, sizeof(double) * 2 * P->ncoeff, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(coeffs, P->w_hout.p, sizeof(double) * 2 * P->nvis, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return check_flags(P);
 }
@@ -1309,6 +1588,8 @@ npcf_status npcf_backward(npcf_plan_t P, const void* pos, const void* w, int64_t
 {
     if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
     if (P->N != 3) return fail(NPCF_ERR_UNSUPPORTED, "the adjoint is implemented for N=3 plans");
+    if (P->opts.remove_self)
+        return fail(NPCF_ERR_UNSUPPORTED, "the adjoint of the remove_self subtraction is not provided");
     if (n < 0 || n > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)n);
     if (!grad_coeffs) return fail(NPCF_ERR_ARG, "grad_coeffs is NULL");
     if (n > 0 && !grad_pos && !grad_w) return fail(NPCF_ERR_ARG, "grad_positions and grad_weights are both NULL");
@@ -1326,6 +1607,27 @@ npcf_status npcf_backward(npcf_plan_t P, const void* pos, const void* w, int64_t
     return NPCF_OK;
 }
 
+npcf_status npcf_selftest_tc(int tf32, int n, int k, const float* a, const float* b, float* d, npcf_stream_t stream)
+{
+    if (tf32 != 0 && tf32 != 1) return fail(NPCF_ERR_ARG, "tf32 must be 0 or 1");
+    if (n < 16 || n > 256 || n % 16) return fail(NPCF_ERR_ARG, "n must be a multiple of 16 in [16, 256]");
+    const int kq = tf32 ? 32 : 64;
+    if (k < kq || k > 4096 || k % kq) return fail(NPCF_ERR_ARG, "k must be a positive multiple of %d, at most 4096", kq);
+    if (!a || !b || !d) return fail(NPCF_ERR_ARG, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* err = nullptr;
+    CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+    int herr = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_tc_selftest(tf32, a, b, d, n, k, err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(err);
+    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "tensor-core self-test: %s", cudaGetErrorString(e));
+    if (herr & 4) return fail(NPCF_ERR_DEVICE_TIMEOUT, "a bounded wait on the MMA completion ran out");
+    return NPCF_OK;
+}
+
 const char* npcf_last_error(void) { return g_err.c_str(); }
 
 void npcf_plan_destroy(npcf_plan_t P)
@@ -1337,7 +1639,11 @@ void npcf_plan_destroy(npcf_plan_t P)
                       &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout,  &P->d_keybase, &P->w_cbuf,
                       &P->w_gpos,  &P->w_gw,    &P->w_gwp,   &P->d_geo,   &P->b_geo,     &P->b_cells,
                       &P->b_offsets, &P->b_first, &P->b_count, &P->b_scales, &P->b_stencil,
-                      &P->d_triples, &P->d_lam5, &P->d_terms5, &P->d_coef5, &P->d_coef5f};
+                      &P->d5_p12,  &P->d5_p34, &P->d5_gx,  &P->d5_gz, &P->d5_terms, &P->d5_coef, &P->d5_nlx,
+                      &P->d5_nlz,  &P->d5_row0, &P->d5_col0, &P->d5_xrow, &P->d5_zcol, &P->d5_rowinfo,
+                      &P->d5_colinfo, &P->d5_xoff, &P->d5_zoff, &P->d5_tiles, &P->d5_lamidx, &P->d5_trikey,
+                      &P->w_x5,    &P->w_z5,
+                      &P->d_colmap,  &P->d_selfc, &P->w_self};
     for (DevBuf* b : bufs) b->release();
     if (P->h_small) cudaFreeHost(P->h_small);
     for (auto& e : P->ev)
@@ -1429,6 +1735,8 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     int4* items = static_cast<int4*>(cv.take(sizeof(int4) * (n + nc + 1)));
     void* a = cv.take((size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins * P->nq);
     void* wprim = cv.take((size_t)tb * std::max<int64_t>(nprim_max, 1));
+    const bool self_on = P->opts.remove_self && P->N == 3;
+    void* self = self_on ? cv.take((size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins) : nullptr;
     int* small = static_cast<int*>(cv.take(128));
     const size_t row_bytes = sizeof(double) * 2 * P->ncoeff;
     size_t left = cv.used <= kNoallocBytes ? kNoallocBytes - ((cv.used + 255) & ~size_t(255)) : 0;
@@ -1441,6 +1749,20 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
                     need, (long long)n, kNoallocBytes);
     }
     double* partial = static_cast<double*>(cv.take(row_bytes * rows));
+    // the factored 5PCF's X and Z scratch: as many primaries per chunk as the array still holds
+    int npc = 0;
+    void *xs = nullptr, *zs = nullptr;
+    if (P->N == 5) {
+        const size_t left5 = cv.used <= kNoallocBytes ? kNoallocBytes - ((cv.used + 255) & ~size_t(255)) : 0;
+        npc = d3n5f_chunk(P, left5 > 4096 ? left5 - 4096 : 0);
+        const size_t xb = d3n5f_scratch_bytes(P, npc, 1), ub = (size_t)P->d5_unit_x * npc * 2 * tb;
+        xs = cv.take(xb);
+        zs = static_cast<unsigned char*>(xs) + ub;
+        if (cv.used > kNoallocBytes)
+            return fail(NPCF_ERR_WORKSPACE,
+                        "npcf_compute_noalloc needs %zu bytes of scratch for n=%lld; its static scratch holds %zu",
+                        (cv.need + 255) & ~size_t(255), (long long)n, kNoallocBytes);
+    }
 
     CUDA_TRY(cudaMemcpyAsync(stencil, g.stencil.data(), sizeof(int) * g.stencil.size(), cudaMemcpyHostToDevice, s));
     const CatGeom hgeo = make_geom(P->D, g.nc, P->box, 0, 0);
@@ -1497,6 +1819,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     pp.ticket = ib.ticket;
     pp.a_out = a;
     pp.w_out = wprim;
+    pp.self_out = self;
     pp.stats = stats;
     cudaError_t e;
     if (P->D == 2) e = launch_pairs_d2(pp, P->fp64, P->Lc, P->nsm, P->pair_smem, s);
@@ -1505,10 +1828,11 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "pair kernel launch: %s", cudaGetErrorString(e));
 
     CoupleParams kp = couple_params(P, a, wprim, ib.nprim, chunk, partial);
+    kp.self = self;
     CUDA_TRY(cudaMemsetAsync(partial, 0, row_bytes * rows, s));
-    e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
-    if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
-    CUDA_TRY(launch_reduce(partial, rows, (int)(2 * P->ncoeff), 1.0 / P->V, coeffs, s));
+    if ((st = plan_coupling(P, kp, small + S_ERR, rows, nprim_max, xs, zs, npc, s)) != NPCF_OK) return st;
+    CUDA_TRY(launch_reduce(partial, rows, (int)(2 * P->ncoeff), plan_colmap(P), (int)(2 * P->nvis), 1.0 / P->V,
+                           coeffs, s));
     P->last_launches = launch_counter();
     CUDA_TRY(cudaMemcpyAsync(P->h_small, small, 16, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(P->h_stats, stats, 64, cudaMemcpyDeviceToHost, s));

@@ -17,8 +17,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("NPCF_LIBRARY") or os.path.join(_HERE, "_build", "libnpcf.so")
 
 NPCF_OK = 0
-NPCF_FP64, NPCF_FP32 = 0, 1
+NPCF_FP64, NPCF_FP32, NPCF_MIXED_BF16X3, NPCF_MIXED_TF32X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": NPCF_FP64, "fp32": NPCF_FP32, "mixed_bf16x3": NPCF_MIXED_BF16X3,
+              "mixed_tf32x3": NPCF_MIXED_TF32X3}
 NPCF_BINS_LE, NPCF_BINS_LT = 0, 1
+PARITIES = {"all": 0, "even": 1, "odd": 2}
 STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPCF_ERR_CUDA",
           -4: "NPCF_ERR_WORKSPACE", -5: "NPCF_ERR_DEVICE_TIMEOUT", -6: "NPCF_ERR_NONFINITE"}
 
@@ -26,7 +29,7 @@ STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPC
 EXPORTS = ("npcf_default_opts", "npcf_plan_create", "npcf_num_coeffs", "npcf_coeff_index", "npcf_compute",
            "npcf_compute_host", "npcf_device_status", "npcf_last_stats", "npcf_last_profile", "npcf_last_error",
            "npcf_plan_destroy", "npcf_compute_noalloc", "npcf_last_counters", "npcf_backward",
-           "npcf_compute_batched")
+           "npcf_compute_batched", "npcf_selftest_tc")
 
 
 class NpcfError(RuntimeError):
@@ -37,7 +40,8 @@ class NpcfError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("periodic", ctypes.c_int), ("bin_order", ctypes.c_int),
-                ("sync_check", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("sync_check", ctypes.c_int), ("timing", ctypes.c_int), ("remove_self", ctypes.c_int),
+                ("parity", ctypes.c_int)]
 
 
 _lib = None
@@ -83,6 +87,8 @@ def load_library(path: str = LIB_PATH):
         lib.npcf_compute_batched.restype = i32
         lib.npcf_backward.argtypes = [P, P, P, i64, P, i64, i64, P, P, P]
         lib.npcf_backward.restype = i32
+        lib.npcf_selftest_tc.argtypes = [i32, i32, i32, P, P, P, P]
+        lib.npcf_selftest_tc.restype = i32
         lib.npcf_last_error.argtypes = []
         lib.npcf_last_error.restype = ctypes.c_char_p
         lib.npcf_plan_destroy.argtypes = [P]
@@ -97,17 +103,43 @@ def _check(status: int):
         raise NpcfError(status, msg)
 
 
+def selftest_tc(a, b, tf32=False, stream=None):
+    """The split-precision tensor-core contraction on caller data: a (128, k) and b (n, k) float32
+    CUDA tensors -> a b^T (128, n) float32, through npcf_selftest_tc (a diagnostic of the MMA path
+    the mixed couplings use)."""
+    import torch
+    lib = load_library()
+    if not (a.is_cuda and b.is_cuda) or a.dtype != torch.float32 or b.dtype != torch.float32:
+        raise TypeError("a and b must be float32 CUDA tensors")
+    a = a.contiguous()
+    b = b.contiguous()
+    if a.dim() != 2 or b.dim() != 2 or a.shape[0] != 128 or a.shape[1] != b.shape[1]:
+        raise ValueError("a must be (128, k) and b (n, k)")
+    d = torch.empty(128, b.shape[0], dtype=torch.float32, device=a.device)
+    s = stream if stream is not None else torch.cuda.current_stream(a.device)
+    with torch.cuda.device(a.device):
+        _check(lib.npcf_selftest_tc(int(bool(tf32)), b.shape[0], a.shape[1], ctypes.c_void_p(a.data_ptr()),
+                                    ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(d.data_ptr()),
+                                    ctypes.c_void_p(s.cuda_stream)))
+    return d
+
+
 class Plan:
     """A plan for one (D, N, lmax, bins, box) estimator configuration.
 
+    remove_self: subtract the tuples whose secondaries coincide (N=3 keys with b1 = b2).
+    parity: "all", "even" or "odd" components (odd ones exist for the D=3 4PCF only).
     precision: "fp32" (positions/weights float32; FP32 pair and coupling
-    arithmetic, FP64 sums over primaries) or "fp64" (double throughout).
+    arithmetic, FP64 sums over primaries), "fp64" (double throughout), or
+    "mixed_bf16x3" / "mixed_tf32x3" (float32 inputs and pair stage; the coupling
+    on the tensor cores with every operand split into BF16 or TF32 hi + lo
+    pairs, FP32 accumulation, FP64 sums across spans of primaries).
     """
 
     def __init__(self, D, N, lmax, edges, box, *, precision="fp32", periodic=True, bin_lt=False, sync_check=True,
-                 timing=False):
-        if precision not in ("fp32", "fp64"):
-            raise ValueError(f"precision must be 'fp32' or 'fp64', not {precision!r}")
+                 timing=False, remove_self=False, parity="all"):
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}, not {precision!r}")
         lib = load_library()
         self.D, self.N, self.lmax = int(D), int(N), int(lmax)
         self.edges = np.ascontiguousarray(edges, dtype=np.float64)
@@ -116,11 +148,15 @@ class Plan:
         self.precision = precision
         o = Opts()
         lib.npcf_default_opts(ctypes.byref(o))
-        o.precision = NPCF_FP64 if precision == "fp64" else NPCF_FP32
+        o.precision = PRECISIONS[precision]
         o.periodic = int(bool(periodic))
         o.bin_order = NPCF_BINS_LT if bin_lt else NPCF_BINS_LE
         o.sync_check = int(bool(sync_check))
         o.timing = int(bool(timing))
+        o.remove_self = int(bool(remove_self))
+        if parity not in PARITIES:
+            raise ValueError(f"parity must be one of {sorted(PARITIES)}, not {parity!r}")
+        o.parity = PARITIES[parity]
         h = ctypes.c_void_p()
         _check(lib.npcf_plan_create(ctypes.byref(h), self.D, self.N, self.lmax,
                                     self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.nbins,
@@ -277,7 +313,7 @@ class Plan:
         lib = load_library()
         c = (ctypes.c_int64 * 8)()
         _check(lib.npcf_last_counters(self._h, c, 8))
-        names = ("pairs", "candidates", "rounds", "busy_lanes", "chunks", "forced_rounds", "flagged", "exact")
+        names = ("pairs", "candidates", "rounds", "busy_lanes", "chunks", "batches", "flagged", "exact")
         return dict(zip(names, (int(x) for x in c)))
 
     def function(self, primaries=None):

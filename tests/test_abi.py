@@ -78,6 +78,9 @@ def _create(lib, D, N, lmax, edges, box, opts=None):
         (3, 5, 7, [0.1, 0.2, 0.3, 0.4, 0.45], [1] * 3, None, -2),  # N=5 lmax limit
         (3, 5, 2, [0.1, 0.2, 0.3], [1] * 3, None, -1),  # N=5 needs 4 bins
         (4, 4, 2, [0.1, 0.2, 0.3, 0.4], [1] * 4, None, -2),  # N=4 in D=4 needs an SO(4) coupling
+        (3, 3, 2, [0.1, 0.2], [1] * 3, {"precision": 2}, -2),  # split precision: tensor-core couplings only
+        (2, 4, 2, list(np.linspace(0.01, 0.1, 19)), [1] * 2, {"precision": 3}, -2),  # > 128 bin pairs
+        (2, 4, 2, [0.1, 0.2, 0.3, 0.4], [1] * 2, {"precision": 7}, -1),  # unknown precision
         (3, 4, 7, [0.1, 0.2, 0.3, 0.4], [1] * 3, None, -2),  # lmax beyond the compiled coupling
         (3, 3, 2, list(np.linspace(0.01, 0.3, 40)), [1] * 3, None, -2),  # more than 32 bins
         (3, 3, 2, [0.2, 0.1], [1] * 3, None, -1),  # decreasing edges

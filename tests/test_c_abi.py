@@ -24,6 +24,7 @@ int main(void)
     npcf_default_opts(&o);
     EXPECT(o.precision == NPCF_FP32 && o.periodic == 1 && o.bin_order == NPCF_BINS_LE);
     EXPECT(o.sync_check == 1 && o.timing == 0);
+    EXPECT(o.remove_self == 0 && o.parity == NPCF_PARITY_ALL);
 
     EXPECT(npcf_compute(NULL, NULL, NULL, 0, NULL, 0, 0, NULL) == NPCF_ERR_ARG);
     EXPECT(strstr(npcf_last_error(), "NULL") != NULL);
@@ -37,6 +38,18 @@ int main(void)
     const double bad_edges[3] = {0.2, 0.1, 0.3};
     EXPECT(npcf_plan_create(&plan, 3, 3, 2, bad_edges, 2, box, NULL) == NPCF_ERR_ARG);
     EXPECT(strlen(npcf_last_error()) > 0);
+    /* the options are validated on the host, before any device work */
+    o.remove_self = 2;
+    EXPECT(npcf_plan_create(&plan, 3, 3, 2, edges, 2, box, &o) == NPCF_ERR_ARG);
+    npcf_default_opts(&o);
+    o.parity = 5;
+    EXPECT(npcf_plan_create(&plan, 3, 3, 2, edges, 2, box, &o) == NPCF_ERR_ARG);
+    o.parity = NPCF_PARITY_ODD; /* N=3 has no odd-parity components */
+    EXPECT(npcf_plan_create(&plan, 3, 3, 2, edges, 2, box, &o) == NPCF_ERR_UNSUPPORTED);
+    npcf_default_opts(&o);
+    o.precision = NPCF_MIXED_TF32X3; /* the split-precision coupling exists for the D=2 4PCF */
+    EXPECT(npcf_plan_create(&plan, 3, 3, 2, edges, 2, box, &o) == NPCF_ERR_UNSUPPORTED);
+    EXPECT(plan == NULL);
     npcf_plan_destroy(NULL);
     printf("%d failures\n", fails);
     return fails != 0;
