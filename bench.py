@@ -66,6 +66,9 @@ def _args():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--no-mixed-arm", action="store_true",
+                    help="skip the split-precision (tensor-core) coupling comparison on the D=2 4PCF workload")
     ap.add_argument("--precision", default=None,
                     help="fp32 | fp64 | mixed_bf16x3 | mixed_tf32x3 (default: the workload's own, fp32 or fp64)")
     return ap.parse_args()
@@ -75,7 +78,9 @@ def _args():
 def pair_flops_per_pair(D: int, lmax: int) -> int:
     """Algorithmic FP32 operations of one pair (FMA = 2): separation and r^2,
     the direction, the harmonic recurrence and the accumulation, counted from
-    the recurrence of the pair kernel (see the design notes)."""
+    the recurrence of the pair kernel: D=3 counts the powers (x - iy)^m, the first step z P_m of
+    each column, the three-term steps (one multiply by the recurrence constant and one FMA per
+    real part) and one add per accumulated component."""
     sep = 3 * D  # D subtractions, D multiply-adds for r^2 (2 each) -> 3D
     direction = 2 + D  # rsqrt, r, D scalings
     if D == 3:
@@ -473,6 +478,8 @@ def run_ours(args, rank, world):
     out = torch.empty(2 * plan.ncoeff, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
+    # launch shapes chosen by the library's autotuner on a sample of this input (outside the timing)
+    tuned = plan.tuned_config() if args.no_autotune else plan.autotune(pos, w)
 
     for _ in range(args.warmup):
         plan.compute(pos, w, out=out)
@@ -573,6 +580,7 @@ def run_ours(args, rank, world):
                    "ncoeff": plan.ncoeff,
                    "l2": "256 MB buffer written before every timed step (outside the events)"},
         "coeffs_per_s": coeffs_per_s, "coupling_terms_per_primary": terms, "pair_counters": counters,
+        "tuned": tuned,
         "stages_ms": {"cells": float(np.mean(cells_ms)), "pairs": float(np.mean(pair_ms)),
                       "couple": float(np.mean(couple_ms))},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -580,6 +588,11 @@ def run_ours(args, rank, world):
     }
     if args.scale != 1.0:
         line["config"]["scale"] = args.scale
+    if rank == 0 and args.workload == "d3n4" and not args.no_mixed_arm:
+        # the D=3 4PCF has no tensor-core coupling (its contraction over primaries would need a
+        # per-primary operand of 58,320 complex products, as costly as its CUDA-core kernel); the
+        # metric's mixed-vs-FP32 comparison is measured on the D=2 4PCF, whose coupling runs there
+        line["mixed_vs_fp32"] = mixed_arm(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def gpu_range(a, b):  # the GPU's coefficients of primaries [a, b), for the per-result error
             z = plan.compute(pos, w, primaries=(a, b)).cpu().numpy()
@@ -591,6 +604,61 @@ def run_ours(args, rank, world):
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def mixed_arm(dev, steps=5, oracle_prims=100):
+    """The split-precision tensor-core coupling against the FP32 CUDA-core coupling, on the D=2 4PCF
+    workload (200k points, 16 bins, lmax 10): coupling-stage times (CUDA events, median of `steps`
+    after a warm-up), the speed-up, the error of each split against the FP32 result (every primary)
+    and against the FP64 oracle (primaries [0, oracle_prims)), and the tensor pipe's rate."""
+    import torch
+
+    from paper_2106_10278_gb300 import catalogs
+    from paper_2106_10278_gb300.npcf import Plan
+    import oracle
+
+    wl = catalogs.workload("d2n4")
+    pos = torch.tensor(wl.pos, dtype=torch.float32, device=dev)
+    w = torch.tensor(wl.w, dtype=torch.float32, device=dev)
+    keys, ref = oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, oracle_prims))
+    index = {tuple(int(x) for x in k): i for i, k in enumerate(keys)}
+    out = {"workload": "d2n4: D=2 4PCF, 200k points (100k uniform + 100k in 400 Gaussian blobs), 16 bins over "
+                       "[0.002,0.05], lmax 10", "couple_ms": {}, "rel_err_vs_fp32": {}, "rel_err_vs_oracle": {}}
+    z32 = None
+    for prec in ("fp32", "mixed_bf16x3", "mixed_tf32x3"):
+        plan = Plan(wl.D, wl.N, wl.lmax, wl.edges, wl.box, precision=prec, sync_check=False, timing=True)
+        plan.autotune(pos, w)
+        z = plan.compute(pos, w).cpu().numpy()
+        ms = []
+        for _ in range(steps):
+            plan.compute(pos, w)
+            ms.append(plan.profile()["couple_ms"])
+        zs = plan.compute(pos, w, primaries=(0, oracle_prims)).cpu().numpy()
+        r = ref[np.array([index[tuple(int(x) for x in k)] for k in plan.keys()])]
+        out["couple_ms"][prec] = float(np.median(ms))
+        out["rel_err_vs_oracle"][prec] = float(np.linalg.norm(zs - r) / np.linalg.norm(r))
+        if prec == "fp32":
+            z32 = z
+        else:
+            out["rel_err_vs_fp32"][prec] = float(np.linalg.norm(z - z32) / np.linalg.norm(z32))
+        if prec == "mixed_bf16x3":
+            out["tuned_bf16x3"] = plan.tuned_config()
+    t32 = out["couple_ms"]["fp32"]
+    out["speedup_vs_fp32"] = {k: t32 / v for k, v in out["couple_ms"].items() if k != "fp32"}
+    # tensor-pipe rate of the BF16x3 kernel: MMA flops issued (3 split products over M=128 rows x N=32
+    # columns x K=2 per primary and label set, padding included) over its time
+    nprim, nlam = wl.n, 176
+    mma_flops = 3 * 2 * 128 * 32 * 2 * nprim * nlam
+    peaks = _peaks()
+    bf = peaks.get("bf16_tflops")
+    out["tensor_roofline"] = {"bound": "tensor", "kernel": "k_couple_d2n4_tc (bf16x3)",
+                              "achieved": mma_flops / (out["couple_ms"]["mixed_bf16x3"] * 1e-3) / 1e12,
+                              "peak": bf, "unit": "TFLOP/s", "peak_note": "MEASURED_PEAKS.json bf16_tflops (of measured)",
+                              "flops_note": "MMA flops issued: 3 split products x 2 x 128 x 32 x 2 per primary and "
+                                            "label set (176 label sets), padding included"}
+    if bf:
+        out["tensor_roofline"]["frac"] = out["tensor_roofline"]["achieved"] / bf
+    return out
 
 
 def _timed(args, world, step, flush, stream, after=None):
@@ -658,6 +726,10 @@ def run_batch64(args, rank, world):
     plans = [Plan(3, N, L, bw.edges, np.full(3, 1000.0), precision="fp32", sync_check=False, timing=True)
              for N, L in ((3, 10), (4, 4))]
     outs = [torch.empty(bw.ncat * 2 * p.ncoeff, dtype=torch.float64, device=dev) for p in plans]
+    # launch shapes tuned on the largest catalogue (outside the timing); the batched calls use them
+    big = int(np.argmax(np.diff(bw.offsets)))
+    a0, a1 = int(bw.offsets[big]), int(bw.offsets[big + 1])
+    tuned = [p.tuned_config() if args.no_autotune else p.autotune(pos[a0:a1], w[a0:a1]) for p in plans]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     prof = []
@@ -691,7 +763,7 @@ def run_batch64(args, rank, world):
         "roofline": {"bound": "alu", "kernel": "k_pairs (lmax 10)", "achieved": achieved, "peak": _alu_peak(),
                      "unit": "TFLOP/s", "frac": achieved / _alu_peak(), "traffic": None,
                      "flops_per_pair": fpp, "pairs_per_launch": pairs, "pair_kernel_ms": pair_ms[0]},
-        "gpu_launches": launches, "clocks": clk, "wall_s_timed_region": wall,
+        "gpu_launches": launches, "clocks": clk, "wall_s_timed_region": wall, "tuned": tuned,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -724,6 +796,7 @@ def run_grad(args, rank, world):
     out = torch.empty(2 * plan.ncoeff, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tuned = plan.tuned_config() if args.no_autotune else plan.autotune(pos, w)
     ev = {}
     bwd_ms, bwd_launches = [], []
 
@@ -766,7 +839,7 @@ def run_grad(args, rank, world):
                      "unit": "TFLOP/s", "traffic": None, "flops_per_pair": adjoint_flops_per_pair(4, 4),
                      "note": "achieved counts the adjoint pair work only, over the whole backward call"},
         "gpu_launches": args.steps * fwd["launches"] + sum(bwd_launches), "clocks": clk,
-        "wall_s_timed_region": wall,
+        "wall_s_timed_region": wall, "tuned": tuned,
     }
     line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     if args.scale != 1.0:

@@ -79,6 +79,15 @@ enum { NPCF_BINS_LE = 0, NPCF_BINS_LT = 1 };    /* npcf_opts.bin_order (N=3 only
  * 4PCF has odd components: N=3 and the D=2 4PCF are even (in D=2, r -> -r is a rotation) and the
  * 5PCF keys are the even label sets, so NPCF_PARITY_ODD is refused for them. */
 enum { NPCF_PARITY_ALL = 0, NPCF_PARITY_EVEN = 1, NPCF_PARITY_ODD = 2 };
+/* npcf_opts.basis.  NPCF_BASIS_ISOTROPIC: the zero-total-angular-momentum basis of
+ * eq. Coupling-C (every key above).  NPCF_BASIS_LOS (D = 3, N = 3 or 4): the basis about the
+ * fixed x_3 line of sight of Sec. "Large-Scale Structure" -- the coupling's final state is (L, 0)
+ * for every L the labels allow, N=3 keys (b1, b2; l1, l2, L) with l1, l2 <= lmax and
+ * |l1 - l2| <= L <= l1 + l2, coupling <l1 m l2 -m|L 0>; N=4 keys (b1 < b2 < b3; l1, l2, l12, l3, L)
+ * through <l1 m1 l2 m2|l12 m12><l12 m12 l3 m3|L 0>.  L = 0 gives the isotropic coefficients.
+ * Coefficients are complex; npcf_coeff_index returns 3 (N=3) or 5 (N=4) labels.  Not with
+ * remove_self, a parity selection, the mixed precisions or npcf_backward. */
+enum { NPCF_BASIS_ISOTROPIC = 0, NPCF_BASIS_LOS = 1 };
 
 typedef struct {
     int precision;  /* NPCF_FP32 (positions/weights float, pair and coupling arithmetic FP32,
@@ -101,10 +110,11 @@ typedef struct {
     int parity;     /* NPCF_PARITY_ALL (default), NPCF_PARITY_EVEN or NPCF_PARITY_ODD: the
                        keys the plan returns (npcf_num_coeffs / npcf_coeff_index count and
                        label only those) */
+    int basis;      /* NPCF_BASIS_ISOTROPIC (default) or NPCF_BASIS_LOS (see above) */
 } npcf_opts;
 
 /* Default options: FP32, periodic, b1 <= b2, sync_check = 1, timing = 0, remove_self = 0,
- * parity = NPCF_PARITY_ALL. */
+ * parity = NPCF_PARITY_ALL, basis = NPCF_BASIS_ISOTROPIC. */
 NPCF_API void npcf_default_opts(npcf_opts* opts);
 
 /*
@@ -123,8 +133,9 @@ NPCF_API npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, 
 NPCF_API npcf_status npcf_num_coeffs(npcf_plan_t plan, int64_t* ncoeff);
 
 /* Labels of coefficient i: bins (N-1 entries, host) and ells (host; 1 for N=3: l; 3 for N=4:
- * l1, l2, l3; 5 for N=5: l1, l2, l12, l3, l4).  N=5 keys have b1 < b2 < b3 < b4 and the
- * even-parity label sets (l1 + l2 + l3 + l4 even), 585 of them at lmax = 4. */
+ * l1, l2, l3; 5 for N=5: l1, l2, l12, l3, l4; with NPCF_BASIS_LOS 3 for N=3: l1, l2, L and 5 for
+ * N=4: l1, l2, l12, l3, L).  N=5 keys have b1 < b2 < b3 < b4 and the even-parity label sets
+ * (l1 + l2 + l3 + l4 even), 585 of them at lmax = 4. */
 NPCF_API npcf_status npcf_coeff_index(npcf_plan_t plan, int64_t i, int* bins, int* ells);
 
 /*
@@ -172,6 +183,32 @@ NPCF_API npcf_status npcf_compute_host(npcf_plan_t plan, const void* positions, 
 NPCF_API npcf_status npcf_compute_batched(npcf_plan_t plan, const void* positions, const void* weights,
                                           const int64_t* offsets, const double* boxes, int ncat, double* coeffs,
                                           npcf_stream_t stream);
+
+/*
+ * Coefficients of a field sampled on a periodic grid (Sec. "Application to
+ * Gridded Data"): the integrals of eq. alm-bin-def and eq. NPCF-mult-estimator
+ * become sums over nodes times the node volume dV = prod_a box[a]/dims[a], the
+ * offset 0 is skipped and a^b_l keeps the 1/v_b of the particle estimator:
+ *   a^b_l(c) = (1/v_b) sum_{u != 0} dV X(c + u) Y*_l(unit(u)) Theta^b(|u|),
+ *   zeta     = (1/V) sum_c dV X(c) sum_[l] C prod_i a^{b_i}_{l^i}(c).
+ * The sum over offsets is evaluated as a circular convolution through FFTs
+ * (cuFFT, one forward transform of the field, one inverse per (bin, harmonic
+ * state)); the kernels' transforms are cached in the plan for the last grid
+ * shape.  The coupling is the plan's, with the nodes as primaries.
+ *   field   : device, prod(dims) values of the plan's precision, row-major (the
+ *             last axis fastest); node c sits at c_a box[a]/dims[a].
+ *   dims    : host, D node counts; 2 floor(r_max / h_a) < dims[a] on every axis
+ *             (every offset within r_max reaches a distinct node).
+ *   coeffs  : device, 2*ncoeff doubles, overwritten.
+ * Plans: periodic, isotropic basis, FP32 or FP64, lmax <= 6, no remove_self.
+ * Device memory: 8 (FP32) or 16 (FP64) bytes x nodes x nbins x (complex
+ * harmonic states) for the cached kernel transforms, plus the particle path's
+ * workspace for prod(dims) primaries.
+ * Errors: NPCF_ERR_ARG, NPCF_ERR_UNSUPPORTED, NPCF_ERR_WORKSPACE, NPCF_ERR_CUDA
+ * (cuFFT failures included).
+ */
+NPCF_API npcf_status npcf_compute_grid(npcf_plan_t plan, const void* field, const int* dims, double* coeffs,
+                                       npcf_stream_t stream);
 
 /*
  * Gradient of a scalar loss through the N=3 estimator (the adjoint of
@@ -250,11 +287,33 @@ NPCF_API npcf_status npcf_compute_noalloc(npcf_plan_t plan, const void* position
  * [2] accumulation rounds of the warps' pair batches (each lane adds one pair
  * per round), [3] lane-rounds that added a pair (= pairs; [3] / (32 [2]) is the
  * lane fill), [4] candidate iterations of a warp (32 candidates each),
- * [5] pair batches, [6] iterations with a pair in an edge-flagged table
- * bucket, [7] iterations with a pair decided in FP64.  Writes min(n, 8)
- * entries (the rest zero).
+ * [5] pair batches, [6] candidates in an edge-flagged table bucket, [7]
+ * candidates whose bin was decided in FP64.  Writes min(n, 8) entries (the
+ * rest zero).
  */
 NPCF_API npcf_status npcf_last_counters(npcf_plan_t plan, int64_t* counters, int n);
+
+/*
+ * Autotuning of the launch shapes (no counterpart in the paper): times candidate shapes on a
+ * bounded sample of this input's primaries (about n/50, at least several waves of pair-kernel
+ * work items) and keeps the fastest in the plan for every later call (npcf_compute,
+ * npcf_compute_batched, npcf_backward, npcf_compute_noalloc).  Searched: the pair kernel's warps
+ * per CTA and pairs per warp batch; then the coupling's CTAs per SM (CUDA-core kernels), its FP32
+ * span in chunks (tensor-core kernel) or its primaries per chunk (factored 5PCF).  With the
+ * environment variable NPCF_TUNE_CACHE naming a file, a choice is appended to it keyed by (device,
+ * D, N, lmax, bins, precision, remove_self, size class 2^floor(log2 n)) and later plans load it
+ * without timing (NPCF_TUNE_FORCE set: time again).  Inputs as for npcf_compute; waits for the
+ * stream.  The results of later calls do not depend on the shapes beyond FP32 rounding of the
+ * per-span sums.  Errors: as npcf_compute.
+ */
+NPCF_API npcf_status npcf_autotune(npcf_plan_t plan, const void* positions, const void* weights, int64_t n,
+                                   npcf_stream_t stream);
+
+/* The launch shapes in use (host): [0] pair-kernel warps per CTA, [1] pairs per warp batch,
+ * [2] coupling CTAs per SM (0: built-in), [3] tensor-core FP32 span in chunks (0: built-in),
+ * [4] 5PCF primaries per chunk (0: built-in), [5] 1 if npcf_autotune set them.  Writes
+ * min(n, 6) entries (the rest zero). */
+NPCF_API npcf_status npcf_tuned_config(npcf_plan_t plan, int* values, int n);
 
 /*
  * Diagnostic (no counterpart in the paper): the split-precision tensor-core contraction

@@ -29,7 +29,7 @@
  *                                                              (Sec. "Large-Scale Structure")
  *
  * Readings of the paper that this file takes where the text is silent or
- * garbled (every one is also listed in the design notes):
+ * garbled (the CUDA library takes the same ones, under the same numbers):
  *   R1 the self pair k=j and any pair with r=0 exactly are skipped (Y(0) is
  *      undefined);
  *   R2 degenerate tuples (two secondaries equal) are kept, as in the naive

@@ -121,6 +121,26 @@ def lognormal_poisson(n_mean: float, L: float, seed: int, grid: int = 256, slope
     return _fp32_in_box(x, np.full(3, float(L)))
 
 
+def lognormal_field(shape, seed: int, slope: float = -1.5, sigma: float = 1.0, fp32: bool = True) -> np.ndarray:
+    """A density field on a periodic grid of the given shape (any number of axes): rho = exp(G - s^2/2)
+    with G Gaussian, power spectrum ~ k^slope (k != 0) and standard deviation s = sigma, so rho has
+    mean 1 (FP32-representable unless fp32 is False)."""
+    g = _rng(seed)
+    shape = tuple(int(m) for m in shape)
+    fk = np.fft.fftn(g.standard_normal(shape))
+    k2 = np.zeros(shape)
+    for a, m in enumerate(shape):
+        f = np.fft.fftfreq(m).reshape([-1 if b == a else 1 for b in range(len(shape))])
+        k2 = k2 + f * f
+    k2.flat[0] = 1.0
+    amp = k2 ** (slope / 4.0)
+    amp.flat[0] = 0.0
+    G = np.fft.ifftn(fk * amp).real
+    G *= sigma / G.std()
+    rho = np.exp(G - 0.5 * sigma * sigma)
+    return rho.astype(np.float32).astype(np.float64) if fp32 else rho
+
+
 def normal_weights(n: int, mean: float, sd: float, seed: int, fp32: bool = True) -> np.ndarray:
     """n weights drawn from N(mean, sd^2) (FP32-representable unless fp32 is False)."""
     w = _rng(seed).normal(mean, sd, n)

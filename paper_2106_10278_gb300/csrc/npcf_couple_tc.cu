@@ -46,24 +46,26 @@ __host__ __device__ constexpr int tc_n(int nbins) { return ((2 * nbins + 15) / 1
 __host__ __device__ constexpr int tc_apad(bool tf32) { return tc_chunk(tf32) + 2; }
 
 struct TcSmem {
-    int a_off, w_off, x_off, y_off, stage_off, stage_bytes, a_tile, b_tile, total;
+    int a_off, a_bytes, w_off, p_off, x_off, stage_off, stage_bytes, a_tile, b_tile, total;
 };
 
-// a_off: the chunk's raw a-rows [KP][nb * nq + 1] (padded); x_off: a^b_l (l >= 0) as
-// [nb][L+1][KP + 2] complex; y_off: the same times w_j (the B operand); then two stages of
-// (A hi, A lo, B hi, B lo).
+// a_off: two buffers of a chunk's raw a-rows [KP][nb * nq + 1] (padded; the next chunk's rows
+// arrive by cp.async while the current one is processed); w_off: two buffers of the weights;
+// p_off: the bin pairs (128 int2); x_off: a^b_l (l >= 0) as [nb][L+1][KP + 2] complex; then two
+// stages of (A hi, A lo, B hi, B lo).
 __host__ __device__ inline TcSmem tc_layout(int nbins, int nq, bool tf32)
 {
     TcSmem s{};
     const int KP = tc_chunk(tf32), N = tc_n(nbins), L1 = (nq + 1) / 2;
     int off = 64;  // mbarriers, TMEM slot, flags
     s.a_off = off;
-    off += ((KP * (nbins * nq + 1) * 4 + 15) / 16) * 16;
+    s.a_bytes = ((KP * (nbins * nq + 1) * 4 + 15) / 16) * 16;
+    off += 2 * s.a_bytes;
     s.w_off = off;
-    off += ((KP * 4 + 15) / 16) * 16;
+    off += 2 * ((KP * 4 + 15) / 16) * 16;
+    s.p_off = off;
+    off += 128 * 8;
     s.x_off = off;
-    off += nbins * L1 * tc_apad(tf32) * 8;
-    s.y_off = off;
     off += nbins * L1 * tc_apad(tf32) * 8;
     off = ((off + 127) / 128) * 128;
     s.stage_off = off;
@@ -141,11 +143,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_couple_d2n4_tc(const CouplePa
     int* s_ok = reinterpret_cast<int*>(smem + 20);
     const int L1 = (nq + 1) / 2;  // l = 0..lmax
     const int astr = nb * nq + 1;   // padded raw a-row: the expansion below reads without bank conflicts
-    float* As = reinterpret_cast<float*>(smem + lay.a_off);           // [KP][astr]
-    float* Ws = reinterpret_cast<float*>(smem + lay.w_off);           // [KP]
     constexpr int AP = tc_apad(TF32);
+    int2* Ps = reinterpret_cast<int2*>(smem + lay.p_off);             // [128] bin pairs
     float2* AX = reinterpret_cast<float2*>(smem + lay.x_off);         // [nb][L1][AP]: a^b_l
-    float2* AY = reinterpret_cast<float2*>(smem + lay.y_off);         // [nb][L1][AP]: w_j a^b_l
     unsigned char* stage0 = smem + lay.stage_off;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_couple_d2n4_tc(const CouplePa
         *s_ok = 1;
     }
     if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    for (int r = tid; r < 128; r += kTcThreads) Ps[r] = r < npair ? p.pairs[r] : make_int2(0, 0);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -177,28 +178,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_couple_d2n4_tc(const CouplePa
     double* prow = p.partial + ((size_t)cat * gridDim.x + blockIdx.x) * 2 * p.ncoeff;
     const int nchunk = (nprim + KP - 1) / KP;
 
-    uint32_t committed[2] = {0u, 0u}, waited[2] = {0u, 0u};
-    int it = 0, span_pos = 0;
-    bool aborted = false;
-    for (int ch = blockIdx.x; ch < nchunk && !aborted; ch += gridDim.x) {
+    // a chunk's raw a-rows and weights, copied asynchronously (zero-filled past the last primary)
+    auto fetch = [&](int ch, int buf) {
+        float* As = reinterpret_cast<float*>(smem + lay.a_off + buf * lay.a_bytes);
+        float* Ws = reinterpret_cast<float*>(smem + lay.w_off) + buf * ((KP + 3) / 4 * 4);
         const int p0 = ch * KP, pn = min(KP, nprim - p0);
-        // the chunk's a-rows (contiguous in the a-array, coalesced) and weights; missing primaries are zero
-        {
-            const float* src = aglob + (size_t)p0 * stride;
-            for (int i = tid; i < KP * stride; i += kTcThreads) {
-                const int j = i / stride, r = i - j * stride;
-                As[j * astr + r] = i < pn * stride ? src[i] : 0.f;
-            }
-            for (int i = tid; i < KP; i += kTcThreads) Ws[i] = i < pn ? wglob[p0 + i] : 0.f;
+        const float* src = aglob + (size_t)p0 * stride;
+        for (int j = warp; j < KP; j += kTcThreads / 32)
+            for (int r = lane; r < stride; r += 32)
+                tc::cp_async4(As + j * astr + r, j < pn ? src + (size_t)j * stride + r : aglob, j < pn);
+        for (int i = tid; i < KP; i += kTcThreads) tc::cp_async4(Ws + i, i < pn ? wglob + p0 + i : wglob, i < pn);
+        tc::cp_async_commit();
+    };
+    uint32_t committed[2] = {0u, 0u}, waited[2] = {0u, 0u};
+    int it = 0, span_pos = 0, cb = 0;
+    bool aborted = false;
+    if (blockIdx.x < nchunk) fetch(blockIdx.x, 0);
+    for (int ch = blockIdx.x; ch < nchunk && !aborted; ch += gridDim.x, cb ^= 1) {
+        // the next chunk's rows go to the other buffer (read by the last expansion, long done)
+        if (ch + (int)gridDim.x < nchunk) {
+            fetch(ch + gridDim.x, cb ^ 1);
+            tc::cp_async_wait<1>();
+        } else {
+            tc::cp_async_wait<0>();
         }
-        __syncthreads();  // (also: the previous chunk's operands are formed)
-        // primary-fastest complex a^b_l, l >= 0 (Re a_0; Re, Im of a_l), and the same times w_j
-        for (int i = tid; i < nb * L1 * KP; i += kTcThreads) {
-            const int j = i % KP, bl = i / KP, b = bl / L1, l = bl - b * L1;
+        __syncthreads();  // this chunk's rows are in; (also: the previous chunk's operands are formed)
+        const float* As = reinterpret_cast<const float*>(smem + lay.a_off + cb * lay.a_bytes);
+        const float* Ws = reinterpret_cast<const float*>(smem + lay.w_off) + cb * ((KP + 3) / 4 * 4);
+        // primary-fastest complex a^b_l, l >= 0 (Re a_0; Re, Im of a_l): lanes walk the primaries
+        // (32 / KP rows of (b, l) per warp step)
+        for (int bl0 = warp * (32 / KP); bl0 < nb * L1; bl0 += (kTcThreads / 32) * (32 / KP)) {
+            const int bl = bl0 + lane / KP, j = lane % KP;
+            if (bl >= nb * L1) continue;
+            const int b = bl / L1, l = bl - b * L1;
             const float* ab = As + j * astr + b * nq;
-            const float2 v = l == 0 ? make_float2(ab[0], 0.f) : make_float2(ab[2 * l - 1], ab[2 * l]);
-            AX[bl * AP + j] = v;
-            AY[bl * AP + j] = make_float2(Ws[j] * v.x, Ws[j] * v.y);
+            AX[bl * AP + j] = l == 0 ? make_float2(ab[0], 0.f) : make_float2(ab[2 * l - 1], ab[2 * l]);
         }
         const bool fresh = span_pos == 0;
         for (int g = 0; g < nlg; ++g, ++it) {
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_couple_d2n4_tc(const CouplePa
                 const int r = t & 127, quad = t >> 7;
                 float2 x[4];
                 if (r < npair) {
-                    const int2 bb = p.pairs[r];
+                    const int2 bb = Ps[r];
                     const float4* u = reinterpret_cast<const float4*>(AX + (bb.x * L1 + l1) * AP + quad * 4);
                     const float4* v = reinterpret_cast<const float4*>(AX + (bb.y * L1 + al2) * AP + quad * 4);
                     const float4 u01 = u[0], u23 = u[1], v01 = v[0], v23 = v[1];
@@ -243,12 +257,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_couple_d2n4_tc(const CouplePa
             }
             // B: rows (b3, re) = (Re Y, Im Y) and (b3, im) = (Im Y, -Re Y) per primary, Y = w a^{b3}_{l3}
             for (int t = tid; t < NN * (KP / 4); t += kTcThreads) {
-                const int n = t % NN, quad = t / NN, b3 = n >> 1;
+                const int quad = t / NN, n = t - quad * NN, b3 = n >> 1;  // NN: a multiple of 16
                 float2 x[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    float2 y = b3 < nb ? AY[(b3 * L1 + al3) * AP + quad * 4 + i] : make_float2(0.f, 0.f);
-                    y.y *= s3;
+                    const float wj = Ws[quad * 4 + i];
+                    float2 y = b3 < nb ? AX[(b3 * L1 + al3) * AP + quad * 4 + i] : make_float2(0.f, 0.f);
+                    y = make_float2(wj * y.x, s3 * wj * y.y);
                     x[i] = (n & 1) ? make_float2(y.y, y.x) : y;
                 }
                 store_quad<TF32>(bh, bl, n, quad, x, (n & 1) ? -1.f : 1.f);
@@ -290,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_couple_d2n4_tc(const CouplePa
             const bool rv = r < npair;
             int b2 = 0, key0 = 0;
             if (rv) {
-                b2 = p.pairs[r].y;
+                b2 = Ps[r].y;
                 key0 = p.pair_key[r];
             }
             for (int g = warp >> 2; g < nlg; g += kTcThreads / 128) {

@@ -60,6 +60,7 @@ struct PairParams {
     double edge2[kMaxBins + 1];  // FP64 squares, the exact bin decision
     float tab_lo, tab_inv;       // radial table: bucket k covers [tab_lo + k/tab_inv, ...)
     int warps;                   // primaries per item (= warps per CTA)
+    int batch;                   // pairs per warp batch (multiple of 32, <= 1024)
     int nstencil;
     const int* stencil;          // packed offsets, 8 bits per axis (signed)
     const unsigned char* tab;    // kTab entries
@@ -73,7 +74,7 @@ struct PairParams {
     void* a_out;                 // nprim x nbins x nq (T)
     void* w_out;                 // nprim (T)
     void* self_out;              // nprim x nbins (T): sum of w_k^2 per bin, or NULL
-    unsigned long long* stats;   // [0] pairs, [1] candidates, [2] accumulation rounds, [3] busy lane-rounds, [4] chunks, [5] batches, [6] flagged-bucket iterations, [7] exact-FP64 iterations
+    unsigned long long* stats;   // [0] pairs, [1] candidates, [2] accumulation rounds, [3] busy lane-rounds, [4] chunks, [5] batches, [6] candidates in flagged buckets, [7] candidates decided in FP64
 };
 
 // ----------------------------------------------------------- coupling kernel
@@ -107,7 +108,37 @@ struct CoupleParams {
     int* err;                  // error word: bit 2 = a bounded wait on the tensor core ran out
     const void* self;          // N=3 remove_self: nprim x nbins sums of w_k^2 (T), or NULL
     const void* selfc;         // nbins x (lmax + 1): coincident-direction value c_l / v_b^2 (T)
+    // line-of-sight basis (npcf_couple_los.cu)
+    const int2* los_lam;       // per label set: (first term, end term)
+    const int* los_terms;      // state(l1,m1) | state(l2,m2) << 8 | state(l3,m3) << 16 (all signed m)
+    const void* los_coef;      // the CG product of each term (T)
 };
+
+// --------------------------------------------------------- gridded field
+// The FFT form of the gridded estimator (npcf_grid.cu).
+struct GridParams {
+    int dims[4];
+    int64_t ncell;            // nodes = prod dims
+    double spacing[4];        // box / dims
+    double dV;                // node volume
+    int nbins, nq;
+    double edge2[kMaxBins + 1];
+    double inv_vb[kMaxBins];
+    int ncs;                  // complex harmonic states kept (m >= 0): components (re, im or -1) each
+    const int2* cstate;       // ncs (device)
+    const void* qnorm;        // nq normalisation constants (T)
+    void* khat;               // nbins x ncs x ncell complex: the kernels, then their transforms
+    void* xhat;               // ncell complex: the field, then its transform
+    void* work;               // a batch of spectral products / inverse transforms
+    void* a;                  // ncell x nbins x nq (T): the a-array
+    void* wprim;              // ncell (T): dV X
+};
+
+int grid_max_lmax();
+cudaError_t launch_grid_kernels(const GridParams& g, int D, int fp64, int L, cudaStream_t s);
+cudaError_t launch_grid_field(const GridParams& g, int fp64, const void* X, cudaStream_t s);
+cudaError_t launch_grid_product(const GridParams& g, int fp64, int bs0, int nbs, cudaStream_t s);
+cudaError_t launch_grid_scatter(const GridParams& g, int fp64, int bs0, int nbs, cudaStream_t s);
 
 // ------------------------------------------------- factored 5PCF coupling
 // Tables and scratch of npcf_couple_d3n5f.cu (D=3, N=5, through the intermediate label l12).
@@ -187,6 +218,11 @@ cudaError_t launch_reduce(const double* partial, int rows, int ncols, const int*
 // per catalogue c: out[c][k] = scales[c] * sum_r partial[c][r][colmap[k]]
 cudaError_t launch_reduce_cats(const double* partial, int rows, int ncols, const int* colmap, int nout, int ncat,
                                const double* scales, double* out, cudaStream_t s);
+
+// the line-of-sight basis (npcf_couple_los.cu)
+int los_group(int nbins, int lmax, int fp64);
+int couple_los_smem(const CoupleParams& p, int fp64);
+cudaError_t launch_couple_los(const CoupleParams& p, int fp64, int grid, int smem, cudaStream_t s);
 
 // split-precision tensor-core couplings (npcf_couple_tc.cu)
 int couple_tc_smem(int nbins, int nq, int tf32);

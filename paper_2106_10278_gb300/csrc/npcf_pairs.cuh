@@ -37,24 +37,24 @@ struct PairCfg {
     static constexpr int kThreads = (sizeof(T) == 4) ? (NQ <= 64 ? 512 : 256) : (NQ <= 40 ? 256 : 128);
 };
 
-// Pairs per warp batch: 512 records of 16 bytes (FP32, D <= 3), 256 of the larger records.
+// Pairs per warp batch (a multiple of 32, at most 1024): by default 512 records of 16 bytes
+// (FP32, D <= 3), 256 of the larger records; the plan may choose others (autotuning).
 __host__ __device__ constexpr int pair_batch(int rec_bytes) { return rec_bytes <= 16 ? 512 : 256; }
 
 // Shared-memory carve-up of one CTA (host and device must agree):
 //   radial table + edges | job lists + scan scratch | the item's CatGeom
 //   | per warp: [records (also the merge scratch) | acc[nbins][nq] | bins u8 | idx u16 | 4 x 32 ints
 //                | sum of w^2 per bin (32)]
-__host__ __device__ inline int pair_rec_region(int rec_bytes, int t_bytes, int nq_compiled)
+__host__ __device__ inline int pair_rec_region(int rec_bytes, int t_bytes, int nq_compiled, int B)
 {
-    const int recs = pair_batch(rec_bytes) * rec_bytes;
+    const int recs = B * rec_bytes;
     const int scratch = 32 * (nq_compiled + 1) * t_bytes;
     return ((recs > scratch ? recs : scratch) + 15) / 16 * 16;
 }
 
-__host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int nbins, int nq_compiled)
+__host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int nbins, int nq_compiled, int B)
 {
-    const int B = pair_batch(rec_bytes);
-    return pair_rec_region(rec_bytes, t_bytes, nq_compiled) + (nbins * nq_compiled * t_bytes + 15) / 16 * 16 +
+    return pair_rec_region(rec_bytes, t_bytes, nq_compiled, B) + (nbins * nq_compiled * t_bytes + 15) / 16 * 16 +
            (3 * B + 15) / 16 * 16 + 4 * 32 * 4 + 32 * t_bytes;
 }
 
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     using R = Rec<D, T>;
     constexpr int NQ = PairCfg<D, LMAX, T>::NQ;
     constexpr bool kFP32 = sizeof(T) == 4;
-    constexpr int kB = pair_batch((int)sizeof(R));
+    const int kB = p.batch;
     const unsigned full = 0xffffffffu;
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -370,9 +370,9 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     int* ws = job_pre + kMaxJobs + 4;                        // 68 ints of scan scratch
     CatGeom* s_geo = reinterpret_cast<CatGeom*>(smem + kGeomOffset);
     unsigned char* wbase = smem + pair_fixed_bytes(sizeof(R), nthreads) +
-                           warp * pair_warp_bytes(sizeof(R), sizeof(T), nbins, NQ);
+                           warp * pair_warp_bytes(sizeof(R), sizeof(T), nbins, NQ, kB);
     R* recs = reinterpret_cast<R*>(wbase);
-    T* acc_s = reinterpret_cast<T*>(wbase + pair_rec_region(sizeof(R), sizeof(T), NQ));
+    T* acc_s = reinterpret_cast<T*>(wbase + pair_rec_region(sizeof(R), sizeof(T), NQ, kB));
     unsigned char* bins = reinterpret_cast<unsigned char*>(acc_s) + (nbins * NQ * (int)sizeof(T) + 15) / 16 * 16;
     unsigned short* idx = reinterpret_cast<unsigned short*>(bins + kB);
     int* hist = reinterpret_cast<int*>(bins + (3 * kB + 15) / 16 * 16);
@@ -495,13 +495,13 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                         else dx[d] = (pk.x(d) - xj[d]) + (xj[d] - xjs[d]);
                         r2 = fma(dx[d], dx[d], r2);
                     }
-                    bool anyflag = false, anyexact = false;
-                    const int bin = valid ? decide_bin<D, T>(p, g, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &anyflag,
-                                                             &anyexact)
+                    bool flagged = false, exact = false;
+                    const int bin = valid ? decide_bin<D, T>(p, g, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &flagged,
+                                                             &exact)
                                           : -1;
                     ++nchunks;
-                    nflag += __any_sync(full, anyflag) ? 1u : 0u;
-                    nexact += __any_sync(full, anyexact) ? 1u : 0u;
+                    nflag += flagged ? 1u : 0u;
+                    nexact += exact ? 1u : 0u;
                     // compact the accepted pairs into the batch: unit separation, weight, bin
                     const bool take = bin >= 0;
                     const unsigned tm = __ballot_sync(full, take);
@@ -538,6 +538,8 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         // statistics
         {
             const unsigned tot = __reduce_add_sync(full, npairs);
+            nflag = __reduce_add_sync(full, nflag);
+            nexact = __reduce_add_sync(full, nexact);
             if (lane == 0 && active) {
                 atomicAdd(&p.stats[0], (unsigned long long)tot);
                 atomicAdd(&p.stats[1], ncand);

@@ -2,6 +2,7 @@
 // normalisation tables, lane map), the cell grid, the device workspace, the
 // launch sequence and the C ABI declared in include/npcf.h.
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include <algorithm>
 #include <cmath>
@@ -113,7 +114,12 @@ struct npcf_plan_s {
     int Lc = 0;        // compiled lmax of the pair kernel
     int nq = 0;        // components written per bin (plan lmax)
     int nq_c = 0;      // components of the compiled kernel
-    int threads = 0, warps = 0, pair_smem = 0;
+    int threads = 0, warps = 0, pair_smem = 0, batch = 0, max_warps = 0;
+    // launch shapes the autotuner may change (npcf_autotune); 0 = the built-in choice
+    int rows_mult = 0;   // CUDA-core coupling CTAs per SM (rows = rows_mult * nsm / key blocks)
+    int tc_span_t = 0;   // tensor-core coupling: chunks per FP32 span
+    int d5_npc = 0;      // factored 5PCF: primaries per chunk
+    int tuned = 0;       // 1 once npcf_autotune chose (or loaded) the shapes
     PairParams pp{};
     // device tables
     DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil, d_task;
@@ -122,6 +128,13 @@ struct npcf_plan_s {
     DevBuf d5_rowinfo, d5_colinfo, d5_xoff, d5_zoff, d5_tiles, d5_lamidx, d5_trikey, w_x5, w_z5;
     D3n5Params d5{};           // host copy with the device table pointers (scratch set per call)
     int64_t d5_unit_x = 0, d5_unit_z = 0;  // complex scratch elements per primary of a chunk
+    DevBuf d_los_lam, d_los_terms, d_los_coef;  // line-of-sight basis: term lists per label set
+    // gridded fields (npcf_compute_grid): the kernels' transforms for the last grid shape
+    DevBuf g_khat, g_xhat, g_work, g_cstate, g_small;
+    int g_dims[4] = {0, 0, 0, 0};
+    int g_nbs = 0;
+    cufftHandle g_fft_k = 0, g_fft_x = 0, g_fft_w = 0;  // kernels (batched), field, products (batched)
+    bool g_ready = false;
     DevBuf d_colmap;  // 2*nvis computed columns of the visible outputs (when a parity is selected)
     DevBuf d_selfc;   // remove_self (N=3): c_l / v_b^2 per (bin, l)
     DevBuf w_self;    // remove_self (N=3): sum of w_k^2 per (primary, bin)
@@ -164,7 +177,20 @@ void build_keys(npcf_plan_s* P)
     const int nb = P->nbins, L = P->lmax;
     P->lam.clear();
     // labels: 5 ints per set (unused entries 0): N=3 (l); N=4 (l1, l2, l3); N=5 (l1, l2, l12, l3, l4)
-    if (P->N == 3) {
+    if (P->opts.basis == NPCF_BASIS_LOS) {
+        // the line-of-sight basis: N=3 (l1, l2, L), N=4 (l1, l2, l12, l3, L), every L allowed
+        for (int l1 = 0; l1 <= L; ++l1)
+            for (int l2 = 0; l2 <= L; ++l2) {
+                if (P->N == 3) {
+                    for (int LL = std::abs(l1 - l2); LL <= l1 + l2; ++LL) P->lam.insert(P->lam.end(), {l1, l2, LL, 0, 0});
+                    continue;
+                }
+                for (int l12 = std::abs(l1 - l2); l12 <= l1 + l2; ++l12)
+                    for (int l3 = 0; l3 <= L; ++l3)
+                        for (int LL = std::abs(l12 - l3); LL <= l12 + l3; ++LL)
+                            P->lam.insert(P->lam.end(), {l1, l2, l12, l3, LL});
+            }
+    } else if (P->N == 3) {
         for (int l = 0; l <= L; ++l) P->lam.insert(P->lam.end(), {l, 0, 0, 0, 0});
     } else if (P->N == 5) {
         // even parity (l1 + l2 + l3 + l4), the components counted for the paper's 5PCF
@@ -442,6 +468,27 @@ int pair_threads(int D, int fp64, int L)
 
 int rec_bytes(int D, int fp64) { return (fp64 ? 8 : 4) * 4 * (D <= 3 ? 1 : 2); }
 
+// The pair kernel's launch shape: up to `warps` warps per CTA (fewer if shared memory runs out)
+// and `batch` pairs per warp batch.  Returns false if not even one warp fits.
+bool set_pair_config(npcf_plan_s* P, int warps, int batch)
+{
+    const int rb = rec_bytes(P->D, P->fp64), tb = P->fp64 ? 8 : 4, nb = P->nbins;
+    batch = std::max(64, std::min(1024, batch / 32 * 32));
+    warps = std::max(1, std::min(P->max_warps, warps));
+    while (warps > 1 && pair_fixed_bytes(rb, warps * 32) + warps * pair_warp_bytes(rb, tb, nb, P->nq_c, batch) >
+                            P->smem_optin)
+        --warps;
+    const int smem = pair_fixed_bytes(rb, warps * 32) + warps * pair_warp_bytes(rb, tb, nb, P->nq_c, batch);
+    if (smem > P->smem_optin) return false;
+    P->warps = warps;
+    P->threads = warps * 32;
+    P->batch = batch;
+    P->pair_smem = smem;
+    P->pp.warps = warps;
+    P->pp.batch = batch;
+    return true;
+}
+
 npcf_status ensure_device(npcf_plan_s* P)
 {
     int dev = 0;
@@ -478,7 +525,7 @@ int tc_span()
         const int v = std::atoi(e);
         if (v > 0 && v <= 1024) return v;
     }
-    return 8;
+    return 16;
 }
 
 // ----------------------------------------------------- factored 5PCF tables
@@ -670,8 +717,10 @@ npcf_status build_d3n5f_tables(npcf_plan_s* P)
 
 // Primaries per chunk of the factored 5PCF coupling: its X and Z scratch near 64 MB (it stays in
 // L2 between the two kernels), a multiple of 16 in [16, 512].
-int d3n5f_chunk(const npcf_plan_s* P, size_t budget = size_t(64) << 20)
+int d3n5f_chunk(const npcf_plan_s* P, size_t budget = 0)
 {
+    if (budget == 0 && P->d5_npc > 0) return P->d5_npc;  // the autotuner's choice
+    if (budget == 0) budget = size_t(64) << 20;
     const size_t per = (size_t)(P->d5_unit_x + P->d5_unit_z) * 2 * (P->fp64 ? 8 : 4);
     const size_t c = budget / std::max<size_t>(per, 1);
     return (int)std::max<size_t>(16, std::min<size_t>(512, c / 16 * 16));
@@ -718,17 +767,10 @@ npcf_status setup_tables(npcf_plan_s* P)
                                 P->fp64 ? "FP64" : "FP32");
     P->nq = num_q(D, P->lmax);
     P->nq_c = num_q(D, P->Lc);
-    P->threads = pair_threads(D, P->fp64, P->Lc);
-    const int rb = rec_bytes(D, P->fp64), tb = P->fp64 ? 8 : 4;
-    int warps = P->threads / 32;
-    while (warps > 1 && pair_fixed_bytes(rb, warps * 32) + warps * pair_warp_bytes(rb, tb, nb, P->nq_c) >
-                            P->smem_optin)
-        --warps;
-    P->warps = warps;
-    P->threads = warps * 32;
-    P->pair_smem = pair_fixed_bytes(rb, P->threads) + warps * pair_warp_bytes(rb, tb, nb, P->nq_c);
-    if (P->pair_smem > P->smem_optin)
-        return fail(NPCF_ERR_UNSUPPORTED, "pair kernel needs %d bytes of shared memory", P->pair_smem);
+    P->max_warps = pair_threads(D, P->fp64, P->Lc) / 32;
+    if (!set_pair_config(P, P->max_warps, pair_batch(rec_bytes(D, P->fp64))))
+        return fail(NPCF_ERR_UNSUPPORTED, "pair kernel needs more shared memory than available");
+    const int warps = P->warps;
 
     PairParams& pp = P->pp;
     std::memset(&pp, 0, sizeof(pp));
@@ -738,6 +780,7 @@ npcf_status setup_tables(npcf_plan_s* P)
     pp.nq = P->nq;
     pp.periodic = P->opts.periodic;
     pp.warps = warps;
+    pp.batch = P->batch;
     double maxL = 0.0;
     for (int d = 0; d < D; ++d) maxL = std::max(maxL, P->box[d]);
     const double rmax = P->edges[nb], rmin = P->edges[0];
@@ -830,6 +873,58 @@ npcf_status setup_tables(npcf_plan_s* P)
     CUDA_TRY(upload(P->d_lam2, lam2));
     CUDA_TRY(upload(P->d_lamodd, lamodd));
     if (P->N == 5) return build_d3n5f_tables(P);
+    if (P->opts.basis == NPCF_BASIS_LOS) {
+        // the terms of every label set: the CG chain ending in the state (L, 0)
+        auto cg = [](int j1, int m1, int j2, int m2, int J, int M) {
+            return cx::neg1_pow(j1 - j2 + M) * std::sqrt(2.0 * J + 1.0) * cx::wigner3j(j1, j2, J, m1, m2, -M);
+        };
+        auto st = [](int l, int m) { return l * l + l + m; };
+        std::vector<int2> ll;
+        std::vector<int> terms;
+        std::vector<double> coef;
+        for (int i = 0; i < P->nlam; ++i) {
+            const int* l = &P->lam[5 * i];
+            const int t0 = (int)terms.size();
+            if (P->N == 3) {
+                const int l1 = l[0], l2 = l[1], LL = l[2];
+                for (int m = -l1; m <= l1; ++m) {
+                    if (std::abs(m) > l2) continue;
+                    const double c = cg(l1, m, l2, -m, LL, 0);
+                    if (c == 0.0) continue;
+                    terms.push_back(st(l1, m) | (st(l2, -m) << 8));
+                    coef.push_back(c);
+                }
+            } else {
+                const int l1 = l[0], l2 = l[1], l12 = l[2], l3 = l[3], LL = l[4];
+                for (int m1 = -l1; m1 <= l1; ++m1)
+                    for (int m2 = -l2; m2 <= l2; ++m2) {
+                        const int m12 = m1 + m2;
+                        if (std::abs(m12) > l12 || std::abs(m12) > l3) continue;
+                        const double c = cg(l1, m1, l2, m2, l12, m12) * cg(l12, m12, l3, -m12, LL, 0);
+                        if (c == 0.0) continue;
+                        terms.push_back(st(l1, m1) | (st(l2, m2) << 8) | (st(l3, -m12) << 16));
+                        coef.push_back(c);
+                    }
+            }
+            ll.push_back(make_int2(t0, (int)terms.size()));
+        }
+        CUDA_TRY(upload(P->d_los_lam, ll));
+        CUDA_TRY(upload(P->d_los_terms, terms));
+        if (P->fp64) CUDA_TRY(upload(P->d_los_coef, coef));
+        else CUDA_TRY(upload(P->d_los_coef, cast_vec<float>(coef)));
+        build_key_blocks(P, (int)P->ncoeff);
+        CUDA_TRY(upload(P->d_pairs, P->pairs));
+        CUDA_TRY(upload(P->d_pair_key, P->pair_key));
+        CUDA_TRY(upload(P->d_kblocks, P->kblocks));
+        CUDA_TRY(upload(P->d_task, P->task_pairs));
+        CoupleParams cp{};
+        cp.nbins = nb;
+        cp.lmax = P->lmax;
+        cp.group = los_group(nb, P->lmax, P->fp64);
+        if (couple_los_smem(cp, P->fp64) > P->smem_optin)
+            return fail(NPCF_ERR_UNSUPPORTED, "the line-of-sight coupling needs more shared memory than available");
+        return NPCF_OK;
+    }
     // key blocks: accumulators get what shared memory the per-primary copy leaves
     CoupleParams cp{};
     cp.D = D;
@@ -849,7 +944,7 @@ npcf_status setup_tables(npcf_plan_s* P)
         if (base > P->smem_optin) return fail(NPCF_ERR_UNSUPPORTED, "D=2 4PCF coupling needs %d bytes of shared memory", base);
         build_key_blocks(P, (int)P->ncoeff);
     } else {
-        build_key_blocks(P, std::max(1, budget / (comps * tb)));
+        build_key_blocks(P, std::max(1, budget / (comps * (P->fp64 ? 8 : 4))));
     }
     CUDA_TRY(upload(P->d_pairs, P->pairs));
     CUDA_TRY(upload(P->d_pair_key, P->pair_key));
@@ -949,14 +1044,17 @@ CoupleParams couple_params(const npcf_plan_s* P, const void* a, const void* wpri
     kp.lam2 = P->d_lam2.as<int2>();
     kp.lam_odd = P->d_lamodd.as<signed char>();
     kp.pref = P->d_pref.p;
-    kp.group = d2n4_group(P->nbins, P->lmax);
+    kp.group = P->opts.basis == NPCF_BASIS_LOS ? los_group(P->nbins, P->lmax, P->fp64) : d2n4_group(P->nbins, P->lmax);
+    kp.los_lam = P->d_los_lam.as<int2>();
+    kp.los_terms = P->d_los_terms.as<int>();
+    kp.los_coef = P->d_los_coef.p;
     kp.ncat = 1;
     kp.tc_npairs = (int)P->pairs.size();
     kp.tc_glam = tc_glam(P);
     int cols = 32;
     while (cols < kp.tc_glam * couple_tc_n(P->nbins)) cols *= 2;
     kp.tc_tmem_cols = cols;
-    kp.tc_span = tc_span();
+    kp.tc_span = P->tc_span_t > 0 ? P->tc_span_t : tc_span();
     kp.self = (P->opts.remove_self && P->N == 3) ? P->w_self.p : nullptr;
     kp.selfc = P->d_selfc.p;
     return kp;
@@ -978,6 +1076,8 @@ npcf_status plan_coupling(npcf_plan_s* P, CoupleParams kp, int* err, int rows, i
     if (tc_coupling(P))
         e = launch_couple_d2n4_tc(kp, P->mixed == 2, rows, tc_groups(P),
                                   couple_tc_smem(P->nbins, P->nq, P->mixed == 2), s);
+    else if (P->opts.basis == NPCF_BASIS_LOS)
+        e = launch_couple_los(kp, P->fp64, rows, couple_los_smem(kp, P->fp64), s);
     else
         e = launch_couple(kp, P->fp64, rows, couple_smem(kp, P->fp64), s);
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "coupling kernel launch: %s", cudaGetErrorString(e));
@@ -1095,9 +1195,15 @@ int couple_rows(const npcf_plan_s* P, int64_t nprim, int chunk)
         return (int)std::min<int64_t>(r, std::max<int64_t>(1, (nprim + KP - 1) / KP));
     }
     if (P->N == 5) return d3n5f_ksplit(P, d3n5f_chunk(P));
+    if (P->opts.basis == NPCF_BASIS_LOS) {  // groups of los_group primaries
+        const int G = los_group(P->nbins, P->lmax, P->fp64);
+        const int mult = P->rows_mult > 0 ? P->rows_mult : 2;
+        return (int)std::min<int64_t>(mult * P->nsm, std::max<int64_t>(1, (nprim + G - 1) / G));
+    }
     const int nkb = (int)P->kblocks.size();
-    int rows = std::max(1, (2 * P->nsm) / std::max(nkb, 1));
-    if (d2n4_registers(P)) rows = P->nsm;
+    const int mult = P->rows_mult > 0 ? P->rows_mult : 2;
+    int rows = std::max(1, (mult * P->nsm) / std::max(nkb, 1));
+    if (d2n4_registers(P)) rows = std::max(1, P->nsm * mult / 2);
     return (int)std::min<int64_t>(rows, std::max<int64_t>(1, (nprim + chunk - 1) / chunk));
 }
 
@@ -1366,6 +1472,321 @@ npcf_status check_flags(npcf_plan_s* P)
     return NPCF_OK;
 }
 
+// ------------------------------------------------------------ gridded field
+// The complex harmonic states kept in the a-array (m >= 0): their real and imaginary components.
+std::vector<int2> complex_states(int D, int lmax)
+{
+    std::vector<int2> cs;
+    if (D == 2)
+        for (int l = 0; l <= lmax; ++l) cs.push_back(make_int2(q_index_d2(l), l > 0 ? q_index_d2(l) + 1 : -1));
+    else if (D == 3)
+        for (int l = 0; l <= lmax; ++l)
+            for (int m = 0; m <= l; ++m) cs.push_back(make_int2(q_index_d3(l, m), m > 0 ? q_index_d3(l, m) + 1 : -1));
+    else
+        for (int l3 = 0; l3 <= lmax; ++l3)
+            for (int l2 = 0; l2 <= l3; ++l2)
+                for (int l1 = 0; l1 <= l2; ++l1)
+                    cs.push_back(make_int2(q_index_d4(l3, l2, l1), l1 > 0 ? q_index_d4(l3, l2, l1) + 1 : -1));
+    return cs;
+}
+
+npcf_status cufft_try(cufftResult r, const char* what)
+{
+    if (r != CUFFT_SUCCESS) return fail(NPCF_ERR_CUDA, "%s: cuFFT error %d", what, (int)r);
+    return NPCF_OK;
+}
+
+// The FFT form of the gridded estimator: the kernels' transforms (cached per grid shape), the
+// field's transform, per batch of (bin, state) pairs the spectral products, inverse transforms and
+// the scatter into the a-array, then the plan's coupling over the nodes (weights dV X) and the
+// reduction with 1/V.
+npcf_status run_grid(npcf_plan_s* P, const void* X, const int* dims, double* coeffs, cudaStream_t s)
+{
+    npcf_status st;
+    if ((st = ensure_device(P)) != NPCF_OK) return st;
+    const int D = P->D;
+    const size_t csz = P->fp64 ? 16 : 8;  // complex element
+    GridParams g{};
+    g.ncell = 1;
+    g.dV = 1.0;
+    for (int a = 0; a < D; ++a) {
+        g.dims[a] = dims[a];
+        g.spacing[a] = P->box[a] / dims[a];
+        g.ncell *= dims[a];
+        g.dV *= g.spacing[a];
+    }
+    for (int a = D; a < 4; ++a) g.dims[a] = 1;
+    g.nbins = P->nbins;
+    g.nq = P->nq;
+    const double sa = sphere_area(D);
+    for (int b = 0; b <= P->nbins; ++b) g.edge2[b] = P->edges[b] * P->edges[b];
+    for (int b = 0; b < P->nbins; ++b)
+        g.inv_vb[b] = 1.0 / (sa / D * (std::pow(P->edges[b + 1], D) - std::pow(P->edges[b], D)));
+    const std::vector<int2> cs = complex_states(D, P->lmax);
+    g.ncs = (int)cs.size();
+    g.qnorm = P->d_qnorm.p;
+    const int nbs_all = P->nbins * g.ncs;
+    const bool same = P->g_ready && std::equal(dims, dims + D, P->g_dims);
+    if (!same) {
+        P->g_ready = false;
+        for (cufftHandle* h : {&P->g_fft_k, &P->g_fft_x, &P->g_fft_w})
+            if (*h) {
+                cufftDestroy(*h);
+                *h = 0;
+            }
+        P->g_nbs = (int)std::max<int64_t>(1, std::min<int64_t>(nbs_all, (int64_t(1) << 30) / (g.ncell * csz)));
+        if (P->g_khat.reserve(csz * g.ncell * nbs_all) != cudaSuccess ||
+            P->g_xhat.reserve(csz * g.ncell) != cudaSuccess ||
+            P->g_work.reserve(csz * g.ncell * P->g_nbs) != cudaSuccess || P->g_small.reserve(16) != cudaSuccess)
+            return fail(NPCF_ERR_WORKSPACE, "device allocation of the grid transforms failed");
+        CUDA_TRY(upload(P->g_cstate, cs));
+        int n[4];
+        for (int a = 0; a < D; ++a) n[a] = dims[a];
+        const cufftType ty = P->fp64 ? CUFFT_Z2Z : CUFFT_C2C;
+        const int dist = (int)g.ncell;
+        if ((st = cufft_try(cufftPlanMany(&P->g_fft_k, D, n, nullptr, 1, dist, nullptr, 1, dist, ty, nbs_all),
+                            "kernel transform plan")) != NPCF_OK ||
+            (st = cufft_try(cufftPlanMany(&P->g_fft_x, D, n, nullptr, 1, dist, nullptr, 1, dist, ty, 1),
+                            "field transform plan")) != NPCF_OK ||
+            (st = cufft_try(cufftPlanMany(&P->g_fft_w, D, n, nullptr, 1, dist, nullptr, 1, dist, ty, P->g_nbs),
+                            "inverse transform plan")) != NPCF_OK)
+            return st;
+    }
+    g.cstate = P->g_cstate.as<int2>();
+    g.khat = P->g_khat.p;
+    g.xhat = P->g_xhat.p;
+    g.work = P->g_work.p;
+    for (cufftHandle h : {P->g_fft_k, P->g_fft_x, P->g_fft_w})
+        if ((st = cufft_try(cufftSetStream(h, s), "cufftSetStream")) != NPCF_OK) return st;
+    auto fwd = [&](cufftHandle h, void* data) {
+        return P->fp64 ? cufftExecZ2Z(h, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data, CUFFT_FORWARD)
+                       : cufftExecC2C(h, (cufftComplex*)data, (cufftComplex*)data, CUFFT_FORWARD);
+    };
+    auto inv = [&](cufftHandle h, void* data) {
+        return P->fp64 ? cufftExecZ2Z(h, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data, CUFFT_INVERSE)
+                       : cufftExecC2C(h, (cufftComplex*)data, (cufftComplex*)data, CUFFT_INVERSE);
+    };
+    launch_counter() = 0;
+    P->timed = 0;
+    if (!same) {
+        CUDA_TRY(cudaMemsetAsync(P->g_khat.p, 0, csz * g.ncell * nbs_all, s));
+        CUDA_TRY(launch_grid_kernels(g, D, P->fp64, P->lmax, s));
+        if ((st = cufft_try(fwd(P->g_fft_k, P->g_khat.p), "kernel transforms")) != NPCF_OK) return st;
+        std::copy(dims, dims + D, P->g_dims);
+        P->g_ready = true;
+    }
+    // the a-array and weights of the nodes (the nodes are the primaries)
+    const int chunk = 128;
+    const int rows = couple_rows(P, g.ncell, chunk);
+    if ((st = reserve_workspace(P, 0, g.ncell, rows, 1)) != NPCF_OK) return st;
+    g.a = P->w_a.p;
+    g.wprim = P->w_wprim.p;
+    CUDA_TRY(launch_grid_field(g, P->fp64, X, s));
+    if ((st = cufft_try(fwd(P->g_fft_x, P->g_xhat.p), "field transform")) != NPCF_OK) return st;
+    for (int bs0 = 0; bs0 < nbs_all; bs0 += P->g_nbs) {
+        const int nbs = std::min(P->g_nbs, nbs_all - bs0);
+        CUDA_TRY(launch_grid_product(g, P->fp64, bs0, nbs, s));
+        if (nbs == P->g_nbs) {
+            if ((st = cufft_try(inv(P->g_fft_w, P->g_work.p), "inverse transforms")) != NPCF_OK) return st;
+        } else {
+            for (int i = 0; i < nbs; ++i)  // a last, partial batch: one transform at a time
+                if ((st = cufft_try(inv(P->g_fft_x, P->g_work.as<unsigned char>() + csz * g.ncell * i),
+                                    "inverse transform")) != NPCF_OK)
+                    return st;
+        }
+        CUDA_TRY(launch_grid_scatter(g, P->fp64, bs0, nbs, s));
+    }
+    // the coupling over the nodes, as for particles
+    int* nprim_dev = P->g_small.as<int>();
+    const int nc32 = (int)g.ncell;
+    CUDA_TRY(cudaMemcpyAsync(nprim_dev, &nc32, sizeof(int), cudaMemcpyHostToDevice, s));
+    const int npc = P->N == 5 ? d3n5f_chunk(P) : 0;
+    if (P->N == 5 && (P->w_x5.reserve(d3n5f_scratch_bytes(P, npc, 1)) != cudaSuccess))
+        return fail(NPCF_ERR_WORKSPACE, "device allocation of the 5PCF scratch failed");
+    CoupleParams kp = couple_params(P, P->w_a.p, P->w_wprim.p, nprim_dev, chunk, P->w_partial.as<double>());
+    CUDA_TRY(cudaMemsetAsync(kp.partial, 0, sizeof(double) * rows * 2 * P->ncoeff, s));
+    CUDA_TRY(cudaMemsetAsync(P->w_small.p, 0, 128, s));  // flags, and zero pair statistics
+    if ((st = plan_coupling(P, kp, P->w_small.as<int>() + S_ERR, rows, g.ncell, P->w_x5.p,
+                            P->w_x5.as<unsigned char>() + (size_t)P->d5_unit_x * npc * 2 * (P->fp64 ? 8 : 4), npc,
+                            s)) != NPCF_OK)
+        return st;
+    CUDA_TRY(launch_reduce(kp.partial, rows, (int)(2 * P->ncoeff), plan_colmap(P), (int)(2 * P->nvis), 1.0 / P->V,
+                           coeffs, s));
+    P->last_launches = launch_counter();
+    CUDA_TRY(cudaMemcpyAsync(P->h_small, P->w_small.p, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_stats, P->w_small.as<unsigned char>() + 64, 64, cudaMemcpyDeviceToHost, s));
+    P->last_stream = s;
+    P->last_nprim = g.ncell;
+    return NPCF_OK;
+}
+
+// ------------------------------------------------------------ autotuning
+// The launch shapes a plan may run with, searched on a bounded sample of the caller's input:
+// the pair kernel's warps per CTA and batch size, then the coupling's CTAs per SM (CUDA-core
+// kernels), FP32 span (tensor-core kernel) or primaries per chunk (factored 5PCF).  Each
+// candidate runs the plan on the sample's primaries with CUDA events around its stages; the
+// fastest stage time wins.  Choices are cached per (device, D, N, lmax, bins, precision, size
+// class) in the file named by NPCF_TUNE_CACHE, if set.
+struct TuneShape {
+    int pair_warps = 0, pair_batch = 0, rows_mult = 0, tc_span = 0, d5_npc = 0;
+    // the coupling's tunable: 0 rows_mult, 1 tc_span, 2 d5_npc
+    int& coupling(int which) { return which == 0 ? rows_mult : (which == 1 ? tc_span : d5_npc); }
+};
+
+std::string tune_key(const npcf_plan_s* P, int64_t n)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, P->device);
+    int nlog = 0;
+    while ((int64_t(1) << (nlog + 1)) <= std::max<int64_t>(n, 1)) ++nlog;
+    char buf[320];
+    std::snprintf(buf, sizeof(buf), "%s|D=%d|N=%d|L=%d|nb=%d|prec=%d|self=%d|n=2^%d", prop.name, P->D, P->N, P->lmax,
+                  P->nbins, P->opts.precision, P->opts.remove_self, nlog);
+    for (char* c = buf; *c; ++c)
+        if (*c == ' ' || *c == '\t' || *c == '\n') *c = '_';
+    return buf;
+}
+
+bool tune_cache_load(const std::string& key, TuneShape* t)
+{
+    const char* path = std::getenv("NPCF_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512], k[340];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        TuneShape v;
+        if (std::sscanf(line, "%339s %d %d %d %d %d", k, &v.pair_warps, &v.pair_batch, &v.rows_mult, &v.tc_span,
+                        &v.d5_npc) == 6 &&
+            key == k) {
+            *t = v;  // the last entry of a key wins
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_store(const std::string& key, const TuneShape& t)
+{
+    const char* path = std::getenv("NPCF_TUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), t.pair_warps, t.pair_batch, t.rows_mult, t.tc_span,
+                     t.d5_npc);
+        std::fclose(f);
+    }
+}
+
+void apply_shape(npcf_plan_s* P, const TuneShape& t)
+{
+    if (t.pair_warps > 0 && t.pair_batch > 0 && !set_pair_config(P, t.pair_warps, t.pair_batch))
+        set_pair_config(P, P->max_warps, pair_batch(rec_bytes(P->D, P->fp64)));
+    P->rows_mult = t.rows_mult;
+    P->tc_span_t = t.tc_span;
+    P->d5_npc = t.d5_npc;
+}
+
+// stage times (ms) of one run of the plan on primaries [0, pe): pair kernel, coupling
+npcf_status time_stages(npcf_plan_s* P, const void* pos, const void* w, int64_t n, int64_t pe, double* coeffs,
+                        cudaStream_t s, float* pair_ms, float* couple_ms)
+{
+    npcf_status st = run(P, pos, w, n, coeffs, 0, pe, s);
+    if (st != NPCF_OK) return st;
+    CUDA_TRY(cudaEventSynchronize(P->ev[4]));
+    CUDA_TRY(cudaEventElapsedTime(pair_ms, P->ev[1], P->ev[2]));
+    CUDA_TRY(cudaEventElapsedTime(couple_ms, P->ev[2], P->ev[3]));
+    return NPCF_OK;
+}
+
+npcf_status autotune(npcf_plan_s* P, const void* pos, const void* w, int64_t n, cudaStream_t s)
+{
+    npcf_status st;
+    if ((st = ensure_device(P)) != NPCF_OK) return st;
+    const std::string key = tune_key(P, n);
+    TuneShape best;
+    const bool force = std::getenv("NPCF_TUNE_FORCE") != nullptr;
+    if (!force && tune_cache_load(key, &best)) {
+        apply_shape(P, best);
+        P->tuned = 1;
+        return NPCF_OK;
+    }
+    if (P->w_hout.reserve(sizeof(double) * 2 * P->nvis + 16) != cudaSuccess)
+        return fail(NPCF_ERR_WORKSPACE, "device allocation of the tuning output failed");
+    double* out = P->w_hout.as<double>();
+    // the sample: enough primaries for several waves of pair-kernel items, at most all of them
+    const int64_t pe = std::min<int64_t>(n, std::max<int64_t>((int64_t)P->nsm * P->max_warps * 8, n / 50));
+    const npcf_opts saved = P->opts;
+    P->opts.timing = 1;
+    auto restore = [&]() { P->opts = saved; };
+    // 1. the pair kernel: warps per CTA x batch size
+    const int b0 = pair_batch(rec_bytes(P->D, P->fp64));
+    const int batches[4] = {b0 / 2, b0 * 3 / 4, b0, b0 * 3 / 2};
+    const int mw = P->max_warps;
+    const int warps[3] = {mw, std::max(1, mw * 3 / 4), std::max(1, mw / 2)};
+    float bestp = 1e30f;
+    for (int wi = 0; wi < 3; ++wi)
+        for (int bi = 0; bi < 4; ++bi) {
+            if (wi > 0 && warps[wi] == warps[wi - 1]) continue;
+            if (!set_pair_config(P, warps[wi], batches[bi]) || P->warps != warps[wi]) continue;
+            float pm = 0.f, cm = 0.f;
+            for (int rep = 0; rep < 2; ++rep)  // the first run warms caches and the cell grid
+                if ((st = time_stages(P, pos, w, n, pe, out, s, &pm, &cm)) != NPCF_OK) {
+                    restore();
+                    return st;
+                }
+            if (pm < bestp) {
+                bestp = pm;
+                best.pair_warps = P->warps;
+                best.pair_batch = P->batch;
+            }
+        }
+    if (best.pair_warps == 0) {
+        best.pair_warps = mw;
+        best.pair_batch = b0;
+    }
+    set_pair_config(P, best.pair_warps, best.pair_batch);
+    // 2. the coupling's launch shape
+    float bestc = 1e30f;
+    int cand[4];
+    int which;
+    if (P->N == 5) {
+        const int c0 = d3n5f_chunk(P, size_t(64) << 20);
+        cand[0] = std::max(16, c0 / 4 / 16 * 16);
+        cand[1] = std::max(16, c0 / 2 / 16 * 16);
+        cand[2] = c0;
+        cand[3] = std::min(1024, c0 * 2);
+        which = 2;
+    } else if (tc_coupling(P)) {
+        cand[0] = 4, cand[1] = 8, cand[2] = 16, cand[3] = 32;
+        which = 1;
+    } else {
+        cand[0] = 1, cand[1] = 2, cand[2] = 3, cand[3] = 4;
+        which = 0;
+    }
+    for (int ci = 0; ci < 4; ++ci) {
+        TuneShape t = best;
+        t.coupling(which) = cand[ci];
+        apply_shape(P, t);
+        float pm = 0.f, cm = 0.f;
+        for (int rep = 0; rep < 2; ++rep)
+            if ((st = time_stages(P, pos, w, n, pe, out, s, &pm, &cm)) != NPCF_OK) {
+                restore();
+                return st;
+            }
+        if (cm < bestc) {
+            bestc = cm;
+            best.coupling(which) = cand[ci];
+        }
+    }
+    apply_shape(P, best);
+    restore();
+    P->tuned = 1;
+    tune_cache_store(key, best);
+    return NPCF_OK;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -1381,6 +1802,7 @@ void npcf_default_opts(npcf_opts* o)
     o->timing = 0;
     o->remove_self = 0;
     o->parity = NPCF_PARITY_ALL;
+    o->basis = NPCF_BASIS_ISOTROPIC;
 }
 
 npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const double* edges, int nbins,
@@ -1419,6 +1841,11 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
     if (o.remove_self != 0 && o.remove_self != 1) return fail(NPCF_ERR_ARG, "remove_self must be 0 or 1");
     if (o.parity != NPCF_PARITY_ALL && o.parity != NPCF_PARITY_EVEN && o.parity != NPCF_PARITY_ODD)
         return fail(NPCF_ERR_ARG, "bad parity");
+    if (o.basis != NPCF_BASIS_ISOTROPIC && o.basis != NPCF_BASIS_LOS) return fail(NPCF_ERR_ARG, "bad basis");
+    if (o.basis == NPCF_BASIS_LOS &&
+        (D != 3 || N > 4 || o.remove_self || o.parity != NPCF_PARITY_ALL || o.precision >= NPCF_MIXED_BF16X3))
+        return fail(NPCF_ERR_UNSUPPORTED,
+                    "the line-of-sight basis is provided for D=3, N=3 or 4, without remove_self, parity or mixed precision");
     if (o.parity == NPCF_PARITY_ODD && !(N == 4 && D == 3))
         return fail(NPCF_ERR_UNSUPPORTED, "this plan has no odd-parity components (only the D=3 4PCF has them)");
     for (int d = 0; d < D; ++d) {
@@ -1466,7 +1893,7 @@ npcf_status npcf_coeff_index(npcf_plan_t P, int64_t i, int* bins, int* ells)
     const int64_t ki = P->vis[i];
     for (int k = 0; k < P->N - 1; ++k) bins[k] = P->key_bins[4 * ki + k];
     const int il = P->key_lam[ki];
-    const int ne = P->N == 3 ? 1 : (P->N == 4 ? 3 : 5);
+    const int ne = P->opts.basis == NPCF_BASIS_LOS ? (P->N == 3 ? 3 : 5) : (P->N == 3 ? 1 : (P->N == 4 ? 3 : 5));
     for (int k = 0; k < ne; ++k) ells[k] = P->lam[5 * il + k];
     return NPCF_OK;
 }
@@ -1590,6 +2017,8 @@ npcf_status npcf_backward(npcf_plan_t P, const void* pos, const void* w, int64_t
     if (P->N != 3) return fail(NPCF_ERR_UNSUPPORTED, "the adjoint is implemented for N=3 plans");
     if (P->opts.remove_self)
         return fail(NPCF_ERR_UNSUPPORTED, "the adjoint of the remove_self subtraction is not provided");
+    if (P->opts.basis != NPCF_BASIS_ISOTROPIC)
+        return fail(NPCF_ERR_UNSUPPORTED, "the adjoint is implemented for the isotropic basis");
     if (n < 0 || n > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)n);
     if (!grad_coeffs) return fail(NPCF_ERR_ARG, "grad_coeffs is NULL");
     if (n > 0 && !grad_pos && !grad_w) return fail(NPCF_ERR_ARG, "grad_positions and grad_weights are both NULL");
@@ -1628,6 +2057,53 @@ npcf_status npcf_selftest_tc(int tf32, int n, int k, const float* a, const float
     return NPCF_OK;
 }
 
+npcf_status npcf_compute_grid(npcf_plan_t P, const void* field, const int* dims, double* coeffs, npcf_stream_t stream)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (!field || !dims || !coeffs) return fail(NPCF_ERR_ARG, "field/dims/coeffs is NULL");
+    if (!P->opts.periodic) return fail(NPCF_ERR_UNSUPPORTED, "the gridded estimator needs a periodic plan");
+    if (P->opts.basis != NPCF_BASIS_ISOTROPIC || P->mixed || P->opts.remove_self)
+        return fail(NPCF_ERR_UNSUPPORTED, "the gridded estimator takes isotropic FP32/FP64 plans");
+    if (P->lmax > grid_max_lmax()) return fail(NPCF_ERR_UNSUPPORTED, "the gridded estimator supports lmax <= %d", grid_max_lmax());
+    int64_t ncell = 1;
+    for (int a = 0; a < P->D; ++a) {
+        if (dims[a] < 1) return fail(NPCF_ERR_ARG, "dims[%d] = %d", a, dims[a]);
+        const double h = P->box[a] / dims[a];
+        if (2 * (int64_t)std::floor(P->edges[P->nbins] / h) >= dims[a])
+            return fail(NPCF_ERR_ARG, "r_max reaches half the grid on axis %d (need 2 floor(r_max / h) < dims)", a);
+        ncell *= dims[a];
+    }
+    if (ncell > (int64_t(1) << 30)) return fail(NPCF_ERR_ARG, "grid of %lld nodes is too large", (long long)ncell);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    npcf_status st = run_grid(P, field, dims, coeffs, s);
+    if (st != NPCF_OK) return st;
+    if (P->opts.sync_check) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return check_flags(P);
+    }
+    return NPCF_OK;
+}
+
+npcf_status npcf_autotune(npcf_plan_t P, const void* pos, const void* w, int64_t n, npcf_stream_t stream)
+{
+    if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (n < 1 || n > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)n);
+    if (!pos || !w) return fail(NPCF_ERR_ARG, "positions/weights are NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    npcf_status st = autotune(P, pos, w, n, s);
+    if (st != NPCF_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return check_flags(P);
+}
+
+npcf_status npcf_tuned_config(npcf_plan_t P, int* values, int n)
+{
+    if (!P || (!values && n > 0)) return fail(NPCF_ERR_ARG, "NULL argument");
+    const int v[6] = {P->warps, P->batch, P->rows_mult, P->tc_span_t, P->d5_npc, P->tuned};
+    for (int i = 0; i < n; ++i) values[i] = i < 6 ? v[i] : 0;
+    return NPCF_OK;
+}
+
 const char* npcf_last_error(void) { return g_err.c_str(); }
 
 void npcf_plan_destroy(npcf_plan_t P)
@@ -1643,7 +2119,10 @@ void npcf_plan_destroy(npcf_plan_t P)
                       &P->d5_nlz,  &P->d5_row0, &P->d5_col0, &P->d5_xrow, &P->d5_zcol, &P->d5_rowinfo,
                       &P->d5_colinfo, &P->d5_xoff, &P->d5_zoff, &P->d5_tiles, &P->d5_lamidx, &P->d5_trikey,
                       &P->w_x5,    &P->w_z5,
-                      &P->d_colmap,  &P->d_selfc, &P->w_self};
+                      &P->d_colmap,  &P->d_selfc, &P->w_self, &P->d_los_lam, &P->d_los_terms, &P->d_los_coef,
+                      &P->g_khat,  &P->g_xhat, &P->g_work, &P->g_cstate, &P->g_small};
+    for (cufftHandle h : {P->g_fft_k, P->g_fft_x, P->g_fft_w})
+        if (h) cufftDestroy(h);
     for (DevBuf* b : bufs) b->release();
     if (P->h_small) cudaFreeHost(P->h_small);
     for (auto& e : P->ev)
@@ -1754,7 +2233,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     void *xs = nullptr, *zs = nullptr;
     if (P->N == 5) {
         const size_t left5 = cv.used <= kNoallocBytes ? kNoallocBytes - ((cv.used + 255) & ~size_t(255)) : 0;
-        npc = d3n5f_chunk(P, left5 > 4096 ? left5 - 4096 : 0);
+        npc = d3n5f_chunk(P, left5 > 4096 ? left5 - 4096 : 1);
         const size_t xb = d3n5f_scratch_bytes(P, npc, 1), ub = (size_t)P->d5_unit_x * npc * 2 * tb;
         xs = cv.take(xb);
         zs = static_cast<unsigned char*>(xs) + ub;

@@ -155,6 +155,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 4-byte asynchronous global -> shared copy (cp.async); when `valid` is false the destination is
+// zero-filled and the source is not read.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ------------------------------------------------------------ split precision
 // x = hi + lo + O(2^-18 |x|) with hi, lo BF16 (8-bit significands): hi is x
 // rounded to BF16, lo the rounded remainder.  Two values are packed per 32-bit

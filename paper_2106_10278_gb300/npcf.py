@@ -22,6 +22,7 @@ PRECISIONS = {"fp64": NPCF_FP64, "fp32": NPCF_FP32, "mixed_bf16x3": NPCF_MIXED_B
               "mixed_tf32x3": NPCF_MIXED_TF32X3}
 NPCF_BINS_LE, NPCF_BINS_LT = 0, 1
 PARITIES = {"all": 0, "even": 1, "odd": 2}
+BASES = {"isotropic": 0, "los": 1}
 STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPCF_ERR_CUDA",
           -4: "NPCF_ERR_WORKSPACE", -5: "NPCF_ERR_DEVICE_TIMEOUT", -6: "NPCF_ERR_NONFINITE"}
 
@@ -29,7 +30,7 @@ STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPC
 EXPORTS = ("npcf_default_opts", "npcf_plan_create", "npcf_num_coeffs", "npcf_coeff_index", "npcf_compute",
            "npcf_compute_host", "npcf_device_status", "npcf_last_stats", "npcf_last_profile", "npcf_last_error",
            "npcf_plan_destroy", "npcf_compute_noalloc", "npcf_last_counters", "npcf_backward",
-           "npcf_compute_batched", "npcf_selftest_tc")
+           "npcf_compute_batched", "npcf_selftest_tc", "npcf_autotune", "npcf_tuned_config", "npcf_compute_grid")
 
 
 class NpcfError(RuntimeError):
@@ -41,7 +42,7 @@ class NpcfError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("periodic", ctypes.c_int), ("bin_order", ctypes.c_int),
                 ("sync_check", ctypes.c_int), ("timing", ctypes.c_int), ("remove_self", ctypes.c_int),
-                ("parity", ctypes.c_int)]
+                ("parity", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
 _lib = None
@@ -87,8 +88,14 @@ def load_library(path: str = LIB_PATH):
         lib.npcf_compute_batched.restype = i32
         lib.npcf_backward.argtypes = [P, P, P, i64, P, i64, i64, P, P, P]
         lib.npcf_backward.restype = i32
+        lib.npcf_autotune.argtypes = [P, P, P, i64, P]
+        lib.npcf_autotune.restype = i32
+        lib.npcf_tuned_config.argtypes = [P, ctypes.POINTER(i32), i32]
+        lib.npcf_tuned_config.restype = i32
         lib.npcf_selftest_tc.argtypes = [i32, i32, i32, P, P, P, P]
         lib.npcf_selftest_tc.restype = i32
+        lib.npcf_compute_grid.argtypes = [P, P, ctypes.POINTER(i32), P, P]
+        lib.npcf_compute_grid.restype = i32
         lib.npcf_last_error.argtypes = []
         lib.npcf_last_error.restype = ctypes.c_char_p
         lib.npcf_plan_destroy.argtypes = [P]
@@ -129,6 +136,8 @@ class Plan:
 
     remove_self: subtract the tuples whose secondaries coincide (N=3 keys with b1 = b2).
     parity: "all", "even" or "odd" components (odd ones exist for the D=3 4PCF only).
+    basis: "isotropic" or "los" (D=3, N=3 or 4: the basis about the x_3 line of sight, labels
+    (l1, l2, L) or (l1, l2, l12, l3, L)).
     precision: "fp32" (positions/weights float32; FP32 pair and coupling
     arithmetic, FP64 sums over primaries), "fp64" (double throughout), or
     "mixed_bf16x3" / "mixed_tf32x3" (float32 inputs and pair stage; the coupling
@@ -137,7 +146,7 @@ class Plan:
     """
 
     def __init__(self, D, N, lmax, edges, box, *, precision="fp32", periodic=True, bin_lt=False, sync_check=True,
-                 timing=False, remove_self=False, parity="all"):
+                 timing=False, remove_self=False, parity="all", basis="isotropic"):
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}, not {precision!r}")
         lib = load_library()
@@ -157,6 +166,10 @@ class Plan:
         if parity not in PARITIES:
             raise ValueError(f"parity must be one of {sorted(PARITIES)}, not {parity!r}")
         o.parity = PARITIES[parity]
+        if basis not in BASES:
+            raise ValueError(f"basis must be one of {sorted(BASES)}, not {basis!r}")
+        o.basis = BASES[basis]
+        self.basis = basis
         h = ctypes.c_void_p()
         _check(lib.npcf_plan_create(ctypes.byref(h), self.D, self.N, self.lmax,
                                     self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.nbins,
@@ -170,15 +183,21 @@ class Plan:
     # ------------------------------------------------------------------
     def keys(self) -> np.ndarray:
         """Output labels, one row per coefficient: (b1, b2, b3, l1, l2, l3) for N <= 4 (b3 = -1 and
-        l2 = l3 = 0 when unused); (b1, b2, b3, b4, l1, l2, l12, l3, l4) for N = 5."""
+        l2 = l3 = 0 when unused); (b1, b2, b3, b4, l1, l2, l12, l3, l4) for N = 5; with the
+        line-of-sight basis (b1, b2, b3, l1, l2, L, 0, 0) for N = 3 and (b1, b2, b3, l1, l2, l12,
+        l3, L) for N = 4."""
         if self._keys is None:
             lib = load_library()
-            nb, ne = (4, 5) if self.N == 5 else (3, 3)
+            los = getattr(self, "basis", "isotropic") == "los"
+            if los:
+                nb, ne, nl = 3, 5, (3 if self.N == 3 else 5)
+            else:
+                nb, ne = (4, 5) if self.N == 5 else (3, 3)
+                nl = {3: 1, 4: 3, 5: 5}[self.N]
             k = np.zeros((self.ncoeff, nb + ne), dtype=np.int32)
             k[:, nb - 1] = -1
             bins = (ctypes.c_int * 4)()
             ells = (ctypes.c_int * 5)()
-            nl = {3: 1, 4: 3, 5: 5}[self.N]
             for i in range(self.ncoeff):
                 _check(lib.npcf_coeff_index(self._h, i, bins, ells))
                 for a in range(self.N - 1):
@@ -248,6 +267,28 @@ class Plan:
                                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
         return torch.view_as_complex(out.view(ncat, -1, 2))
 
+    def compute_grid(self, field, out=None, stream=None):
+        """Coefficients of a periodic grid field (a D-dimensional CUDA tensor of the plan's precision
+        over the plan's box, row-major) by the FFT form of the estimator (npcf_compute_grid).
+        Returns a complex128 tensor of ncoeff entries."""
+        import torch
+        lib = load_library()
+        dt = self._dtype()
+        if not field.is_cuda or field.dtype != dt:
+            raise TypeError(f"field must be a {dt} CUDA tensor")
+        if field.dim() != self.D:
+            raise ValueError(f"field must have {self.D} axes")
+        field = field.contiguous()
+        dims = np.ascontiguousarray(field.shape, dtype=np.int32)
+        if out is None:
+            out = torch.empty(2 * self.ncoeff, dtype=torch.float64, device=field.device)
+        s = stream if stream is not None else torch.cuda.current_stream(field.device)
+        with torch.cuda.device(field.device):
+            _check(lib.npcf_compute_grid(self._h, ctypes.c_void_p(field.data_ptr()),
+                                         dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
+        return torch.view_as_complex(out.view(-1, 2))
+
     def backward(self, pos, w, grad_coeffs, primaries=None, stream=None, want_pos=True, want_w=True):
         """dL/dpos (n, D) and dL/dw (n) for device tensors, given dL/dcoeff.
 
@@ -292,6 +333,30 @@ class Plan:
         _check(lib.npcf_compute_host(self._h, pos.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
                                      n, out.ctypes.data_as(ctypes.c_void_p), pb, pe, sptr))
         return out[0::2] + 1j * out[1::2]
+
+    def autotune(self, pos, w, stream=None) -> dict:
+        """Time candidate launch shapes on a sample of these device tensors' primaries and keep the
+        fastest (npcf_autotune); returns the shapes chosen (tuned_config)."""
+        import torch
+        lib = load_library()
+        dt = self._dtype()
+        if not (pos.is_cuda and w.is_cuda) or pos.dtype != dt or w.dtype != dt:
+            raise TypeError(f"pos and w must be {dt} CUDA tensors")
+        pos = pos.contiguous()
+        w = w.contiguous()
+        s = stream if stream is not None else torch.cuda.current_stream(pos.device)
+        with torch.cuda.device(pos.device):
+            _check(lib.npcf_autotune(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                     pos.shape[0], ctypes.c_void_p(s.cuda_stream)))
+        return self.tuned_config()
+
+    def tuned_config(self) -> dict:
+        """The launch shapes in use (npcf_tuned_config)."""
+        lib = load_library()
+        v = (ctypes.c_int * 6)()
+        _check(lib.npcf_tuned_config(self._h, v, 6))
+        names = ("pair_warps", "pair_batch", "couple_ctas_per_sm", "tc_span", "d5_chunk", "tuned")
+        return dict(zip(names, (int(x) for x in v)))
 
     def stats(self) -> dict:
         """Pairs accumulated, primaries and candidate secondaries of the last call."""

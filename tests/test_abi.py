@@ -81,6 +81,10 @@ def _create(lib, D, N, lmax, edges, box, opts=None):
         (3, 3, 2, [0.1, 0.2], [1] * 3, {"precision": 2}, -2),  # split precision: tensor-core couplings only
         (2, 4, 2, list(np.linspace(0.01, 0.1, 19)), [1] * 2, {"precision": 3}, -2),  # > 128 bin pairs
         (2, 4, 2, [0.1, 0.2, 0.3, 0.4], [1] * 2, {"precision": 7}, -1),  # unknown precision
+        (2, 3, 2, [0.1, 0.2], [1] * 2, {"basis": 1}, -2),  # the line-of-sight basis is D=3 only
+        (3, 5, 2, [0.1, 0.2, 0.3, 0.4, 0.45], [1] * 3, {"basis": 1}, -2),  # ... and N <= 4
+        (3, 3, 2, [0.1, 0.2], [1] * 3, {"basis": 1, "remove_self": 1}, -2),
+        (3, 3, 2, [0.1, 0.2], [1] * 3, {"basis": 9}, -1),  # unknown basis
         (3, 4, 7, [0.1, 0.2, 0.3, 0.4], [1] * 3, None, -2),  # lmax beyond the compiled coupling
         (3, 3, 2, list(np.linspace(0.01, 0.3, 40)), [1] * 3, None, -2),  # more than 32 bins
         (3, 3, 2, [0.2, 0.1], [1] * 3, None, -1),  # decreasing edges

@@ -122,3 +122,22 @@ def test_grid_rejects_offsets_that_alias():
         oracle.grid_alm(2, np.array([0.1, 0.5]), 1.0, X)
     with pytest.raises(ValueError):
         oracle.estimate_grid(3, 2, np.array([0.1, 0.5]), 1.0, X)
+
+
+def test_grid_constant_field_shell_counts():
+    """A constant field X: a^b_00 = X dV (nodes in shell b, offset 0 excluded) / (v_b sqrt(4 pi)),
+    every node alike, so the l = 0 coefficient of the 3PCF is X a^0_00 a^1_00 (the node sum of
+    dV X is X V); the shell's nodes are counted here by brute force."""
+    edges = np.array([0.1, 0.2, 0.3])
+    X = np.full((20, 20, 20), 1.5)
+    keys, z = oracle.estimate_grid(3, 2, edges, np.ones(3), X)
+    h = 1.0 / 20
+    o = np.arange(-6, 7)
+    r2 = (o[:, None, None] ** 2 + o[None, :, None] ** 2 + o[None, None, :] ** 2) * h * h
+    cnt = [np.count_nonzero((r2 >= edges[b] ** 2) & (r2 < edges[b + 1] ** 2) & (r2 > 0)) for b in range(2)]
+    vb = [4 * np.pi / 3 * (edges[b + 1] ** 3 - edges[b] ** 3) for b in range(2)]
+    a0 = [1.5 * h ** 3 * cnt[b] / vb[b] / np.sqrt(4 * np.pi) for b in range(2)]
+    i = [j for j in range(len(keys)) if keys[j][0] == 0 and keys[j][1] == 1 and all(x == 0 for x in keys[j][3:])]
+    assert len(i) == 1
+    expect = 1.5 * a0[0] * a0[1]
+    assert abs(z[i[0]] - expect) <= 1e-13 * abs(expect)
