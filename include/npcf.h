@@ -298,8 +298,9 @@ NPCF_API npcf_status npcf_last_counters(npcf_plan_t plan, int64_t* counters, int
  * bounded sample of this input's primaries (about n/50, at least several waves of pair-kernel
  * work items) and keeps the fastest in the plan for every later call (npcf_compute,
  * npcf_compute_batched, npcf_backward, npcf_compute_noalloc).  Searched: the pair kernel's warps
- * per CTA and pairs per warp batch; then the coupling's CTAs per SM (CUDA-core kernels), its FP32
- * span in chunks (tensor-core kernel) or its primaries per chunk (factored 5PCF).  With the
+ * per CTA and pairs per warp batch; then, timed alone on the a-array of a quarter of the
+ * primaries, the coupling's CTAs per SM (CUDA-core kernels), its FP32 span in chunks (tensor-core
+ * kernel) or its primaries per chunk (factored 5PCF).  With the
  * environment variable NPCF_TUNE_CACHE naming a file, a choice is appended to it keyed by (device,
  * D, N, lmax, bins, precision, remove_self, size class 2^floor(log2 n)) and later plans load it
  * without timing (NPCF_TUNE_FORCE set: time again).  Inputs as for npcf_compute; waits for the

@@ -393,9 +393,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nbins = p.nbins, nq = p.nq;
     unsigned char* tab = smem;
-    float* s_edge = reinterpret_cast<float*>(tab + kTab);
-    double* s_edge2 = reinterpret_cast<double*>(tab + kTab + 192);
-    int* job_a = reinterpret_cast<int*>(tab + kTab + 576);
+    float* s_edge = reinterpret_cast<float*>(tab + kTabBytes);
+    double* s_edge2 = reinterpret_cast<double*>(tab + kTabBytes + 192);
+    int* job_a = reinterpret_cast<int*>(tab + kTabBytes + 576);
     int* job_pk = job_a + kMaxJobs;
     int* job_pre = job_pk + kMaxJobs;
     int* ws = job_pre + kMaxJobs + 4;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_pairs_adjoint(const PairParams 
     int* ring_b = ring_k + kRing;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    for (int i = threadIdx.x; i < kTab / 4; i += nthreads)
+    for (int i = threadIdx.x; i < kTabBytes / 4; i += nthreads)
         reinterpret_cast<int*>(tab)[i] = reinterpret_cast<const int*>(p.tab)[i];
     if (threadIdx.x <= nbins) {
         s_edge[threadIdx.x] = p.edgef[threadIdx.x];

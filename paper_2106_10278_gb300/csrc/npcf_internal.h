@@ -9,7 +9,9 @@ namespace npcf {
 
 constexpr int kMaxBins = 32;   // the pair kernel shares a warp's 32 lanes out among the bins
 constexpr int kMaxD = 4;
-constexpr int kTab = 4096;     // radial lookup-table entries
+constexpr int kTab = 4096;     // radial lookup-table buckets
+constexpr int kTabBytes = kTab + 16;  // the table: a guard entry, the buckets, a guard entry, padding
+constexpr int kRecPad = 128;   // records readable past the last one (the pair kernel's prefetch runs ahead)
 
 // ------------------------------------------------------- catalogue geometry
 // The cell grid of one catalogue.  A call covers one or more catalogues; their
@@ -63,7 +65,7 @@ struct PairParams {
     int batch;                   // pairs per warp batch (multiple of 32, <= 1024)
     int nstencil;
     const int* stencil;          // packed offsets, 8 bits per axis (signed)
-    const unsigned char* tab;    // kTab entries
+    const unsigned char* tab;    // kTabBytes entries: [0] and [kTab + 1] "no bin", bucket k at [k + 1]
     const void* rec;             // sorted records
     const int* cell_start;
     const int4* items;           // (global cell, slot_lo, count | catalogue << 8, primary_base)

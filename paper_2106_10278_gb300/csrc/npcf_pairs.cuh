@@ -7,10 +7,10 @@
 //  * One CTA takes one work item = up to W primaries of one cell; warp w owns
 //    primary w.  The CTA lists the item's neighbour cells (the stencil cells
 //    within r_max of the primary cell that are non-empty) in shared memory
-//    once; then every warp walks that list on its own, skips the cells its
-//    primary cannot reach, and streams the candidates from global memory
-//    (L1/L2 resident) with a two-deep register prefetch -- no block barriers
-//    while scanning.
+//    once; every warp then marks, 32 cells at a time, the cells its primary
+//    can reach (a bit mask), walks the marked cells on its own and streams
+//    their candidates from global memory (L1/L2 resident) with a two-deep
+//    register prefetch -- no block barriers while scanning.
 //  * Accepted pairs (unit separation, weight, bin) are compacted into a
 //    per-warp batch in shared memory.  A full batch is counting-sorted by bin
 //    (arrival order kept inside a bin), the 32 lanes are shared out among the
@@ -20,8 +20,11 @@
 //    accumulators in shared memory.  Every sum runs in a fixed order, so the
 //    results are bitwise reproducible.
 //  * The bin of a pair is decided exactly as the FP64 definition decides it:
-//    FP32 distances pick the bin, and any pair within a few FP32 ulps of an
-//    edge is re-decided from the original coordinates in FP64.
+//    the FP32 r^2 indexes a table of bins (guard entries catch r^2 outside
+//    the bins); the few table buckets that an edge's FP32 error window
+//    touches are re-decided in FP32, and pairs within that window from the
+//    original coordinates in FP64 -- a warp-uniform branch taken only when a
+//    lane needs it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -37,6 +40,9 @@ struct PairCfg {
     static constexpr int kThreads = (sizeof(T) == 4) ? (NQ <= 64 ? 512 : 256) : (NQ <= 40 ? 256 : 128);
 };
 
+constexpr int kMaxJobs = 640;   // neighbour cells of one item (the largest stencil used: 613 cells, D=3 c=4)
+constexpr int kJobWords = kMaxJobs / 32;
+
 // Pairs per warp batch (a multiple of 32, at most 1024): by default 512 records of 16 bytes
 // (FP32, D <= 3), 256 of the larger records; the plan may choose others (autotuning).
 __host__ __device__ constexpr int pair_batch(int rec_bytes) { return rec_bytes <= 16 ? 512 : 256; }
@@ -44,7 +50,7 @@ __host__ __device__ constexpr int pair_batch(int rec_bytes) { return rec_bytes <
 // Shared-memory carve-up of one CTA (host and device must agree):
 //   radial table + edges | job lists + scan scratch | the item's CatGeom
 //   | per warp: [records (also the merge scratch) | acc[nbins][nq] | bins u8 | idx u16 | 4 x 32 ints
-//                | sum of w^2 per bin (32)]
+//                | sum of w^2 per bin (32) | reachable-cell mask (kMaxJobs bits)]
 __host__ __device__ inline int pair_rec_region(int rec_bytes, int t_bytes, int nq_compiled, int B)
 {
     const int recs = B * rec_bytes;
@@ -55,13 +61,11 @@ __host__ __device__ inline int pair_rec_region(int rec_bytes, int t_bytes, int n
 __host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int nbins, int nq_compiled, int B)
 {
     return pair_rec_region(rec_bytes, t_bytes, nq_compiled, B) + (nbins * nq_compiled * t_bytes + 15) / 16 * 16 +
-           (3 * B + 15) / 16 * 16 + 4 * 32 * 4 + 32 * t_bytes;
+           (3 * B + 15) / 16 * 16 + 4 * 32 * 4 + 32 * t_bytes + kJobWords * 4;
 }
 
-constexpr int kMaxJobs = 640;   // neighbour cells of one item (the largest stencil used: 613 cells, D=3 c=4)
-
 // fixed part: radial table | edges (576) | job lists + scan scratch | the item's CatGeom
-constexpr int kGeomOffset = kTab + 576 + (3 * kMaxJobs + 4 + 72) * 4;
+constexpr int kGeomOffset = kTabBytes + 576 + (3 * kMaxJobs + 4 + 72) * 4;
 __host__ __device__ inline int pair_fixed_bytes(int rec_bytes, int threads)
 {
     (void)rec_bytes;
@@ -137,26 +141,22 @@ __device__ __forceinline__ void block_scan2(int a, int b, int* ea, int* eb, int*
 
 
 // The radial bin of one candidate pair, decided exactly as the FP64 definition
-// decides it ([e_b, e_{b+1}) on the FP64 r^2 of the original coordinates):
-// the FP32 r^2 indexes a table over r^2 (bits 0-5 the bin, 63 = none; bit 6:
-// an edge lies within the FP32 error window of the bucket); flagged buckets
-// are re-decided in FP32 unless the pair sits within that window, and those
-// few pairs in FP64.  Returns -1 outside the bins.  Shared by the forward and
-// adjoint pair kernels so that both see the same pair set.
+// decides it ([e_b, e_{b+1}) on the FP64 r^2 of the original coordinates).
+// `code` is the table entry of the pair's FP32 r^2 (bits 0-5 the bin, 63 = none;
+// bit 6: an edge lies within the FP32 error window of the bucket): a flagged
+// bucket is re-decided in FP32 unless the pair sits within that window, and
+// those few pairs in FP64 (FP64 plans: every pair in FP64).  Returns -1
+// outside the bins.
 template <int D, typename T>
-__device__ __forceinline__ int decide_bin(const PairParams& p, const CatGeom& g, const unsigned char* tab,
-                                          const float* s_edge, const double* s_edge2, const int* cc, int packed,
-                                          const T* xj, const Rec<D, T>& pk, T r2, bool* flagged, bool* exact_out)
+__device__ __forceinline__ int bin_refine(const PairParams& p, const CatGeom& g, const float* s_edge,
+                                          const double* s_edge2, const int* cc, int packed, const T* xj,
+                                          const Rec<D, T>& pk, T r2, int code, bool* exact_out)
 {
     constexpr bool kFP32 = sizeof(T) == 4;
-    if (!(r2 > T(0) && r2 < T(p.rmax2f) && r2 >= T(p.rmin2f))) return -1;
-    int kk = (int)(((float)r2 - p.tab_lo) * p.tab_inv);
-    kk = kk < 0 ? 0 : (kk >= kTab ? kTab - 1 : kk);
-    const int code = tab[kk];
+    if (!(r2 > T(0))) return -1;
     int b = (code & 63) == 63 ? -1 : (code & 63);
     bool exact = !kFP32;
     if (kFP32 && (code & 64)) {
-        *flagged = true;
         const float r = (float)r2 * rsqrtf((float)r2);
         // bb = number of edges <= r, walked from the bucket's own count (0-1 steps)
         int bb = (code & 63) == 63 ? (r >= s_edge[p.nbins >> 1] ? p.nbins + 1 : 0) : (code & 63) + 1;
@@ -185,6 +185,33 @@ __device__ __forceinline__ int decide_bin(const PairParams& p, const CatGeom& g,
         }
     }
     return b;
+}
+
+// The same decision from r^2 alone (range check, table, refinement); shared by
+// the adjoint pair kernel and the FP64 forward path so that all see one pair set.
+// tab: the guarded table (bucket k at tab[k + 1]).
+template <int D, typename T>
+__device__ __forceinline__ int decide_bin(const PairParams& p, const CatGeom& g, const unsigned char* tab,
+                                          const float* s_edge, const double* s_edge2, const int* cc, int packed,
+                                          const T* xj, const Rec<D, T>& pk, T r2, bool* flagged, bool* exact_out)
+{
+    constexpr bool kFP32 = sizeof(T) == 4;
+    if (!(r2 > T(0) && r2 < T(p.rmax2f) && r2 >= T(p.rmin2f))) return -1;
+    int kk = (int)(((float)r2 - p.tab_lo) * p.tab_inv);
+    kk = kk < 0 ? 0 : (kk >= kTab ? kTab - 1 : kk);
+    const int code = tab[kk + 1];
+    if (kFP32 && (code & 64)) *flagged = true;
+    return bin_refine<D, T>(p, g, s_edge, s_edge2, cc, packed, xj, pk, r2, code, exact_out);
+}
+
+// ceil(a / b) for 0 <= a < 2^20, 1 <= b < 2^20, without an integer division: the FP32
+// quotient is within one of the true one and is corrected with exact integer products.
+__device__ __forceinline__ int ceil_div_small(int a, int b)
+{
+    int q = (int)((float)a * __frcp_rn((float)b));
+    q -= (q * b > a) ? 1 : 0;
+    q += ((q + 1) * b <= a) ? 1 : 0;
+    return q + ((q * b < a) ? 1 : 0);
 }
 
 // Cell geometry of one stencil cell for one primary: the shifted primary
@@ -264,13 +291,18 @@ __device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned
         if (lane >= o) incl += v;
     }
     const int start = incl - cnt;
-    // 2. rounds R: the fewest with sum_b ceil(n_b / R) <= 32 lanes
-    int R = (nbuf + 31) >> 5, nl = 0;
-    for (;;) {
-        nl = cnt > 0 ? (cnt + R - 1) / R : 0;
-        if (__reduce_add_sync(full, nl) <= 32) break;
-        ++R;
+    // 2. rounds R: the fewest with sum_b ceil(n_b / R) <= 32 lanes.  R = ceil(nbuf / 32) is a lower
+    // bound and ceil(nbuf / (32 - nonempty bins)) satisfies it (sum ceil <= nbuf / R + nonempty);
+    // bisect between them
+    const int nne = __popc(__ballot_sync(full, cnt > 0));
+    int R = (nbuf + 31) >> 5;
+    int Rhi = nne < 32 ? ceil_div_small(nbuf, 32 - nne) : nbuf;
+    while (R < Rhi) {
+        const int mid = (R + Rhi) >> 1;
+        if (__reduce_add_sync(full, ceil_div_small(cnt, mid)) <= 32) Rhi = mid;
+        else R = mid + 1;
     }
+    const int nl = ceil_div_small(cnt, R);
     nrounds += (unsigned)R;
     int ninc = nl;
 #pragma unroll
@@ -311,18 +343,26 @@ __device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned
         __syncwarp();
     }
     // 5. every lane accumulates the pairs of its bin, lanes of one bin taking every my_nl-th
+    // (the next record is loaded before the current one is accumulated; the index is clamped into
+    // the batch, so the extra load at the end is harmless)
     T w2 = T(0);
-    if (my_rank < my_nl) {
+    if (my_rank < my_nl && my_rank < my_cnt) {
+        const int last = nbuf - 1;
+        Rec<D, T> e = recs[idx[my_start + my_rank]];
         for (int k = my_rank; k < my_cnt; k += my_nl) {
-            const Rec<D, T> e = recs[idx[my_start + k]];
+            const Rec<D, T> en = recs[idx[min(my_start + k + my_nl, last)]];
             if constexpr (D == 2) accum_d2<LMAX, T>(acc, e.x(0), e.x(1), e.w());
             else if constexpr (D == 3) accum_d3<LMAX, T>(acc, e.x(0), e.x(1), e.x(2), e.w());
             else accum_d4<LMAX, T>(acc, e.x(0), e.x(1), e.x(2), e.x(3), e.w());
             w2 = fma(e.w(), e.w(), w2);
+            e = en;
         }
     }
     __syncwarp();
-    // 6. merge: the lanes' sums through the record space into acc_s (segments in lane order)
+    // 6. merge: the lanes' sums through the record space into acc_s (segments in lane order).
+    // Components 0..31 go lane = component over the bins in turn (the segment length is the same
+    // for the whole warp); the last NQ - 32 components and the w^2 sums are shared out over
+    // (bin, component).
     T* scr = reinterpret_cast<T*>(recs);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -331,18 +371,27 @@ __device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned
     }
     scr[lane * (NQ + 1) + NQ] = w2;
     __syncwarp();
-    if (lane < nbins) {
-        const int f = segf[lane], n = segn[lane];
-        T sum = T(0);
-        for (int l = 0; l < n; ++l) sum += scr[(f + l) * (NQ + 1) + NQ];
-        w2_s[lane] += sum;
+    constexpr int QA = NQ < 32 ? NQ : 32;  // components merged lane-parallel
+    constexpr int QB = NQ + 1 - QA;         // the rest (w^2 last)
+    unsigned bm = E;                        // bins with a segment
+    while (bm) {
+        const int b = __ffs(bm) - 1;
+        bm &= bm - 1;
+        const int f = __shfl_sync(full, first, b), n = __shfl_sync(full, nl, b);
+        if (lane < QA) {
+            const T* col = scr + f * (NQ + 1) + lane;
+            T sum = col[0];
+            for (int l = 1; l < n; ++l) sum += col[l * (NQ + 1)];
+            acc_s[b * NQ + lane] += sum;
+        }
     }
-    for (int o = lane; o < nbins * NQ; o += 32) {
-        const int b = o / NQ, q = o - b * NQ;
+    for (int o = lane; o < nbins * QB; o += 32) {
+        const int b = o / QB, q = QA + (o - b * QB);
         const int f = segf[b], n = segn[b];
         T sum = T(0);
         for (int l = 0; l < n; ++l) sum += scr[(f + l) * (NQ + 1) + q];
-        acc_s[o] += sum;
+        if (q < NQ) acc_s[b * NQ + q] += sum;
+        else w2_s[b] += sum;
     }
     __syncwarp();
 }
@@ -361,10 +410,10 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int nbins = p.nbins;
-    unsigned char* tab = smem;
-    float* s_edge = reinterpret_cast<float*>(tab + kTab);          // nbins + 1
-    double* s_edge2 = reinterpret_cast<double*>(tab + kTab + 192);  // nbins + 1
-    int* job_a = reinterpret_cast<int*>(tab + kTab + 576);  // kMaxJobs: first slot of the cell
+    unsigned char* tab = smem;                                          // guarded table (kTabBytes)
+    float* s_edge = reinterpret_cast<float*>(tab + kTabBytes);          // nbins + 1
+    double* s_edge2 = reinterpret_cast<double*>(tab + kTabBytes + 192);  // nbins + 1
+    int* job_a = reinterpret_cast<int*>(tab + kTabBytes + 576);  // kMaxJobs: first slot of the cell
     int* job_pk = job_a + kMaxJobs;                          // kMaxJobs: packed stencil offset
     int* job_pre = job_pk + kMaxJobs;                        // kMaxJobs + 1: record prefix
     int* ws = job_pre + kMaxJobs + 4;                        // 68 ints of scan scratch
@@ -379,8 +428,9 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     int* cursor = hist + 32;
     int* seg = cursor + 32;  // 64 ints
     T* w2_s = reinterpret_cast<T*>(seg + 64);  // 32
+    unsigned* jmask = reinterpret_cast<unsigned*>(w2_s + 32);  // kJobWords: cells this warp's primary reaches
 
-    for (int i = threadIdx.x; i < kTab / 4; i += nthreads)
+    for (int i = threadIdx.x; i < kTabBytes / 4; i += nthreads)
         reinterpret_cast<int*>(tab)[i] = reinterpret_cast<const int*>(p.tab)[i];
     if (threadIdx.x <= nbins) {
         s_edge[threadIdx.x] = p.edgef[threadIdx.x];
@@ -390,6 +440,10 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     const T* inv_vb = static_cast<const T*>(p.inv_vb);
     const R* rec = static_cast<const R*>(p.rec);
     const int nq = p.nq;
+
+    // work counters of this warp, added to the statistics once at the end
+    unsigned long long ncand = 0, npairs_w = 0;
+    unsigned nrounds = 0, nbatch = 0, nchunks = 0, nflag = 0, nexact = 0;
 
     __shared__ int s_item;
     for (;;) {
@@ -402,9 +456,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         load_geom(s_geo, p.geo, it.z >> 8);
         __syncthreads();
         const CatGeom& g = *s_geo;
-        const bool active = warp < (it.z & 0xff);
-        const int jslot = it.y + (active ? warp : 0);
-        const int pidx = it.w + warp;
+        const int nprim_item = it.z & 0xff;
 
         int cc[D];
 #pragma unroll
@@ -451,80 +503,128 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         if (threadIdx.x == 0) job_pre[njobs] = V;
         __syncthreads();
 
-        const R pj = rec[jslot];
-        T xj[D];
+        // warp w takes the item's primary w
+        if (warp < nprim_item) {
+            const int jslot = it.y + warp;
+            const int pidx = it.w + warp;
+            const R pj = rec[jslot];
+            T xj[D];
 #pragma unroll
-        for (int d = 0; d < D; ++d) xj[d] = pj.x(d);
-        const T wj = pj.w();
+            for (int d = 0; d < D; ++d) xj[d] = pj.x(d);
+            const T wj = pj.w();
 
-        T acc[NQ];
+            T acc[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = T(0);
-        for (int i = lane; i < nbins * NQ; i += 32) acc_s[i] = T(0);
-        w2_s[lane] = T(0);
-        __syncwarp();
-        int nbuf = 0;  // warp-uniform: staged pairs of the current batch
-        unsigned npairs = 0;
-        unsigned long long ncand = 0;
-        unsigned nrounds = 0, nbatch = 0, nchunks = 0, nflag = 0, nexact = 0;
+            for (int q = 0; q < NQ; ++q) acc[q] = T(0);
+            for (int i = lane; i < nbins * NQ; i += 32) acc_s[i] = T(0);
+            w2_s[lane] = T(0);
 
-        // every warp walks the item's cells on its own, streaming candidates from
-        // global memory (L1/L2) with a two-deep register prefetch: no block barriers
-        if (active) {
-            for (int j = 0; j < njobs; ++j) {
-                const int seg_a = job_a[j];
-                const int seg_n = job_pre[j + 1] - job_pre[j];
-                const int packed = job_pk[j];
+            // the cells this primary can reach, 32 at a time
+            for (int j0 = 0; j0 < njobs; j0 += 32) {
+                const int j = j0 + lane;
                 T xjs[D];
-                if (!cell_geometry<D, T>(p, g, cc, packed, xj, xjs)) continue;
-                ncand += seg_n;
-                const R* src = rec + seg_a;
-                R nxt0 = ldg_rec(src, lane < seg_n ? lane : 0);
-                R nxt1 = ldg_rec(src, 32 + lane < seg_n ? 32 + lane : 0);
-                for (int c0 = 0; c0 < seg_n; c0 += 32) {
-                    const int k = c0 + lane;
-                    const bool valid = k < seg_n;
-                    const R pk = nxt0;
-                    nxt0 = nxt1;
-                    if (c0 + 64 < seg_n) nxt1 = ldg_rec(src, c0 + 64 + lane < seg_n ? c0 + 64 + lane : 0);
-                    T dx[D];
-                    T r2 = T(0);
+                const bool ok = j < njobs && cell_geometry<D, T>(p, g, cc, job_pk[j], xj, xjs);
+                const unsigned m = __ballot_sync(full, ok);
+                if (lane == 0) jmask[j0 >> 5] = m;
+            }
+            __syncwarp();
+
+            // walk the marked cells, streaming their candidates from global memory (L1/L2)
+            int nbuf = 0;  // warp-uniform: staged pairs of the current batch
+            const int nwords = (njobs + 31) >> 5;
+            for (int jw = 0; jw < nwords; ++jw) {
+                unsigned mword = jmask[jw];
+                while (mword) {
+                    const int j = (jw << 5) + __ffs(mword) - 1;
+                    mword &= mword - 1;
+                    const int seg_a = job_a[j];
+                    const int seg_n = job_pre[j + 1] - job_pre[j];
+                    const int packed = job_pk[j];
+                    T xjs[D];
 #pragma unroll
                     for (int d = 0; d < D; ++d) {
-                        if constexpr (kFP32) dx[d] = pk.x(d) - xjs[d];
-                        else dx[d] = (pk.x(d) - xj[d]) + (xj[d] - xjs[d]);
-                        r2 = fma(dx[d], dx[d], r2);
+                        const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
+                        T box;
+                        if constexpr (kFP32) box = g.boxf[d];
+                        else box = g.box[d];
+                        xjs[d] = xj[d] - (c < 0 ? -box : (c >= g.nc[d] ? box : T(0)));
                     }
-                    bool flagged = false, exact = false;
-                    const int bin = valid ? decide_bin<D, T>(p, g, tab, s_edge, s_edge2, cc, packed, xj, pk, r2, &flagged,
-                                                             &exact)
-                                          : -1;
-                    ++nchunks;
-                    nflag += flagged ? 1u : 0u;
-                    nexact += exact ? 1u : 0u;
-                    // compact the accepted pairs into the batch: unit separation, weight, bin
-                    const bool take = bin >= 0;
-                    const unsigned tm = __ballot_sync(full, take);
-                    if (tm == 0u) continue;
-                    if (take) {
-                        const int slot = nbuf + __popc(tm & lt_mask);
-                        R e;
-                        T* f = reinterpret_cast<T*>(e.v);
-                        const T rinv = rsqrt_t(r2);
+                    ncand += seg_n;
+                    nchunks += (unsigned)((seg_n + 31) >> 5);
+                    // candidates in chunks of 32, two chunks per trip; each buffer is refilled two
+                    // chunks ahead right after it is consumed (the record array is padded, so the
+                    // loads past the cell's end are harmless and masked)
+                    const R* src = rec + seg_a;
+                    R buf0 = ldg_rec(src, lane);
+                    R buf1 = ldg_rec(src, 32 + lane);
+                    auto chunk = [&](const R& pk, int c0) {
+                        const bool valid = c0 + lane < seg_n;
+                        T dx[D];
+                        T r2 = T(0);
 #pragma unroll
-                        for (int d = 0; d < D; ++d) f[d] = dx[d] * rinv;
-                        f[D] = pk.w();
-                        recs[slot] = e;
-                        bins[slot] = (unsigned char)bin;
-                        ++npairs;
-                    }
-                    nbuf += __popc(tm);
-                    if (nbuf > kB - 32) {
-                        __syncwarp();
-                        pair_batch_flush<D, LMAX, T>(recs, bins, idx, acc_s, w2_s, hist, cursor, seg, nbuf,
-                                                     nbins, acc, nrounds);
-                        nbuf = 0;
-                        ++nbatch;
+                        for (int d = 0; d < D; ++d) {
+                            if constexpr (kFP32) dx[d] = pk.x(d) - xjs[d];
+                            else dx[d] = (pk.x(d) - xj[d]) + (xj[d] - xjs[d]);
+                            r2 = fma(dx[d], dx[d], r2);
+                        }
+                        int bin;
+                        if constexpr (kFP32) {
+                            // table lookup on the FP32 r^2 (floor; the guards at -1 and kTab catch r^2
+                            // outside the table), then the warp-uniform refinement of flagged buckets
+                            int kk = __float2int_rd(((float)r2 - p.tab_lo) * p.tab_inv);
+                            kk = max(-1, min(kk, kTab));
+                            const int code = valid ? (int)tab[kk + 1] : 63;
+                            bin = code & 63;
+                            const bool flg = (code & 64) != 0;
+                            if (__any_sync(full, flg)) {
+                                if (flg) {
+                                    bool ex = false;
+                                    const int b = bin_refine<D, T>(p, g, s_edge, s_edge2, cc, packed, xj, pk, r2,
+                                                                   code, &ex);
+                                    bin = b < 0 ? 63 : b;
+                                    ++nflag;
+                                    nexact += ex ? 1u : 0u;
+                                }
+                            }
+                        } else {
+                            bool flagged = false, exact = false;
+                            const int b = valid ? decide_bin<D, T>(p, g, tab, s_edge, s_edge2, cc, packed, xj, pk,
+                                                                   r2, &flagged, &exact)
+                                                : -1;
+                            bin = b < 0 ? 63 : b;
+                            nexact += exact ? 1u : 0u;
+                        }
+                        // compact the accepted pairs into the batch: unit separation, weight, bin
+                        const bool take = bin != 63;
+                        const unsigned tm = __ballot_sync(full, take);
+                        if (take) {
+                            const int slot = nbuf + __popc(tm & lt_mask);
+                            R e;
+                            T* f = reinterpret_cast<T*>(e.v);
+                            const T rinv = rsqrt_t(r2);
+#pragma unroll
+                            for (int d = 0; d < D; ++d) f[d] = dx[d] * rinv;
+                            f[D] = pk.w();
+                            recs[slot] = e;
+                            bins[slot] = (unsigned char)bin;
+                        }
+                        nbuf += __popc(tm);
+                        npairs_w += __popc(tm);
+                    };
+                    for (int c0 = 0;; c0 += 64) {
+                        if (nbuf > kB - 64) {  // room for the trip's two chunks
+                            __syncwarp();
+                            pair_batch_flush<D, LMAX, T>(recs, bins, idx, acc_s, w2_s, hist, cursor, seg, nbuf,
+                                                         nbins, acc, nrounds);
+                            nbuf = 0;
+                            ++nbatch;
+                        }
+                        chunk(buf0, c0);
+                        buf0 = ldg_rec(src, c0 + 64 + lane);
+                        if (c0 + 32 >= seg_n) break;
+                        chunk(buf1, c0 + 32);
+                        buf1 = ldg_rec(src, c0 + 96 + lane);
+                        if (c0 + 64 >= seg_n) break;
                     }
                 }
             }
@@ -534,26 +634,8 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                                              nrounds);
                 ++nbatch;
             }
-        }
-        // statistics
-        {
-            const unsigned tot = __reduce_add_sync(full, npairs);
-            nflag = __reduce_add_sync(full, nflag);
-            nexact = __reduce_add_sync(full, nexact);
-            if (lane == 0 && active) {
-                atomicAdd(&p.stats[0], (unsigned long long)tot);
-                atomicAdd(&p.stats[1], ncand);
-                atomicAdd(&p.stats[2], (unsigned long long)nrounds);
-                atomicAdd(&p.stats[3], (unsigned long long)tot);
-                atomicAdd(&p.stats[4], (unsigned long long)nchunks);
-                atomicAdd(&p.stats[5], (unsigned long long)nbatch);
-                atomicAdd(&p.stats[6], (unsigned long long)nflag);
-                atomicAdd(&p.stats[7], (unsigned long long)nexact);
-            }
-        }
-        // write a^b (normalised)
-        __syncwarp();
-        if (active) {
+            // write a^b (normalised)
+            __syncwarp();
             T* aout = static_cast<T*>(p.a_out) + (size_t)pidx * nbins * nq;
             for (int i = lane; i < nbins * nq; i += 32) {
                 const int b = i / nq, q = i - b * nq;
@@ -561,8 +643,21 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
             }
             if (lane == 0) static_cast<T*>(p.w_out)[pidx] = wj;
             if (p.self_out && lane < nbins) static_cast<T*>(p.self_out)[(size_t)pidx * nbins + lane] = w2_s[lane];
+            __syncwarp();
         }
-        __syncwarp();
+    }
+    // statistics (the candidate counts are warp-uniform; the flags are per lane)
+    nflag = __reduce_add_sync(full, nflag);
+    nexact = __reduce_add_sync(full, nexact);
+    if (lane == 0) {
+        atomicAdd(&p.stats[0], npairs_w);
+        atomicAdd(&p.stats[1], ncand);
+        atomicAdd(&p.stats[2], (unsigned long long)nrounds);
+        atomicAdd(&p.stats[3], npairs_w);
+        atomicAdd(&p.stats[4], (unsigned long long)nchunks);
+        atomicAdd(&p.stats[5], (unsigned long long)nbatch);
+        atomicAdd(&p.stats[6], (unsigned long long)nflag);
+        atomicAdd(&p.stats[7], (unsigned long long)nexact);
     }
 }
 

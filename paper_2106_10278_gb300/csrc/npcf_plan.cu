@@ -86,6 +86,61 @@ double sphere_area(int D) { return 2.0 * std::pow(M_PI, 0.5 * D) / std::tgamma(0
 
 }  // namespace
 
+// A batched in-place complex FFT of nf fields on a D-dimensional grid (row-major, fields
+// contiguous).  cuFFT plans cover ranks 1-3; D = 4 runs as a 3-D transform over the last three
+// axes (batched over the first axis and the fields) followed by a 1-D transform along the first
+// axis (stride = the 3-D block, batched over the block, once per field).
+struct GridFFT {
+    cufftHandle a = 0, b = 0;
+    int D = 0, nf = 0;
+    int64_t ncell = 0, block = 0;
+    void destroy()
+    {
+        if (a) cufftDestroy(a);
+        if (b) cufftDestroy(b);
+        a = b = 0;
+    }
+    cufftResult make(int D_, const int* dims, int nf_, bool fp64)
+    {
+        destroy();
+        D = D_;
+        nf = nf_;
+        const cufftType ty = fp64 ? CUFFT_Z2Z : CUFFT_C2C;
+        ncell = 1;
+        for (int i = 0; i < D; ++i) ncell *= dims[i];
+        int n[3];
+        if (D <= 3) {
+            for (int i = 0; i < D; ++i) n[i] = dims[i];
+            return cufftPlanMany(&a, D, n, nullptr, 1, (int)ncell, nullptr, 1, (int)ncell, ty, nf);
+        }
+        block = ncell / dims[0];
+        for (int i = 0; i < 3; ++i) n[i] = dims[i + 1];
+        cufftResult r = cufftPlanMany(&a, 3, n, nullptr, 1, (int)block, nullptr, 1, (int)block, ty, dims[0] * nf);
+        if (r != CUFFT_SUCCESS) return r;
+        int n0[1] = {dims[0]};
+        return cufftPlanMany(&b, 1, n0, n0, (int)block, 1, n0, (int)block, 1, ty, (int)block);
+    }
+    cufftResult stream(cudaStream_t s)
+    {
+        cufftResult r = cufftSetStream(a, s);
+        if (r == CUFFT_SUCCESS && b) r = cufftSetStream(b, s);
+        return r;
+    }
+    // data: nf fields of `ncell` complex values (complex<float> or complex<double>)
+    cufftResult exec(void* data, bool fp64, int dir) const
+    {
+        auto run = [&](cufftHandle h, void* d) {
+            return fp64 ? cufftExecZ2Z(h, (cufftDoubleComplex*)d, (cufftDoubleComplex*)d, dir)
+                        : cufftExecC2C(h, (cufftComplex*)d, (cufftComplex*)d, dir);
+        };
+        cufftResult r = run(a, data);
+        if (r != CUFFT_SUCCESS || !b) return r;
+        const size_t csz = fp64 ? 16 : 8;
+        for (int f = 0; f < nf && r == CUFFT_SUCCESS; ++f) r = run(b, static_cast<unsigned char*>(data) + csz * ncell * f);
+        return r;
+    }
+};
+
 struct npcf_plan_s {
     int D = 3, N = 3, lmax = 0, nbins = 0;
     npcf_opts opts{};
@@ -133,7 +188,7 @@ struct npcf_plan_s {
     DevBuf g_khat, g_xhat, g_work, g_cstate, g_small;
     int g_dims[4] = {0, 0, 0, 0};
     int g_nbs = 0;
-    cufftHandle g_fft_k = 0, g_fft_x = 0, g_fft_w = 0;  // kernels (batched), field, products (batched)
+    GridFFT g_fft_k, g_fft_x, g_fft_w;  // kernels (batched), field, products (batched)
     bool g_ready = false;
     DevBuf d_colmap;  // 2*nvis computed columns of the visible outputs (when a parity is selected)
     DevBuf d_selfc;   // remove_self (N=3): c_l / v_b^2 per (bin, l)
@@ -802,7 +857,7 @@ npcf_status setup_tables(npcf_plan_s* P)
     const double wb = (hi2 - lo2) / kTab;
     pp.tab_lo = (float)lo2;
     pp.tab_inv = (float)(1.0 / wb);
-    std::vector<unsigned char> tab(kTab);
+    std::vector<unsigned char> tab(kTabBytes, (unsigned char)63);  // guards and padding: no bin
     for (int k = 0; k < kTab; ++k) {
         // widen the bucket by the FP32 error of r^2 and of the bucket index itself
         const double a2 = lo2 + (k - 1) * wb, b2 = lo2 + (k + 2) * wb;
@@ -814,7 +869,7 @@ npcf_status setup_tables(npcf_plan_s* P)
         bool near = false;
         for (int e = 0; e <= nb; ++e)
             if (P->edges[e] >= ra && P->edges[e] <= rb) near = true;
-        tab[k] = (unsigned char)((b < 0 ? 63 : b) | (near ? 64 : 0));
+        tab[k + 1] = (unsigned char)((b < 0 ? 63 : b) | (near ? 64 : 0));
     }
     CUDA_TRY(upload(P->d_tab, tab));
     std::vector<double> qn = component_norms(D, P->lmax);
@@ -982,7 +1037,7 @@ npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int 
     npcf_status st;
     if ((st = R(P->w_cid, sizeof(int) * (n + 1))) != NPCF_OK) return st;
     if ((st = R(P->w_perm, sizeof(int) * (n + 1))) != NPCF_OK) return st;
-    if ((st = R(P->w_rec, (size_t)rb * (n + 1))) != NPCF_OK) return st;
+    if ((st = R(P->w_rec, (size_t)rb * (n + 1 + kRecPad))) != NPCF_OK) return st;
     // cells: count(nc+1) start(nc+1) fill(nc) lo prims pstart items istart (nc each) scan(8192)
     if ((st = R(P->w_cells, sizeof(int) * (8 * nc + 16 + 8192))) != NPCF_OK) return st;
     if ((st = R(P->w_items, sizeof(int4) * (n + nc + 1))) != NPCF_OK) return st;
@@ -1529,43 +1584,25 @@ npcf_status run_grid(npcf_plan_s* P, const void* X, const int* dims, double* coe
     const bool same = P->g_ready && std::equal(dims, dims + D, P->g_dims);
     if (!same) {
         P->g_ready = false;
-        for (cufftHandle* h : {&P->g_fft_k, &P->g_fft_x, &P->g_fft_w})
-            if (*h) {
-                cufftDestroy(*h);
-                *h = 0;
-            }
         P->g_nbs = (int)std::max<int64_t>(1, std::min<int64_t>(nbs_all, (int64_t(1) << 30) / (g.ncell * csz)));
         if (P->g_khat.reserve(csz * g.ncell * nbs_all) != cudaSuccess ||
             P->g_xhat.reserve(csz * g.ncell) != cudaSuccess ||
             P->g_work.reserve(csz * g.ncell * P->g_nbs) != cudaSuccess || P->g_small.reserve(16) != cudaSuccess)
             return fail(NPCF_ERR_WORKSPACE, "device allocation of the grid transforms failed");
         CUDA_TRY(upload(P->g_cstate, cs));
-        int n[4];
-        for (int a = 0; a < D; ++a) n[a] = dims[a];
-        const cufftType ty = P->fp64 ? CUFFT_Z2Z : CUFFT_C2C;
-        const int dist = (int)g.ncell;
-        if ((st = cufft_try(cufftPlanMany(&P->g_fft_k, D, n, nullptr, 1, dist, nullptr, 1, dist, ty, nbs_all),
-                            "kernel transform plan")) != NPCF_OK ||
-            (st = cufft_try(cufftPlanMany(&P->g_fft_x, D, n, nullptr, 1, dist, nullptr, 1, dist, ty, 1),
-                            "field transform plan")) != NPCF_OK ||
-            (st = cufft_try(cufftPlanMany(&P->g_fft_w, D, n, nullptr, 1, dist, nullptr, 1, dist, ty, P->g_nbs),
-                            "inverse transform plan")) != NPCF_OK)
+        if ((st = cufft_try(P->g_fft_k.make(D, dims, nbs_all, P->fp64), "kernel transform plan")) != NPCF_OK ||
+            (st = cufft_try(P->g_fft_x.make(D, dims, 1, P->fp64), "field transform plan")) != NPCF_OK ||
+            (st = cufft_try(P->g_fft_w.make(D, dims, P->g_nbs, P->fp64), "inverse transform plan")) != NPCF_OK)
             return st;
     }
     g.cstate = P->g_cstate.as<int2>();
     g.khat = P->g_khat.p;
     g.xhat = P->g_xhat.p;
     g.work = P->g_work.p;
-    for (cufftHandle h : {P->g_fft_k, P->g_fft_x, P->g_fft_w})
-        if ((st = cufft_try(cufftSetStream(h, s), "cufftSetStream")) != NPCF_OK) return st;
-    auto fwd = [&](cufftHandle h, void* data) {
-        return P->fp64 ? cufftExecZ2Z(h, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data, CUFFT_FORWARD)
-                       : cufftExecC2C(h, (cufftComplex*)data, (cufftComplex*)data, CUFFT_FORWARD);
-    };
-    auto inv = [&](cufftHandle h, void* data) {
-        return P->fp64 ? cufftExecZ2Z(h, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data, CUFFT_INVERSE)
-                       : cufftExecC2C(h, (cufftComplex*)data, (cufftComplex*)data, CUFFT_INVERSE);
-    };
+    for (GridFFT* h : {&P->g_fft_k, &P->g_fft_x, &P->g_fft_w})
+        if ((st = cufft_try(h->stream(s), "cufftSetStream")) != NPCF_OK) return st;
+    auto fwd = [&](const GridFFT& h, void* data) { return h.exec(data, P->fp64, CUFFT_FORWARD); };
+    auto inv = [&](const GridFFT& h, void* data) { return h.exec(data, P->fp64, CUFFT_INVERSE); };
     launch_counter() = 0;
     P->timed = 0;
     if (!same) {
@@ -1700,6 +1737,33 @@ npcf_status time_stages(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     return NPCF_OK;
 }
 
+// The coupling stage alone, again, on the a-array the last call left (nprim_max primaries, their
+// count on the device where the pair stage put it); its time in *ms.
+npcf_status time_coupling_only(npcf_plan_s* P, int64_t nprim_max, double* coeffs, cudaStream_t s, float* ms)
+{
+    const int chunk = 128;
+    const int rows = couple_rows(P, nprim_max, chunk);
+    if (P->w_partial.reserve(sizeof(double) * rows * 2 * P->ncoeff) != cudaSuccess)
+        return fail(NPCF_ERR_WORKSPACE, "device allocation of the partial rows failed");
+    const int npc = P->N == 5 ? d3n5f_chunk(P) : 0;
+    if (P->N == 5 && (P->w_x5.reserve(d3n5f_scratch_bytes(P, npc, 1)) != cudaSuccess))
+        return fail(NPCF_ERR_WORKSPACE, "device allocation of the 5PCF scratch failed");
+    int* small = P->w_small.as<int>();
+    CoupleParams kp = couple_params(P, P->w_a.p, P->w_wprim.p, small + S_NPRIM, chunk, P->w_partial.as<double>());
+    CUDA_TRY(cudaEventRecord(P->ev[2], s));
+    CUDA_TRY(cudaMemsetAsync(kp.partial, 0, sizeof(double) * rows * 2 * P->ncoeff, s));
+    npcf_status st = plan_coupling(P, kp, small + S_ERR, rows, nprim_max, P->w_x5.p,
+                                   P->w_x5.as<unsigned char>() + (size_t)P->d5_unit_x * npc * 2 * (P->fp64 ? 8 : 4),
+                                   npc, s);
+    if (st != NPCF_OK) return st;
+    CUDA_TRY(cudaEventRecord(P->ev[3], s));
+    CUDA_TRY(launch_reduce(kp.partial, rows, (int)(2 * P->ncoeff), plan_colmap(P), (int)(2 * P->nvis), 1.0 / P->V,
+                           coeffs, s));
+    CUDA_TRY(cudaEventSynchronize(P->ev[3]));
+    CUDA_TRY(cudaEventElapsedTime(ms, P->ev[2], P->ev[3]));
+    return NPCF_OK;
+}
+
 npcf_status autotune(npcf_plan_s* P, const void* pos, const void* w, int64_t n, cudaStream_t s)
 {
     npcf_status st;
@@ -1747,7 +1811,16 @@ npcf_status autotune(npcf_plan_s* P, const void* pos, const void* w, int64_t n, 
         best.pair_batch = b0;
     }
     set_pair_config(P, best.pair_warps, best.pair_batch);
-    // 2. the coupling's launch shape
+    // 2. the coupling's launch shape, timed alone on the a-array of a larger sample (a quarter of the
+    // primaries): its grid is sized by the primary count, so a small sample misjudges it
+    const int64_t pe2 = std::min<int64_t>(n, std::max<int64_t>(pe, n / 4));
+    {
+        float pm = 0.f, cm = 0.f;
+        if ((st = time_stages(P, pos, w, n, pe2, out, s, &pm, &cm)) != NPCF_OK) {
+            restore();
+            return st;
+        }
+    }
     float bestc = 1e30f;
     int cand[4];
     int which;
@@ -1769,9 +1842,9 @@ npcf_status autotune(npcf_plan_s* P, const void* pos, const void* w, int64_t n, 
         TuneShape t = best;
         t.coupling(which) = cand[ci];
         apply_shape(P, t);
-        float pm = 0.f, cm = 0.f;
+        float cm = 0.f;
         for (int rep = 0; rep < 2; ++rep)
-            if ((st = time_stages(P, pos, w, n, pe, out, s, &pm, &cm)) != NPCF_OK) {
+            if ((st = time_coupling_only(P, pe2, out, s, &cm)) != NPCF_OK) {
                 restore();
                 return st;
             }
@@ -2121,8 +2194,9 @@ void npcf_plan_destroy(npcf_plan_t P)
                       &P->w_x5,    &P->w_z5,
                       &P->d_colmap,  &P->d_selfc, &P->w_self, &P->d_los_lam, &P->d_los_terms, &P->d_los_coef,
                       &P->g_khat,  &P->g_xhat, &P->g_work, &P->g_cstate, &P->g_small};
-    for (cufftHandle h : {P->g_fft_k, P->g_fft_x, P->g_fft_w})
-        if (h) cufftDestroy(h);
+    P->g_fft_k.destroy();
+    P->g_fft_x.destroy();
+    P->g_fft_w.destroy();
     for (DevBuf* b : bufs) b->release();
     if (P->h_small) cudaFreeHost(P->h_small);
     for (auto& e : P->ev)
@@ -2209,7 +2283,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     int* stencil = static_cast<int*>(cv.take(sizeof(int) * g.stencil.size()));
     int* cid = static_cast<int*>(cv.take(sizeof(int) * (n + 1)));
     int* perm = static_cast<int*>(cv.take(sizeof(int) * (n + 1)));
-    void* rec = cv.take((size_t)rb * (n + 1));
+    void* rec = cv.take((size_t)rb * (n + 1 + kRecPad));
     int* cells = static_cast<int*>(cv.take(sizeof(int) * (8 * (size_t)nc + 16 + 8192)));
     int4* items = static_cast<int4*>(cv.take(sizeof(int4) * (n + nc + 1)));
     void* a = cv.take((size_t)tb * std::max<int64_t>(nprim_max, 1) * P->nbins * P->nq);
