@@ -8,7 +8,7 @@ uniform randoms with weight -1, periodic box of side 1000, 10 radial bins
 over [20, 160], lmax = 5 (13,320 complex coefficients).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload d3n4|d3n3_fp64|d2n3|d2n4|d4n3|d3n5|d4n3-grad|batch64] [--scale S]
+                    [--workload d3n4|d3n3_fp64|d2n3|d2n4|d4n3|d3n5|s2n4|d4n3-grad|batch64] [--scale S]
 
 Other workloads: d4n3-grad times one gradient step of the D=4 3PCF (forward,
 chi^2 upstream gradient, backward: npcf_backward); batch64 times the 64
@@ -98,6 +98,12 @@ def pair_flops_per_pair(D: int, lmax: int) -> int:
     return sep + direction + 6 * lmax + 5 * lmax * lmax + 2 * nq
 
 
+# the 2-sphere's pair beyond the D=2 one: a third separation component (3), the tangent vector
+# chord + (chord^2 / 2) n_j (1 + 3 FMA = 7) and its two frame components (2 x 3 FMA = 12), less the
+# D=2 direction's scalings it replaces (no change): 22
+SPHERE_EXTRA_FLOPS = 22
+
+
 # algorithmic FP32 operations per coupling term: N=3 a complex product and its accumulation, N=4 the
 # complex triple product (8, as counted for the 4PCF), N=5 one more complex multiplication
 COUPLING_FLOPS_PER_TERM = {3: 4, 4: 8, 5: 14}
@@ -145,8 +151,16 @@ def adjoint_flops_per_pair(D: int, lmax: int) -> int:
     return 3 * D + 2 + D + (2 * D + 1) * fwd + 6 * D
 
 
-def count_pairs_numpy(pos, edges, box, primaries):
-    """Ordered pairs (j, k != j, r in [e0, e_nb), minimum image) of the given primaries."""
+def count_pairs_numpy(pos, edges, box, primaries, geometry="box"):
+    """Ordered pairs (j, k != j, r in [e0, e_nb), minimum image) of the given primaries; on the
+    2-sphere, cos theta in [e0, e_nb) between the normalised directions."""
+    if geometry == "sphere":
+        u = pos / np.linalg.norm(pos, axis=1, keepdims=True)
+        tot = 0
+        for j in range(*primaries):
+            c = u @ u[j]
+            tot += int(np.count_nonzero((c >= edges[0]) & (c < edges[-1])))
+        return tot
     lo, hi = edges[0] ** 2, edges[-1] ** 2
     tot = 0
     for j in range(*primaries):
@@ -259,9 +273,21 @@ def _oracle_worker_block(prims):
 
     x = _ORACLE_INPUT
     t0 = time.perf_counter()
-    _, z = oracle.estimate(int(x["D"]), int(x["N"]), int(x["lmax"]), x["edges"], x["box"], x["pos"], x["w"],
-                           primaries=prims)
+    if str(x.get("geometry", "box")) == "sphere":
+        _, z = oracle.estimate_sphere(int(x["N"]), int(x["lmax"]), x["edges"], x["pos"], x["w"], primaries=prims)
+    else:
+        _, z = oracle.estimate(int(x["D"]), int(x["N"]), int(x["lmax"]), x["edges"], x["box"], x["pos"], x["w"],
+                               primaries=prims)
     return z, time.perf_counter() - t0
+
+
+def _oracle_estimate(wl, primaries):
+    """The oracle's estimate of a workload on a range of primaries (Euclidean or 2-sphere)."""
+    import oracle
+
+    if wl.geometry == "sphere":
+        return oracle.estimate_sphere(wl.N, wl.lmax, wl.edges, wl.pos, wl.w, primaries=primaries)
+    return oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=primaries)
 
 
 def _cpu_baseline(wl, target_s, gpu_range_fn=None):
@@ -275,13 +301,13 @@ def _cpu_baseline(wl, target_s, gpu_range_fn=None):
 
     oracle.build()
     t0 = time.perf_counter()
-    oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, 1))
+    _oracle_estimate(wl, (0, 1))
     t1 = time.perf_counter() - t0
     nprim = int(max(1, min(256, round(target_s / max(t1, 1e-3)))))
     t0 = time.perf_counter()
-    keys, ref = oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, nprim))
+    keys, ref = _oracle_estimate(wl, (0, nprim))
     dt = time.perf_counter() - t0
-    pairs = count_pairs_numpy(wl.pos, wl.edges, wl.box, (0, nprim))
+    pairs = count_pairs_numpy(wl.pos, wl.edges, wl.box, (0, nprim), wl.geometry)
     host = os.cpu_count() or 1
     out = {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "host_cores": host, "kind": "oracle",
            "sample": f"primaries [0,{nprim}) of the {wl.n}-particle workload, all secondaries, "
@@ -301,14 +327,15 @@ def _cpu_baseline(wl, target_s, gpu_range_fn=None):
             fd, path = tempfile.mkstemp(suffix=".npz")
             os.close(fd)
             try:
-                np.savez(path, D=wl.D, N=wl.N, lmax=wl.lmax, edges=wl.edges, box=wl.box, pos=wl.pos, w=wl.w)
+                np.savez(path, D=wl.D, N=wl.N, lmax=wl.lmax, edges=wl.edges, box=wl.box, pos=wl.pos, w=wl.w,
+                         geometry=wl.geometry)
                 ctx = mp.get_context("spawn")
                 with ctx.Pool(host, initializer=_oracle_worker_init, initargs=(path,)) as pool:
                     pool.map(_oracle_worker_block, [(i, i + 1) for i in range(host)])  # warm every worker
                     t0 = time.perf_counter()
                     res = pool.map(_oracle_worker_block, blocks)
                     wall = time.perf_counter() - t0
-                ppairs = sum(count_pairs_numpy(wl.pos, wl.edges, wl.box, b) for b in blocks)
+                ppairs = sum(count_pairs_numpy(wl.pos, wl.edges, wl.box, b, wl.geometry) for b in blocks)
                 out["all_cores"] = {"value": ppairs / wall, "unit": "pairs/s", "cores": host,
                                     "sample": f"{host} processes x {m} primaries ([{nprim},{blocks[-1][1]})), "
                                               f"{ppairs} pairs in {wall:.2f} s wall (the same oracle, one spawned "
@@ -422,14 +449,15 @@ def run_reference(args, rank, world):
     # in one spawned process per host core, each on its own block of primaries
     host = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, 1))
+    _oracle_estimate(wl, (0, 1))
     t1 = time.perf_counter() - t0
     per_proc = max(1, min(_reference_per_step(args, t1), wl.n // max(host, 1)))
     fd, path = tempfile.mkstemp(suffix=".npz")
     os.close(fd)
     total_pairs, total_t = 0, 0.0
     try:
-        np.savez(path, D=wl.D, N=wl.N, lmax=wl.lmax, edges=wl.edges, box=wl.box, pos=wl.pos, w=wl.w)
+        np.savez(path, D=wl.D, N=wl.N, lmax=wl.lmax, edges=wl.edges, box=wl.box, pos=wl.pos, w=wl.w,
+                         geometry=wl.geometry)
         with mp.get_context("spawn").Pool(host, initializer=_oracle_worker_init, initargs=(path,)) as pool:
             for k in range(args.warmup):
                 pool.map(_oracle_worker_block, [(i, i + 1) for i in range(host)])
@@ -440,7 +468,7 @@ def run_reference(args, rank, world):
                 t0 = time.perf_counter()
                 pool.map(_oracle_worker_block, blocks)
                 total_t += time.perf_counter() - t0
-                total_pairs += sum(count_pairs_numpy(wl.pos, wl.edges, wl.box, b) for b in blocks)
+                total_pairs += sum(count_pairs_numpy(wl.pos, wl.edges, wl.box, b, wl.geometry) for b in blocks)
     finally:
         os.unlink(path)
     v = total_pairs / total_t
@@ -468,11 +496,12 @@ def run_ours(args, rank, world):
         pbuild.build()
     if world > 1:
         torch.distributed.barrier()
-    base_seed = {"d3n4": 2, "d2n3": 1, "d2n4": 1, "d4n3": 4, "d3n3_fp64": 0, "d3n5": 5}[args.workload]
+    base_seed = {"d3n4": 2, "d2n3": 1, "d2n4": 1, "d4n3": 4, "d3n3_fp64": 0, "d3n5": 5, "s2n4": 6}[args.workload]
     wl = catalogs.workload(args.workload, seed=base_seed + 1000 * rank, scale=args.scale)
     prec = args.precision or ("fp64" if wl.precision == "fp64" else "fp32")
     tdt = torch.float64 if prec == "fp64" else torch.float32
-    plan = Plan(wl.D, wl.N, wl.lmax, wl.edges, wl.box, precision=prec, sync_check=False, timing=True)
+    plan = Plan(wl.D, wl.N, wl.lmax, wl.edges, wl.box, precision=prec, sync_check=False, timing=True,
+                geometry=wl.geometry)
     pos = torch.tensor(wl.pos, dtype=tdt, device=dev)
     w = torch.tensor(wl.w, dtype=tdt, device=dev)
     out = torch.empty(2 * plan.ncoeff, dtype=torch.float64, device=dev)
@@ -530,7 +559,7 @@ def run_ours(args, rank, world):
 
     # roofline of the dominant kernel: the pair kernel, or the coupling where it takes longer
     # (both FP32 ALU bound)
-    fpp = pair_flops_per_pair(wl.D, wl.lmax)
+    fpp = pair_flops_per_pair(wl.D, wl.lmax) + (SPHERE_EXTRA_FLOPS if wl.geometry == "sphere" else 0)
     pk_s = float(np.mean(pair_ms)) / 1e3
     ck_s = float(np.mean(couple_ms)) / 1e3
     sm_clock = 2070.0

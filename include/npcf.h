@@ -88,6 +88,17 @@ enum { NPCF_PARITY_ALL = 0, NPCF_PARITY_EVEN = 1, NPCF_PARITY_ODD = 2 };
  * Coefficients are complex; npcf_coeff_index returns 3 (N=3) or 5 (N=4) labels.  Not with
  * remove_self, a parity selection, the mixed precisions or npcf_backward. */
 enum { NPCF_BASIS_ISOTROPIC = 0, NPCF_BASIS_LOS = 1 };
+/* npcf_opts.geometry.  NPCF_GEOMETRY_BOX: Euclidean positions in a box (everything above).
+ * NPCF_GEOMETRY_SPHERE: points on the unit 2-sphere (Sec. "Cosmic Microwave Background"), with
+ * the D = 2 basis about every primary: the plan has D = 2 and N = 3 or 4; a position is a
+ * 3-vector (any nonzero length; the library normalises it); the radial coordinate is the
+ * great-circle angle theta between two points, binned on cos theta in half-open intervals
+ * [c_b, c_{b+1}) of bin_edges (-1 < c_0 < ... < c_nbins <= 1); the azimuth is that of the
+ * tangent vector n_k - (n_j . n_k) n_j in a right-handed frame (e1, e2, n_j); v_b = 2 pi
+ * (c_{b+1} - c_b) and 1/(4 pi) replaces 1/V_D.  box is ignored (may be NULL), periodic is
+ * ignored.  Not with remove_self, the line-of-sight basis, npcf_backward,
+ * npcf_compute_batched, npcf_compute_noalloc or npcf_compute_grid. */
+enum { NPCF_GEOMETRY_BOX = 0, NPCF_GEOMETRY_SPHERE = 1 };
 
 typedef struct {
     int precision;  /* NPCF_FP32 (positions/weights float, pair and coupling arithmetic FP32,
@@ -111,17 +122,20 @@ typedef struct {
                        keys the plan returns (npcf_num_coeffs / npcf_coeff_index count and
                        label only those) */
     int basis;      /* NPCF_BASIS_ISOTROPIC (default) or NPCF_BASIS_LOS (see above) */
+    int geometry;   /* NPCF_GEOMETRY_BOX (default) or NPCF_GEOMETRY_SPHERE (see above) */
 } npcf_opts;
 
 /* Default options: FP32, periodic, b1 <= b2, sync_check = 1, timing = 0, remove_self = 0,
- * parity = NPCF_PARITY_ALL, basis = NPCF_BASIS_ISOTROPIC. */
+ * parity = NPCF_PARITY_ALL, basis = NPCF_BASIS_ISOTROPIC, geometry = NPCF_GEOMETRY_BOX. */
 NPCF_API void npcf_default_opts(npcf_opts* opts);
 
 /*
  * Build a plan (host call; allocates the coupling tables on the current device).
  *   D, N, lmax : dimension (2..4), order (3, 4 or 5), maximum total angular momentum.
- *   bin_edges  : host, nbins+1 ascending edges, bin_edges[0] >= 0; r_max = bin_edges[nbins].
- *   box        : host, D side lengths (> 0).  Required in both modes (gives V_D).
+ *   bin_edges  : host, nbins+1 ascending edges, bin_edges[0] >= 0; r_max = bin_edges[nbins]
+ *                (NPCF_GEOMETRY_SPHERE: cos theta edges, -1 < bin_edges[0], bin_edges[nbins] <= 1).
+ *   box        : host, D side lengths (> 0).  Required in both periodic modes (gives V_D);
+ *                ignored (may be NULL) for NPCF_GEOMETRY_SPHERE.
  *   opts       : host, may be NULL for the defaults.
  * Errors: NPCF_ERR_ARG for bad sizes/edges/box, NPCF_ERR_UNSUPPORTED for
  * combinations outside the list above (or nbins > 32), NPCF_ERR_CUDA.
@@ -140,7 +154,8 @@ NPCF_API npcf_status npcf_coeff_index(npcf_plan_t plan, int64_t i, int* bins, in
 
 /*
  * Compute the coefficients.
- *   positions : device, n x D row-major, float (NPCF_FP32) or double (NPCF_FP64).
+ *   positions : device, n x D row-major (n x 3 for NPCF_GEOMETRY_SPHERE), float (NPCF_FP32) or
+ *               double (NPCF_FP64).
  *   weights   : device, n, same type.
  *   coeffs    : device, 2*ncoeff doubles (re, im), overwritten.
  *   [primary_begin, primary_end): the primaries summed over (indices into the

@@ -61,7 +61,9 @@
  *      annulus and 1/(4 pi) replaces 1/V; the azimuth is counter-clockwise
  *      seen from outside the sphere (the flat D = 2 orientation at the north
  *      pole); a^b_l uses Y*_l as in eq. NPCF-estimator-discrete (the section
- *      prints e^{+il phi}, which would conjugate every coefficient).
+ *      prints e^{+il phi}, which would conjugate every coefficient).  Two
+ *      points whose unit vectors coincide have no azimuth and are no pair, as
+ *      r = 0 is skipped in a box (R1).
  *   R18 the anisotropic basis: the line of sight is the fixed x_3 axis (as
  *      the paper sets it); N=3 labels (l1, l2, L) with every l1, l2 <= lmax
  *      and every L of the triangle rule, coupled as printed for the
@@ -605,6 +607,8 @@ static int geom_pair(const geom_t *g, const double *yk, const double *yj, double
         separation(g->Dp, yk, yj, g->box, g->periodic, d);
         return bin_of(norm2(g->Dp, d), g->nbins, g->edges);
     }
+    /* coinciding directions have no azimuth: skipped, as r = 0 is in a box (reading R1) */
+    if (yk[0] == yj[0] && yk[1] == yj[1] && yk[2] == yj[2]) return -1;
     double c = (yk[0] * yj[0] + yk[1] * yj[1]) + yk[2] * yj[2];
     if (c < g->edges[0]) return -1;
     int b = -1;

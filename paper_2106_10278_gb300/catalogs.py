@@ -164,6 +164,7 @@ class Workload:
     precision: str = "fp32"
     periodic: bool = True
     extra: dict = field(default_factory=dict)
+    geometry: str = "box"  # "sphere": pos are directions on S^2, edges in cos theta, box unused
 
     @property
     def n(self) -> int:
@@ -250,4 +251,11 @@ def workload(name: str, seed: int | None = None, scale: float = 1.0) -> Workload
         pos = np.concatenate([uniform(n_half, 4, 1.0, s), gaussian_blobs(n_half, 4, 1.0, nc, 0.01, s + 500)])
         w = normal_weights(2 * n_half, 1.0, 0.1, s + 900)
         return Workload(name, 4, 3, 4, linear_edges(0.01, 0.12, 8), np.full(4, 1.0), pos, w)
+    if name == "s2n4":
+        # the paper's 2-sphere 4PCF example (evenly distributed points, ten bins over cos theta in
+        # [-0.5, 0.5), lmax 4) at n = 100k
+        s = 6 if seed is None else seed
+        n = max(8, int(round(100_000 * scale)))
+        return Workload(name, 2, 4, 4, linear_edges(-0.5, 0.5, 10), np.ones(2), sphere_uniform(n, s), np.ones(n),
+                        periodic=False, geometry="sphere")
     raise KeyError(name)

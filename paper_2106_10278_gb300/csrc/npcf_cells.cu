@@ -53,6 +53,22 @@ __global__ void k_cell_ids(const CellParams p)
     atomicAdd(&p.cell_count[cell], 1);
 }
 
+// Points on the unit 2-sphere: each 3-vector normalised and shifted by +1 per axis, so that the
+// cell search runs in the cube [0, 2]^3 (a zero or non-finite vector gives NaN, which the cell
+// stage flags).
+template <typename T>
+__global__ void k_sphere_prep(const T* pos, int64_t n, T* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T x0 = pos[3 * i], x1 = pos[3 * i + 1], x2 = pos[3 * i + 2];
+    const T r2 = (x0 * x0 + x1 * x1) + x2 * x2;
+    const T ir = T(1) / sqrt(r2);
+    out[3 * i] = x0 * ir + T(1);
+    out[3 * i + 1] = x1 * ir + T(1);
+    out[3 * i + 2] = x2 * ir + T(1);
+}
+
 __global__ void k_cell_scatter(const CellParams p)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -256,6 +272,16 @@ cudaError_t launch_cell_ids(const CellParams& p, int fp64, cudaStream_t s)
     const int t = 256;
     if (fp64) k_cell_ids<double><<<blocks_for(p.n, t), t, 0, s>>>(p);
     else k_cell_ids<float><<<blocks_for(p.n, t), t, 0, s>>>(p); ++launch_counter();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sphere_prep(const void* pos, int64_t n, int fp64, void* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int t = 256;
+    if (fp64) k_sphere_prep<double><<<blocks_for(n, t), t, 0, s>>>(static_cast<const double*>(pos), n, static_cast<double*>(out));
+    else k_sphere_prep<float><<<blocks_for(n, t), t, 0, s>>>(static_cast<const float*>(pos), n, static_cast<float*>(out));
+    ++launch_counter();
     return cudaGetLastError();
 }
 

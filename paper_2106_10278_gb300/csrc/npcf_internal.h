@@ -76,6 +76,8 @@ struct PairParams {
     void* a_out;                 // nprim x nbins x nq (T)
     void* w_out;                 // nprim (T)
     void* self_out;              // nprim x nbins (T): sum of w_k^2 per bin, or NULL
+    const int* perm;             // sorted slot -> input index (the 2-sphere's exact path)
+    const void* orig;            // the caller's positions, n x 3 (the 2-sphere's exact path)
     unsigned long long* stats;   // [0] pairs, [1] candidates, [2] accumulation rounds, [3] busy lane-rounds, [4] chunks, [5] batches, [6] candidates in flagged buckets, [7] candidates decided in FP64
 };
 
@@ -193,6 +195,8 @@ inline int& launch_counter()
     return n;
 }
 cudaError_t launch_cell_ids(const CellParams& p, int fp64, cudaStream_t s);
+// the 2-sphere: positions normalised and shifted by +1 per axis into out (n x 3)
+cudaError_t launch_sphere_prep(const void* pos, int64_t n, int fp64, void* out, cudaStream_t s);
 cudaError_t launch_cell_scatter(const CellParams& p, int fp64, cudaStream_t s);
 cudaError_t launch_exclusive_scan(const int* in, int* out, int n, int* scratch, cudaStream_t s);
 struct ItemBuffers {

@@ -214,6 +214,49 @@ __device__ __forceinline__ int ceil_div_small(int a, int b)
     return q + ((q * b < a) ? 1 : 0);
 }
 
+// The 2-sphere (Sec. "Cosmic Microwave Background"): the bin of the pair (original input j, sorted
+// slot k) decided as the FP64 definition decides it -- both directions normalised from the
+// caller's coordinates (sqrt of the squares summed in axis order, then a division), cos theta
+// summed in axis order, half-open bins [c_b, c_{b+1}) held in edge2; identical directions have no
+// azimuth and are no pair (as r = 0 in a box).  Returns -1 outside.  For a pair in a bin it also
+// gives the tangent vector n_k - cos(theta) n_j in FP64, projected on the frame (e1, e2) -- the
+// direction of the pairs so close that the FP32 chord loses it.
+template <typename T>
+__device__ __forceinline__ void unit3_fp64(const T* x, double* u)
+{
+    const double x0 = (double)x[0], x1 = (double)x[1], x2 = (double)x[2];
+    const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x0, x0), __dmul_rn(x1, x1)), __dmul_rn(x2, x2)));
+    u[0] = __ddiv_rn(x0, r);
+    u[1] = __ddiv_rn(x1, r);
+    u[2] = __ddiv_rn(x2, r);
+}
+
+template <typename T>
+__device__ __forceinline__ int bin_refine_sph(const PairParams& p, int jorig, int kslot, const T* e1, const T* e2,
+                                              T* d0, T* d1)
+{
+    const T* o = static_cast<const T*>(p.orig);
+    double uk[3], uj[3];
+    unit3_fp64<T>(o + 3 * (size_t)p.perm[kslot], uk);
+    unit3_fp64<T>(o + 3 * (size_t)jorig, uj);
+    if (uk[0] == uj[0] && uk[1] == uj[1] && uk[2] == uj[2]) return -1;
+    const double c = __dadd_rn(__dadd_rn(__dmul_rn(uk[0], uj[0]), __dmul_rn(uk[1], uj[1])), __dmul_rn(uk[2], uj[2]));
+    if (!(c >= p.edge2[0])) return -1;
+    int b = -1;
+    for (int e = 0; e < p.nbins; ++e)
+        if (c < p.edge2[e + 1]) {
+            b = e;
+            break;
+        }
+    if (b >= 0) {
+        double t[3];
+        for (int a = 0; a < 3; ++a) t[a] = uk[a] - c * uj[a];
+        *d0 = (T)(t[0] * (double)e1[0] + t[1] * (double)e1[1] + t[2] * (double)e1[2]);
+        *d1 = (T)(t[0] * (double)e2[0] + t[1] * (double)e2[1] + t[2] * (double)e2[2]);
+    }
+    return b;
+}
+
 // Cell geometry of one stencil cell for one primary: the shifted primary
 // position (so that pk - xjs is the minimum-image separation) and whether the
 // cell can hold a pair in [e_0, e_nb) of that primary.
@@ -396,10 +439,16 @@ __device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned
     __syncwarp();
 }
 
-template <int D, int LMAX, typename T>
+// SPH: points on the unit 2-sphere, stored as n + 1 (a cube [0, 2] of 3-vectors for the cell
+// search); the separation is the chord, binned through the table on its square, and the
+// direction handed to the D = 2 harmonics is the tangent vector's azimuth in the primary's frame.
+template <int D, int LMAX, typename T, bool SPH = false>
 __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(const PairParams p)
 {
-    using R = Rec<D, T>;
+    static_assert(!SPH || D == 2, "the 2-sphere uses the D = 2 basis");
+    constexpr int DP = SPH ? 3 : D;  // components of a position
+    using R = Rec<D, T>;              // a staged pair
+    using RP = Rec<DP, T>;            // a sorted particle
     constexpr int NQ = PairCfg<D, LMAX, T>::NQ;
     constexpr bool kFP32 = sizeof(T) == 4;
     const int kB = p.batch;
@@ -438,7 +487,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     }
     const T* qnorm = static_cast<const T*>(p.qnorm);
     const T* inv_vb = static_cast<const T*>(p.inv_vb);
-    const R* rec = static_cast<const R*>(p.rec);
+    const RP* rec = static_cast<const RP*>(p.rec);
     const int nq = p.nq;
 
     // work counters of this warp, added to the statistics once at the end
@@ -458,9 +507,9 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         const CatGeom& g = *s_geo;
         const int nprim_item = it.z & 0xff;
 
-        int cc[D];
+        int cc[DP];
 #pragma unroll
-        for (int d = 0; d < D; ++d) cc[d] = ((it.x - g.base) / g.stride[d]) % g.nc[d];
+        for (int d = 0; d < DP; ++d) cc[d] = ((it.x - g.base) / g.stride[d]) % g.nc[d];
 
         // the item's neighbour cells: valid (periodic or inside the grid) and non-empty,
         // in stencil order, with the prefix of their record counts
@@ -473,7 +522,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                 int cell = g.base;
                 bool ok = true;
 #pragma unroll
-                for (int d = 0; d < D; ++d) {
+                for (int d = 0; d < DP; ++d) {
                     int c = cc[d] + (int)(signed char)((pk >> (8 * d)) & 0xff);
                     if (c < 0) {
                         ok = ok && p.periodic;
@@ -507,11 +556,37 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
         if (warp < nprim_item) {
             const int jslot = it.y + warp;
             const int pidx = it.w + warp;
-            const R pj = rec[jslot];
-            T xj[D];
+            const RP pj = rec[jslot];
+            T xj[DP];
 #pragma unroll
-            for (int d = 0; d < D; ++d) xj[d] = pj.x(d);
+            for (int d = 0; d < DP; ++d) xj[d] = pj.x(d);
             const T wj = pj.w();
+            // the sphere: the primary's direction and a right-handed tangent frame (e1, e2, n_j),
+            // e1 from the coordinate axis least aligned with n_j (any frame gives the same
+            // isotropic coefficients)
+            T uj[3], e1[3], e2[3];
+            int jorig = 0;
+            if constexpr (SPH) {
+                jorig = p.perm[jslot];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) uj[a] = xj[a] - T(1);
+                int a0 = 0;
+                if (fabs(uj[1]) < fabs(uj[a0])) a0 = 1;
+                if (fabs(uj[2]) < fabs(uj[a0])) a0 = 2;
+                const T c = uj[a0];
+                T nu = T(0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    e1[a] = (a == a0 ? T(1) : T(0)) - c * uj[a];
+                    nu = fma(e1[a], e1[a], nu);
+                }
+                const T inu = rsqrt_t(nu);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) e1[a] *= inu;
+                e2[0] = uj[1] * e1[2] - uj[2] * e1[1];
+                e2[1] = uj[2] * e1[0] - uj[0] * e1[2];
+                e2[2] = uj[0] * e1[1] - uj[1] * e1[0];
+            }
 
             T acc[NQ];
 #pragma unroll
@@ -522,8 +597,8 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
             // the cells this primary can reach, 32 at a time
             for (int j0 = 0; j0 < njobs; j0 += 32) {
                 const int j = j0 + lane;
-                T xjs[D];
-                const bool ok = j < njobs && cell_geometry<D, T>(p, g, cc, job_pk[j], xj, xjs);
+                T xjs[DP];
+                const bool ok = j < njobs && cell_geometry<DP, T>(p, g, cc, job_pk[j], xj, xjs);
                 const unsigned m = __ballot_sync(full, ok);
                 if (lane == 0) jmask[j0 >> 5] = m;
             }
@@ -540,9 +615,9 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                     const int seg_a = job_a[j];
                     const int seg_n = job_pre[j + 1] - job_pre[j];
                     const int packed = job_pk[j];
-                    T xjs[D];
+                    T xjs[DP];
 #pragma unroll
-                    for (int d = 0; d < D; ++d) {
+                    for (int d = 0; d < DP; ++d) {
                         const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
                         T box;
                         if constexpr (kFP32) box = g.boxf[d];
@@ -554,21 +629,40 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                     // candidates in chunks of 32, two chunks per trip; each buffer is refilled two
                     // chunks ahead right after it is consumed (the record array is padded, so the
                     // loads past the cell's end are harmless and masked)
-                    const R* src = rec + seg_a;
-                    R buf0 = ldg_rec(src, lane);
-                    R buf1 = ldg_rec(src, 32 + lane);
-                    auto chunk = [&](const R& pk, int c0) {
+                    const RP* src = rec + seg_a;
+                    RP buf0 = ldg_rec(src, lane);
+                    RP buf1 = ldg_rec(src, 32 + lane);
+                    auto chunk = [&](const RP& pk, int c0) {
                         const bool valid = c0 + lane < seg_n;
-                        T dx[D];
+                        T dx[DP];
                         T r2 = T(0);
 #pragma unroll
-                        for (int d = 0; d < D; ++d) {
+                        for (int d = 0; d < DP; ++d) {
                             if constexpr (kFP32) dx[d] = pk.x(d) - xjs[d];
                             else dx[d] = (pk.x(d) - xj[d]) + (xj[d] - xjs[d]);
                             r2 = fma(dx[d], dx[d], r2);
                         }
                         int bin;
-                        if constexpr (kFP32) {
+                        bool refined = false;  // the sphere: direction from the FP64 path
+                        T rd0 = T(0), rd1 = T(0);
+                        if constexpr (SPH) {
+                            // the table on the squared chord (2 - 2 cos theta); flagged buckets (FP32)
+                            // or every candidate inside the table (FP64 plans) decided in FP64
+                            int kk = __float2int_rd(((float)r2 - p.tab_lo) * p.tab_inv);
+                            kk = max(-1, min(kk, kTab));
+                            const int code = valid ? (int)tab[kk + 1] : 63;
+                            bin = code & 63;
+                            const bool flg = kFP32 ? (code & 64) != 0 : code != 63;
+                            if (__any_sync(full, flg)) {
+                                if (flg) {
+                                    const int b = bin_refine_sph<T>(p, jorig, seg_a + c0 + lane, e1, e2, &rd0, &rd1);
+                                    bin = b < 0 ? 63 : b;
+                                    refined = true;
+                                    ++nflag;
+                                    ++nexact;
+                                }
+                            }
+                        } else if constexpr (kFP32) {
                             // table lookup on the FP32 r^2 (floor; the guards at -1 and kTab catch r^2
                             // outside the table), then the warp-uniform refinement of flagged buckets
                             int kk = __float2int_rd(((float)r2 - p.tab_lo) * p.tab_inv);
@@ -601,9 +695,22 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                             const int slot = nbuf + __popc(tm & lt_mask);
                             R e;
                             T* f = reinterpret_cast<T*>(e.v);
-                            const T rinv = rsqrt_t(r2);
+                            if constexpr (SPH) {
+                                // tangent vector n_k - cos(theta) n_j = chord + (chord^2 / 2) n_j
+                                const T h = T(0.5) * r2;
+                                T t[3];
 #pragma unroll
-                            for (int d = 0; d < D; ++d) f[d] = dx[d] * rinv;
+                                for (int a = 0; a < 3; ++a) t[a] = fma(h, uj[a], dx[a]);
+                                const T d0 = refined ? rd0 : fma(t[0], e1[0], fma(t[1], e1[1], t[2] * e1[2]));
+                                const T d1 = refined ? rd1 : fma(t[0], e2[0], fma(t[1], e2[1], t[2] * e2[2]));
+                                const T rinv = rsqrt_t(fma(d0, d0, d1 * d1));
+                                f[0] = d0 * rinv;
+                                f[1] = d1 * rinv;
+                            } else {
+                                const T rinv = rsqrt_t(r2);
+#pragma unroll
+                                for (int d = 0; d < D; ++d) f[d] = dx[d] * rinv;
+                            }
                             f[D] = pk.w();
                             recs[slot] = e;
                             bins[slot] = (unsigned char)bin;
@@ -661,10 +768,10 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     }
 }
 
-template <int D, int LMAX, typename T>
+template <int D, int LMAX, typename T, bool SPH = false>
 cudaError_t launch_pairs_t(const PairParams& p, int grid, int smem, cudaStream_t s)
 {
-    auto kern = k_pairs<D, LMAX, T>;
+    auto kern = k_pairs<D, LMAX, T, SPH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, p.warps * 32, smem, s>>>(p); ++launch_counter();

@@ -32,6 +32,8 @@ int pair_threads_d4(int fp64, int L);
 cudaError_t launch_pairs_d2(const PairParams& p, int fp64, int L, int grid, int smem, cudaStream_t s);
 cudaError_t launch_pairs_d3(const PairParams& p, int fp64, int L, int grid, int smem, cudaStream_t s);
 cudaError_t launch_pairs_d4(const PairParams& p, int fp64, int L, int grid, int smem, cudaStream_t s);
+int pair_compiled_lmax_sph(int fp64, int lmax);
+cudaError_t launch_pairs_sph(const PairParams& p, int fp64, int L, int grid, int smem, cudaStream_t s);
 int couple_max_lmax_d3n4();
 }  // namespace npcf
 
@@ -149,6 +151,9 @@ struct npcf_plan_s {
     std::vector<double> edges;
     double box[4] = {1, 1, 1, 1};
     double V = 1.0;
+    int Dp = 3;         // components of a position (D; 3 on the 2-sphere)
+    int sphere = 0;     // NPCF_GEOMETRY_SPHERE
+    double rcut = 0.0;  // reach of the cell search (r_max; the largest chord on the sphere)
     // keys
     int nlam = 0;
     std::vector<int> lam;       // nlam x 3
@@ -195,6 +200,7 @@ struct npcf_plan_s {
     DevBuf w_self;    // remove_self (N=3): sum of w_k^2 per (primary, bin)
     // workspace
     DevBuf w_cid, w_perm, w_rec, w_cells, w_items, w_a, w_wprim, w_partial, w_small, w_hpos, w_hw, w_hout;
+    DevBuf w_upos;  // the 2-sphere: normalised, shifted positions
     // adjoint (npcf_backward)
     DevBuf d_keybase, w_cbuf, w_gpos, w_gw, w_gwp;
     // the single-catalogue grid (one CatGeom) and the last batched layout
@@ -448,7 +454,7 @@ GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
     // otherwise (very sparse inputs) the cheapest valid grid of any density.
     GridChoice best, any;
     double best_cost = 1e300, any_cost = 1e300;
-    const double rmax = P->edges[P->nbins];
+    const double rmax = P->rcut;
     const double reach = rmax * (1.0 + 1e-6) + 1e-12;
     for (int c = 1; c <= 4; ++c) {
         GridChoice g;
@@ -456,7 +462,7 @@ GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
         bool ok = true;
         double side[4];
         int64_t ncells = 1;
-        for (int d = 0; d < P->D; ++d) {
+        for (int d = 0; d < P->Dp; ++d) {
             int k = (int)std::floor(P->box[d] * c / rmax);
             if (k < 1) k = 1;
             if (P->opts.periodic && k < 2 * c + 1) ok = false;
@@ -468,7 +474,7 @@ GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
         if (!ok || ncells >= (1 << 24)) continue;
         g.ncells = (int)ncells;
         const double npc = (double)std::max<int64_t>(n, 1) / (double)ncells;
-        g.stencil = make_stencil(P->D, c, side, reach);
+        g.stencil = make_stencil(P->Dp, c, side, reach);
         if ((int)g.stencil.size() > kMaxJobs) continue;  // the pair kernel lists an item's cells in smem
         const double cost = g.stencil.size() * (npc + 24.0);
         if (cost < any_cost) {
@@ -817,7 +823,7 @@ npcf_status setup_tables(npcf_plan_s* P)
 {
     const int D = P->D, nb = P->nbins;
     // pair kernel
-    P->Lc = pair_compiled_lmax(D, P->fp64, P->lmax);
+    P->Lc = P->sphere ? pair_compiled_lmax_sph(P->fp64, P->lmax) : pair_compiled_lmax(D, P->fp64, P->lmax);
     if (P->Lc < 0) return fail(NPCF_ERR_UNSUPPORTED, "lmax=%d is not compiled for D=%d (%s)", P->lmax, D,
                                 P->fp64 ? "FP64" : "FP32");
     P->nq = num_q(D, P->lmax);
@@ -836,46 +842,78 @@ npcf_status setup_tables(npcf_plan_s* P)
     pp.periodic = P->opts.periodic;
     pp.warps = warps;
     pp.batch = P->batch;
-    double maxL = 0.0;
-    for (int d = 0; d < D; ++d) maxL = std::max(maxL, P->box[d]);
-    const double rmax = P->edges[nb], rmin = P->edges[0];
-    const double tol = 4.0 * (std::sqrt((double)D) * maxL * std::ldexp(1.0, -23) + rmax * std::ldexp(1.0, -21));
-    pp.tol = (float)tol;
-    pp.rmax2f = (float)((rmax + 2 * tol) * (rmax + 2 * tol));
-    const double rl = std::max(rmin - 2 * tol, 0.0);
-    pp.rmin2f = (float)(rl * rl);
-    for (int b = 0; b <= nb; ++b) {
-        pp.edgef[b] = (float)P->edges[b];
-        pp.edge2[b] = P->edges[b] * P->edges[b];
-    }
-    // radial table over r^2 (so the common path needs no square root): bucket k
-    // covers [lo2 + k*w, lo2 + (k+1)*w); the entry is the bin of the whole bucket
-    // (63 = outside the bins) and bit 64 marks buckets that an edge, widened by
-    // the FP32 error window, touches (those pairs are decided exactly in FP64)
-    const double lo2 = std::max(rmin - 2 * tol, 0.0) * std::max(rmin - 2 * tol, 0.0);
-    const double hi2 = (rmax + 2 * tol) * (rmax + 2 * tol);
-    const double wb = (hi2 - lo2) / kTab;
-    pp.tab_lo = (float)lo2;
-    pp.tab_inv = (float)(1.0 / wb);
     std::vector<unsigned char> tab(kTabBytes, (unsigned char)63);  // guards and padding: no bin
-    for (int k = 0; k < kTab; ++k) {
-        // widen the bucket by the FP32 error of r^2 and of the bucket index itself
-        const double a2 = lo2 + (k - 1) * wb, b2 = lo2 + (k + 2) * wb;
-        const double ra = std::sqrt(std::max(a2, 0.0)) - tol, rb = std::sqrt(b2) + tol;
-        const double rc = std::sqrt(lo2 + (k + 0.5) * wb);
-        int b = -1;
-        for (int e = 0; e < nb; ++e)
-            if (rc >= P->edges[e] && rc < P->edges[e + 1]) b = e;
-        bool near = false;
-        for (int e = 0; e <= nb; ++e)
-            if (P->edges[e] >= ra && P->edges[e] <= rb) near = true;
-        tab[k + 1] = (unsigned char)((b < 0 ? 63 : b) | (near ? 64 : 0));
+    if (!P->sphere) {
+        double maxL = 0.0;
+        for (int d = 0; d < D; ++d) maxL = std::max(maxL, P->box[d]);
+        const double rmax = P->edges[nb], rmin = P->edges[0];
+        const double tol = 4.0 * (std::sqrt((double)D) * maxL * std::ldexp(1.0, -23) + rmax * std::ldexp(1.0, -21));
+        pp.tol = (float)tol;
+        pp.rmax2f = (float)((rmax + 2 * tol) * (rmax + 2 * tol));
+        const double rl = std::max(rmin - 2 * tol, 0.0);
+        pp.rmin2f = (float)(rl * rl);
+        for (int b = 0; b <= nb; ++b) {
+            pp.edgef[b] = (float)P->edges[b];
+            pp.edge2[b] = P->edges[b] * P->edges[b];
+        }
+        // radial table over r^2 (so the common path needs no square root): bucket k
+        // covers [lo2 + k*w, lo2 + (k+1)*w); the entry is the bin of the whole bucket
+        // (63 = outside the bins) and bit 64 marks buckets that an edge, widened by
+        // the FP32 error window, touches (those pairs are decided exactly in FP64)
+        const double lo2 = std::max(rmin - 2 * tol, 0.0) * std::max(rmin - 2 * tol, 0.0);
+        const double hi2 = (rmax + 2 * tol) * (rmax + 2 * tol);
+        const double wb = (hi2 - lo2) / kTab;
+        pp.tab_lo = (float)lo2;
+        pp.tab_inv = (float)(1.0 / wb);
+        for (int k = 0; k < kTab; ++k) {
+            // widen the bucket by the FP32 error of r^2 and of the bucket index itself
+            const double a2 = lo2 + (k - 1) * wb, b2 = lo2 + (k + 2) * wb;
+            const double ra = std::sqrt(std::max(a2, 0.0)) - tol, rb = std::sqrt(b2) + tol;
+            const double rc = std::sqrt(lo2 + (k + 0.5) * wb);
+            int b = -1;
+            for (int e = 0; e < nb; ++e)
+                if (rc >= P->edges[e] && rc < P->edges[e + 1]) b = e;
+            bool near = false;
+            for (int e = 0; e <= nb; ++e)
+                if (P->edges[e] >= ra && P->edges[e] <= rb) near = true;
+            tab[k + 1] = (unsigned char)((b < 0 ? 63 : b) | (near ? 64 : 0));
+        }
+} else {
+        // the 2-sphere: the table runs over the squared chord s = 2 - 2 cos(theta) (decreasing in
+        // cos theta); an edge c_e sits at s_e = 2 - 2 c_e.  tol bounds the FP32 error of s from
+        // normalised, shifted coordinates; flagged buckets are decided in FP64 from the input.
+        const double tol = 1e-5;
+        const double slo = std::max(2.0 - 2.0 * P->edges[nb] - tol, 0.0), shi = 2.0 - 2.0 * P->edges[0] + tol;
+        pp.tol = (float)tol;
+        pp.rmax2f = (float)shi;
+        pp.rmin2f = (float)slo;
+        for (int b = 0; b <= nb; ++b) {
+            pp.edgef[b] = (float)P->edges[b];
+            pp.edge2[b] = P->edges[b];  // cos theta edges, FP64
+        }
+        const double wb = (shi - slo) / kTab;
+        pp.tab_lo = (float)slo;
+        pp.tab_inv = (float)(1.0 / wb);
+        for (int k = 0; k < kTab; ++k) {
+            const double sa = slo + (k - 1) * wb - tol, sb = slo + (k + 2) * wb + tol;
+            const double cc = 1.0 - 0.5 * (slo + (k + 0.5) * wb);
+            int b = -1;
+            for (int e = 0; e < nb; ++e)
+                if (cc >= P->edges[e] && cc < P->edges[e + 1]) b = e;
+            bool near = false;
+            for (int e = 0; e <= nb; ++e) {
+                const double se = 2.0 - 2.0 * P->edges[e];
+                if (se >= sa && se <= sb) near = true;
+            }
+            tab[k + 1] = (unsigned char)((b < 0 ? 63 : b) | (near ? 64 : 0));
+        }
     }
     CUDA_TRY(upload(P->d_tab, tab));
     std::vector<double> qn = component_norms(D, P->lmax);
     std::vector<double> ivb(nb);
     for (int b = 0; b < nb; ++b)
-        ivb[b] = 1.0 / (sphere_area(D) / D * (std::pow(P->edges[b + 1], D) - std::pow(P->edges[b], D)));
+        ivb[b] = P->sphere ? 1.0 / (2.0 * M_PI * (P->edges[b + 1] - P->edges[b]))  // annulus area on S^2
+                           : 1.0 / (sphere_area(D) / D * (std::pow(P->edges[b + 1], D) - std::pow(P->edges[b], D)));
     if (P->fp64) {
         CUDA_TRY(upload(P->d_qnorm, qn));
         CUDA_TRY(upload(P->d_invvb, ivb));
@@ -1020,14 +1058,14 @@ npcf_status prepare_grid(npcf_plan_s* P, int64_t n)
     P->ncells = g.ncells;
     P->nstencil = (int)g.stencil.size();
     CUDA_TRY(upload(P->d_stencil, g.stencil));
-    CUDA_TRY(upload(P->d_geo, std::vector<CatGeom>{make_geom(P->D, g.nc, P->box, 0, 0)}));
+    CUDA_TRY(upload(P->d_geo, std::vector<CatGeom>{make_geom(P->Dp, g.nc, P->box, 0, 0)}));
     P->grid_n = n;
     return NPCF_OK;
 }
 
 npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int rows, int ncells)
 {
-    const int rb = rec_bytes(P->D, P->fp64), tb = P->fp64 ? 8 : 4;
+    const int rb = rec_bytes(P->Dp, P->fp64), tb = P->fp64 ? 8 : 4;
     const size_t nc = (size_t)ncells;
     auto R = [&](DevBuf& b, size_t bytes) -> npcf_status {
         if (b.reserve(bytes) != cudaSuccess)
@@ -1048,6 +1086,7 @@ npcf_status reserve_workspace(npcf_plan_s* P, int64_t n, int64_t nprim_max, int 
         return st;
     if ((st = R(P->w_partial, sizeof(double) * rows * 2 * P->ncoeff)) != NPCF_OK) return st;
     if ((st = R(P->w_small, 128)) != NPCF_OK) return st;
+    if (P->sphere && (st = R(P->w_upos, (size_t)tb * 3 * (n + 1))) != NPCF_OK) return st;
     return NPCF_OK;
 }
 
@@ -1189,8 +1228,13 @@ npcf_status run_pairs(npcf_plan_s* P, const GridView& gv, const void* pos, const
     CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(int) * (3 * (size_t)nc + 2), s));
     CUDA_TRY(cudaMemsetAsync(small, 0, 128, s));
 
+    const void* orig = pos;
+    if (P->sphere) {  // the cell search runs on the normalised directions, shifted into [0, 2]^3
+        CUDA_TRY(launch_sphere_prep(pos, n, P->fp64, P->w_upos.p, s));
+        pos = P->w_upos.p;
+    }
     CellParams cp{};
-    cp.D = P->D;
+    cp.D = P->Dp;
     cp.n = n;
     cp.ncells = nc;
     cp.ncat = gv.ncat;
@@ -1225,9 +1269,12 @@ npcf_status run_pairs(npcf_plan_s* P, const GridView& gv, const void* pos, const
     pp.w_out = P->w_wprim.p;
     pp.self_out = (P->opts.remove_self && P->N == 3) ? P->w_self.p : nullptr;
     pp.stats = stats;
+    pp.perm = P->w_perm.as<int>();
+    pp.orig = orig;
     const int grid = P->nsm;
     cudaError_t e;
-    if (P->D == 2) e = launch_pairs_d2(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
+    if (P->sphere) e = launch_pairs_sph(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
+    else if (P->D == 2) e = launch_pairs_d2(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
     else if (P->D == 3) e = launch_pairs_d3(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
     else e = launch_pairs_d4(pp, P->fp64, P->Lc, grid, P->pair_smem, s);
     if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "pair kernel launch: %s", cudaGetErrorString(e));
@@ -1876,6 +1923,7 @@ void npcf_default_opts(npcf_opts* o)
     o->remove_self = 0;
     o->parity = NPCF_PARITY_ALL;
     o->basis = NPCF_BASIS_ISOTROPIC;
+    o->geometry = NPCF_GEOMETRY_BOX;
 }
 
 npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const double* edges, int nbins,
@@ -1894,14 +1942,28 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
         return fail(NPCF_ERR_UNSUPPORTED, "N=4, D=3 supports lmax <= %d", couple_max_lmax_d3n4());
     if (nbins < 1 || nbins > kMaxBins) return fail(NPCF_ERR_UNSUPPORTED, "nbins must be in [1, %d]", kMaxBins);
     if (N == 4 && nbins < 3) return fail(NPCF_ERR_ARG, "N=4 needs at least 3 bins");
-    if (!edges || !box) return fail(NPCF_ERR_ARG, "bin_edges and box are required");
-    if (!(edges[0] >= 0.0) || !std::isfinite(edges[0])) return fail(NPCF_ERR_ARG, "bin_edges[0] must be >= 0");
-    for (int b = 0; b < nbins; ++b)
-        if (!(edges[b + 1] > edges[b]) || !std::isfinite(edges[b + 1]))
-            return fail(NPCF_ERR_ARG, "bin_edges must be finite and strictly increasing");
     npcf_opts o;
     npcf_default_opts(&o);
     if (opts) o = *opts;
+    if (o.geometry != NPCF_GEOMETRY_BOX && o.geometry != NPCF_GEOMETRY_SPHERE) return fail(NPCF_ERR_ARG, "bad geometry");
+    const bool sph = o.geometry == NPCF_GEOMETRY_SPHERE;
+    if (!edges || (!box && !sph)) return fail(NPCF_ERR_ARG, "bin_edges and box are required");
+    if (sph) {
+        if (D != 2 || N > 4)
+            return fail(NPCF_ERR_UNSUPPORTED, "the 2-sphere takes D=2 (its basis) and N=3 or 4");
+        if (!(edges[0] > -1.0) || !(edges[nbins] <= 1.0))
+            return fail(NPCF_ERR_ARG, "cos(theta) edges must lie in (-1, 1]");
+        if (o.remove_self || o.basis != NPCF_BASIS_ISOTROPIC)
+            return fail(NPCF_ERR_UNSUPPORTED, "the 2-sphere is provided without remove_self and with the isotropic basis");
+        if (pair_compiled_lmax_sph(o.precision == NPCF_FP64, lmax) < 0)
+            return fail(NPCF_ERR_UNSUPPORTED, "lmax=%d is not compiled for the 2-sphere", lmax);
+        o.periodic = 0;
+    } else if (!(edges[0] >= 0.0) || !std::isfinite(edges[0])) {
+        return fail(NPCF_ERR_ARG, "bin_edges[0] must be >= 0");
+    }
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b + 1] > edges[b]) || !std::isfinite(edges[b + 1]))
+            return fail(NPCF_ERR_ARG, "bin_edges must be finite and strictly increasing");
     if (o.precision != NPCF_FP32 && o.precision != NPCF_FP64 && o.precision != NPCF_MIXED_BF16X3 &&
         o.precision != NPCF_MIXED_TF32X3)
         return fail(NPCF_ERR_ARG, "bad precision");
@@ -1921,7 +1983,7 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
                     "the line-of-sight basis is provided for D=3, N=3 or 4, without remove_self, parity or mixed precision");
     if (o.parity == NPCF_PARITY_ODD && !(N == 4 && D == 3))
         return fail(NPCF_ERR_UNSUPPORTED, "this plan has no odd-parity components (only the D=3 4PCF has them)");
-    for (int d = 0; d < D; ++d) {
+    for (int d = 0; d < D && !sph; ++d) {
         if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(NPCF_ERR_ARG, "box sides must be > 0");
         if (o.periodic && !(edges[nbins] < 0.5 * box[d]))
             return fail(NPCF_ERR_ARG, "periodic boxes need r_max < box/2 (axis %d)", d);
@@ -1937,9 +1999,20 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
     P->mixed = o.precision == NPCF_MIXED_BF16X3 ? 1 : (o.precision == NPCF_MIXED_TF32X3 ? 2 : 0);
     P->edges.assign(edges, edges + nbins + 1);
     P->V = 1.0;
-    for (int d = 0; d < D; ++d) {
-        P->box[d] = box[d];
-        P->V *= box[d];
+    if (sph) {
+        // directions n + 1 fill the cube [0, 2]^3; the cell search reaches the largest chord
+        P->sphere = 1;
+        P->Dp = 3;
+        for (int d = 0; d < 3; ++d) P->box[d] = 2.0 + std::ldexp(1.0, -20);
+        P->V = 4.0 * M_PI;
+        P->rcut = std::sqrt(2.0 - 2.0 * edges[0] + 2e-5);  // covers the table's widened range
+    } else {
+        P->Dp = D;
+        P->rcut = edges[nbins];
+        for (int d = 0; d < D; ++d) {
+            P->box[d] = box[d];
+            P->V *= box[d];
+        }
     }
     build_keys(P);
     npcf_status st = ensure_device(P);
@@ -2003,13 +2076,13 @@ npcf_status npcf_compute_host(npcf_plan_t P, const void* pos, const void* w, int
     npcf_status st = ensure_device(P);
     if (st != NPCF_OK) return st;
     const size_t tb = P->fp64 ? 8 : 4;
-    if (P->w_hpos.reserve(tb * P->D * std::max<int64_t>(n, 1)) != cudaSuccess ||
+    if (P->w_hpos.reserve(tb * P->Dp * std::max<int64_t>(n, 1)) != cudaSuccess ||
         P->w_hw.reserve(tb * std::max<int64_t>(n, 1)) != cudaSuccess ||
         P->w_hout.reserve(sizeof(double) * 2 * P->nvis + 16) != cudaSuccess)
         return fail(NPCF_ERR_WORKSPACE, "device staging allocation failed");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n > 0) {
-        CUDA_TRY(cudaMemcpyAsync(P->w_hpos.p, pos, tb * P->D * n, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(P->w_hpos.p, pos, tb * P->Dp * n, cudaMemcpyHostToDevice, s));
         CUDA_TRY(cudaMemcpyAsync(P->w_hw.p, w, tb * n, cudaMemcpyHostToDevice, s));
     }
     st = run(P, P->w_hpos.p, P->w_hw.p, n, P->w_hout.as<double>(), pb, pe, s);
@@ -2063,6 +2136,7 @@ npcf_status npcf_compute_batched(npcf_plan_t P, const void* pos, const void* w, 
                                  const double* boxes, int ncat, double* coeffs, npcf_stream_t stream)
 {
     if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (P->sphere) return fail(NPCF_ERR_UNSUPPORTED, "%s is not provided for the 2-sphere", "npcf_compute_batched");
     if (ncat < 1 || ncat > (1 << 20)) return fail(NPCF_ERR_ARG, "ncat=%d out of range", ncat);
     if (!offsets || !boxes || !coeffs) return fail(NPCF_ERR_ARG, "offsets/boxes/coeffs is NULL");
     if (offsets[0] != 0) return fail(NPCF_ERR_ARG, "offsets[0] must be 0");
@@ -2087,6 +2161,7 @@ npcf_status npcf_backward(npcf_plan_t P, const void* pos, const void* w, int64_t
                           int64_t pb, int64_t pe, void* grad_pos, void* grad_w, npcf_stream_t stream)
 {
     if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (P->sphere) return fail(NPCF_ERR_UNSUPPORTED, "%s is not provided for the 2-sphere", "npcf_backward");
     if (P->N != 3) return fail(NPCF_ERR_UNSUPPORTED, "the adjoint is implemented for N=3 plans");
     if (P->opts.remove_self)
         return fail(NPCF_ERR_UNSUPPORTED, "the adjoint of the remove_self subtraction is not provided");
@@ -2133,6 +2208,7 @@ npcf_status npcf_selftest_tc(int tf32, int n, int k, const float* a, const float
 npcf_status npcf_compute_grid(npcf_plan_t P, const void* field, const int* dims, double* coeffs, npcf_stream_t stream)
 {
     if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (P->sphere) return fail(NPCF_ERR_UNSUPPORTED, "%s is not provided for the 2-sphere", "npcf_compute_grid");
     if (!field || !dims || !coeffs) return fail(NPCF_ERR_ARG, "field/dims/coeffs is NULL");
     if (!P->opts.periodic) return fail(NPCF_ERR_UNSUPPORTED, "the gridded estimator needs a periodic plan");
     if (P->opts.basis != NPCF_BASIS_ISOTROPIC || P->mixed || P->opts.remove_self)
@@ -2185,7 +2261,7 @@ void npcf_plan_destroy(npcf_plan_t P)
     DevBuf* bufs[] = {&P->d_task,  &P->d_tab,   &P->d_qnorm, &P->d_invvb, &P->d_pairs, &P->d_pair_key, &P->d_kblocks,
                       &P->d_lam2,  &P->d_lamodd, &P->d_pref, &P->d_stencil, &P->w_cid,    &P->w_perm,
                       &P->w_rec,   &P->w_cells, &P->w_items, &P->w_a,     &P->w_wprim,   &P->w_partial,
-                      &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout,  &P->d_keybase, &P->w_cbuf,
+                      &P->w_small, &P->w_hpos,  &P->w_hw,    &P->w_hout,  &P->d_keybase, &P->w_cbuf, &P->w_upos,
                       &P->w_gpos,  &P->w_gw,    &P->w_gwp,   &P->d_geo,   &P->b_geo,     &P->b_cells,
                       &P->b_offsets, &P->b_first, &P->b_count, &P->b_scales, &P->b_stencil,
                       &P->d5_p12,  &P->d5_p34, &P->d5_gx,  &P->d5_gz, &P->d5_terms, &P->d5_coef, &P->d5_nlx,
@@ -2400,6 +2476,7 @@ extern "C" npcf_status npcf_compute_noalloc(npcf_plan_t P, const void* pos, cons
                                             double* coeffs, int64_t pb, int64_t pe, npcf_stream_t stream)
 {
     if (!P) return fail(NPCF_ERR_ARG, "plan is NULL");
+    if (P->sphere) return fail(NPCF_ERR_UNSUPPORTED, "%s is not provided for the 2-sphere", "npcf_compute_noalloc");
     if (n < 0 || n > (int64_t)0x7fffff00) return fail(NPCF_ERR_ARG, "n=%lld out of range", (long long)n);
     if (!coeffs) return fail(NPCF_ERR_ARG, "coeffs is NULL");
     if (n > 0 && (!pos || !w)) return fail(NPCF_ERR_ARG, "positions/weights are NULL");

@@ -23,6 +23,7 @@ PRECISIONS = {"fp64": NPCF_FP64, "fp32": NPCF_FP32, "mixed_bf16x3": NPCF_MIXED_B
 NPCF_BINS_LE, NPCF_BINS_LT = 0, 1
 PARITIES = {"all": 0, "even": 1, "odd": 2}
 BASES = {"isotropic": 0, "los": 1}
+GEOMETRIES = {"box": 0, "sphere": 1}
 STATUS = {0: "NPCF_OK", -1: "NPCF_ERR_ARG", -2: "NPCF_ERR_UNSUPPORTED", -3: "NPCF_ERR_CUDA",
           -4: "NPCF_ERR_WORKSPACE", -5: "NPCF_ERR_DEVICE_TIMEOUT", -6: "NPCF_ERR_NONFINITE"}
 
@@ -42,7 +43,7 @@ class NpcfError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("periodic", ctypes.c_int), ("bin_order", ctypes.c_int),
                 ("sync_check", ctypes.c_int), ("timing", ctypes.c_int), ("remove_self", ctypes.c_int),
-                ("parity", ctypes.c_int), ("basis", ctypes.c_int)]
+                ("parity", ctypes.c_int), ("basis", ctypes.c_int), ("geometry", ctypes.c_int)]
 
 
 _lib = None
@@ -138,6 +139,8 @@ class Plan:
     parity: "all", "even" or "odd" components (odd ones exist for the D=3 4PCF only).
     basis: "isotropic" or "los" (D=3, N=3 or 4: the basis about the x_3 line of sight, labels
     (l1, l2, L) or (l1, l2, l12, l3, L)).
+    geometry: "box" (Euclidean) or "sphere" (points on the unit 2-sphere: D=2, N=3 or 4, positions
+    (n, 3) directions, edges in cos theta, box ignored -- pass None).
     precision: "fp32" (positions/weights float32; FP32 pair and coupling
     arithmetic, FP64 sums over primaries), "fp64" (double throughout), or
     "mixed_bf16x3" / "mixed_tf32x3" (float32 inputs and pair stage; the coupling
@@ -146,12 +149,18 @@ class Plan:
     """
 
     def __init__(self, D, N, lmax, edges, box, *, precision="fp32", periodic=True, bin_lt=False, sync_check=True,
-                 timing=False, remove_self=False, parity="all", basis="isotropic"):
+                 timing=False, remove_self=False, parity="all", basis="isotropic", geometry="box"):
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}, not {precision!r}")
         lib = load_library()
         self.D, self.N, self.lmax = int(D), int(N), int(lmax)
         self.edges = np.ascontiguousarray(edges, dtype=np.float64)
+        if geometry not in GEOMETRIES:
+            raise ValueError(f"geometry must be one of {sorted(GEOMETRIES)}, not {geometry!r}")
+        self.geometry = geometry
+        self.Dp = 3 if geometry == "sphere" else self.D  # components of a position
+        if box is None and geometry == "sphere":
+            box = 1.0
         self.box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (self.D,)))
         self.nbins = len(self.edges) - 1
         self.precision = precision
@@ -170,6 +179,7 @@ class Plan:
             raise ValueError(f"basis must be one of {sorted(BASES)}, not {basis!r}")
         o.basis = BASES[basis]
         self.basis = basis
+        o.geometry = GEOMETRIES[geometry]
         h = ctypes.c_void_p()
         _check(lib.npcf_plan_create(ctypes.byref(h), self.D, self.N, self.lmax,
                                     self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.nbins,
@@ -212,7 +222,7 @@ class Plan:
         return torch.float64 if self.precision == "fp64" else torch.float32
 
     def compute(self, pos, w, primaries=None, out=None, stream=None):
-        """Coefficients on the device for device tensors pos (n, D) and w (n).
+        """Coefficients on the device for device tensors pos (n, D) (n, 3 on the sphere) and w (n).
 
         Returns a complex128 tensor of ncoeff entries (a view of `out`, a float64
         tensor of 2*ncoeff, allocated if not given)."""
@@ -223,7 +233,7 @@ class Plan:
             raise ValueError("pos and w must be CUDA tensors (use compute_host for host arrays)")
         if pos.dtype != dt or w.dtype != dt:
             raise TypeError(f"pos and w must be {dt} for a {self.precision} plan")
-        if pos.dim() != 2 or pos.shape[1] != self.D or w.shape != (pos.shape[0],):
+        if pos.dim() != 2 or pos.shape[1] != self.Dp or w.shape != (pos.shape[0],):
             raise ValueError("pos must be (n, D) and w (n,)")
         pos = pos.contiguous()
         w = w.contiguous()
@@ -253,7 +263,7 @@ class Plan:
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         ncat = len(off) - 1
         bx = np.ascontiguousarray(np.broadcast_to(np.asarray(boxes, dtype=np.float64), (ncat, self.D)))
-        if pos.dim() != 2 or pos.shape[1] != self.D or w.shape != (pos.shape[0],) or off[-1] != pos.shape[0]:
+        if pos.dim() != 2 or pos.shape[1] != self.Dp or w.shape != (pos.shape[0],) or off[-1] != pos.shape[0]:
             raise ValueError("pos must be (n, D), w (n,) and offsets[-1] == n")
         pos = pos.contiguous()
         w = w.contiguous()
@@ -301,7 +311,7 @@ class Plan:
             raise ValueError("pos, w and grad_coeffs must be CUDA tensors")
         if pos.dtype != dt or w.dtype != dt:
             raise TypeError(f"pos and w must be {dt} for a {self.precision} plan")
-        if pos.dim() != 2 or pos.shape[1] != self.D or w.shape != (pos.shape[0],):
+        if pos.dim() != 2 or pos.shape[1] != self.Dp or w.shape != (pos.shape[0],):
             raise ValueError("pos must be (n, D) and w (n,)")
         g = torch.view_as_real(grad_coeffs).reshape(-1) if grad_coeffs.is_complex() else grad_coeffs.reshape(-1)
         g = g.to(torch.float64).contiguous()

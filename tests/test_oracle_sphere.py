@@ -113,6 +113,34 @@ def test_sphere_l0_weighted_pair_counts():
         assert abs(v - ref) <= 1e-12 * max(1.0, abs(ref))
 
 
+def test_sphere_coinciding_directions_are_skipped():
+    """Duplicated directions (and a rescaled copy, the same direction) are no pair -- they have no
+    azimuth, as r = 0 has no direction in a box -- while every other pair up to cos theta = 1
+    counts: the l = 0 weighted pair counts from dot products, with identical unit vectors left
+    out, give zeta_0 again."""
+    pos, w = _cat(60, 21)
+    pos = np.concatenate([pos, pos[:10], 3.0 * pos[10:15]])
+    w = catalogs.normal_weights(len(pos), 1.0, 0.3, 22)
+    ce = np.array([-0.3, 0.2, 0.7, 1.0])
+    keys, z = oracle.estimate_sphere(3, 2, ce, pos, w)
+    assert np.all(np.isfinite(z))
+    u = pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    vb = 2 * np.pi * np.diff(ce)
+    W = np.zeros((len(pos), 3))
+    for j in range(len(pos)):
+        c = u @ u[j]
+        b = np.searchsorted(ce, c, side="right") - 1
+        same = np.all(np.isclose(u, u[j], rtol=0, atol=1e-15), axis=1)
+        ok = ~same & (b >= 0) & (b < 3)
+        for bb in range(3):
+            W[j, bb] = np.sum(w[ok & (b == bb)])
+    for k, v in zip(keys, z):
+        if k[3] != 0:
+            continue
+        ref = np.sum(w * W[:, k[0]] * W[:, k[1]]) / (4 * np.pi * 2 * np.pi * vb[k[0]] * vb[k[1]])
+        assert abs(v - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
 def test_sphere_4pcf_paper_example_component_counts():
     """The paper's 2-sphere example: 4PCF, ten bins over cos(theta) in [-0.5, 0.5), lmax = 4 ->
     35 angular and 120 radial components."""
