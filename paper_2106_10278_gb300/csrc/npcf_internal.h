@@ -65,6 +65,8 @@ struct PairParams {
     int batch;                   // pairs per warp batch (multiple of 32, <= 1024)
     int nstencil;
     const int* stencil;          // packed offsets, 8 bits per axis (signed)
+    int nrows;
+    const int2* rows;            // stencil rows: (offsets of axes 1..3, 8 bits each; x range lo | hi << 8)
     const unsigned char* tab;    // kTabBytes entries: [0] and [kTab + 1] "no bin", bucket k at [k + 1]
     const void* rec;             // sorted records
     const int* cell_start;

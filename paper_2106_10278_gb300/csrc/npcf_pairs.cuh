@@ -5,12 +5,13 @@
 //
 // Design (GB300, sm_103a):
 //  * One CTA takes one work item = up to W primaries of one cell; warp w owns
-//    primary w.  The CTA lists the item's neighbour cells (the stencil cells
-//    within r_max of the primary cell that are non-empty) in shared memory
-//    once; every warp then marks, 32 cells at a time, the cells its primary
-//    can reach (a bit mask), walks the marked cells on its own and streams
-//    their candidates from global memory (L1/L2 resident) with a two-deep
-//    register prefetch -- no block barriers while scanning.
+//    primary w.  The stencil is walked by rows: the cells that differ only in
+//    their axis-0 offset are consecutive in the sorted records, so each row is
+//    one run of candidates.  The CTA tabulates the item's rows once; every
+//    warp trims each row to the cells its primary can reach (the x range that
+//    the row's distance across the other axes leaves within r_max, split where
+//    it wraps) and streams the run from global memory (L1/L2 resident) with a
+//    two-chunk register prefetch -- no block barriers while scanning.
 //  * Accepted pairs (unit separation, weight, bin) are compacted into a
 //    per-warp batch in shared memory.  A full batch is counting-sorted by bin
 //    (arrival order kept inside a bin), the 32 lanes are shared out among the
@@ -50,7 +51,7 @@ __host__ __device__ constexpr int pair_batch(int rec_bytes) { return rec_bytes <
 // Shared-memory carve-up of one CTA (host and device must agree):
 //   radial table + edges | job lists + scan scratch | the item's CatGeom
 //   | per warp: [records (also the merge scratch) | acc[nbins][nq] | bins u8 | idx u16 | 4 x 32 ints
-//                | sum of w^2 per bin (32) | reachable-cell mask (kMaxJobs bits)]
+//                | sum of w^2 per bin (32)]
 __host__ __device__ inline int pair_rec_region(int rec_bytes, int t_bytes, int nq_compiled, int B)
 {
     const int recs = B * rec_bytes;
@@ -61,7 +62,7 @@ __host__ __device__ inline int pair_rec_region(int rec_bytes, int t_bytes, int n
 __host__ __device__ inline int pair_warp_bytes(int rec_bytes, int t_bytes, int nbins, int nq_compiled, int B)
 {
     return pair_rec_region(rec_bytes, t_bytes, nq_compiled, B) + (nbins * nq_compiled * t_bytes + 15) / 16 * 16 +
-           (3 * B + 15) / 16 * 16 + 4 * 32 * 4 + 32 * t_bytes + kJobWords * 4;
+           (3 * B + 15) / 16 * 16 + 4 * 32 * 4 + 32 * t_bytes;
 }
 
 // fixed part: radial table | edges (576) | job lists + scan scratch | the item's CatGeom
@@ -477,7 +478,6 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
     int* cursor = hist + 32;
     int* seg = cursor + 32;  // 64 ints
     T* w2_s = reinterpret_cast<T*>(seg + 64);  // 32
-    unsigned* jmask = reinterpret_cast<unsigned*>(w2_s + 32);  // kJobWords: cells this warp's primary reaches
 
     for (int i = threadIdx.x; i < kTabBytes / 4; i += nthreads)
         reinterpret_cast<int*>(tab)[i] = reinterpret_cast<const int*>(p.tab)[i];
@@ -511,45 +511,30 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
 #pragma unroll
         for (int d = 0; d < DP; ++d) cc[d] = ((it.x - g.base) / g.stride[d]) % g.nc[d];
 
-        // the item's neighbour cells: valid (periodic or inside the grid) and non-empty,
-        // in stencil order, with the prefix of their record counts
-        int njobs = 0, V = 0;
-        for (int base = 0; base < p.nstencil; base += nthreads) {
-            const int sidx = base + threadIdx.x;
-            int keep = 0, len = 0, a = 0, pk = 0;
-            if (sidx < p.nstencil) {
-                pk = p.stencil[sidx];
-                int cell = g.base;
-                bool ok = true;
+        // the item's stencil rows (runs of cells along axis 0, contiguous in the sorted records):
+        // the global index of the row's cell at x = 0 (-1: the row leaves a non-periodic grid), its
+        // offsets along the other axes and its x range
+        const int nrows = p.nrows;
+        for (int r = threadIdx.x; r < nrows; r += nthreads) {
+            const int2 rw = p.rows[r];
+            int base = g.base;
+            bool ok = true;
 #pragma unroll
-                for (int d = 0; d < DP; ++d) {
-                    int c = cc[d] + (int)(signed char)((pk >> (8 * d)) & 0xff);
-                    if (c < 0) {
-                        ok = ok && p.periodic;
-                        c += g.nc[d];
-                    } else if (c >= g.nc[d]) {
-                        ok = ok && p.periodic;
-                        c -= g.nc[d];
-                    }
-                    cell += c * g.stride[d];
+            for (int d = 1; d < DP; ++d) {
+                int c = cc[d] + (int)(signed char)((rw.x >> (8 * (d - 1))) & 0xff);
+                if (c < 0) {
+                    ok = ok && p.periodic;
+                    c += g.nc[d];
+                } else if (c >= g.nc[d]) {
+                    ok = ok && p.periodic;
+                    c -= g.nc[d];
                 }
-                if (ok) {
-                    a = p.cell_start[cell];
-                    len = p.cell_start[cell + 1] - a;
-                    keep = len > 0;
-                }
+                base += c * g.stride[d];
             }
-            int pos, off, tcount, tlen;
-            block_scan2(keep, keep ? len : 0, &pos, &off, &tcount, &tlen, ws);
-            if (keep) {
-                job_a[njobs + pos] = a;
-                job_pk[njobs + pos] = pk;
-                job_pre[njobs + pos] = V + off;
-            }
-            njobs += tcount;
-            V += tlen;
+            job_a[r] = ok ? base : -1;
+            job_pk[r] = rw.x;
+            job_pre[r] = rw.y;
         }
-        if (threadIdx.x == 0) job_pre[njobs] = V;
         __syncthreads();
 
         // warp w takes the item's primary w
@@ -594,41 +579,69 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
             for (int i = lane; i < nbins * NQ; i += 32) acc_s[i] = T(0);
             w2_s[lane] = T(0);
 
-            // the cells this primary can reach, 32 at a time
-            for (int j0 = 0; j0 < njobs; j0 += 32) {
-                const int j = j0 + lane;
-                T xjs[DP];
-                const bool ok = j < njobs && cell_geometry<DP, T>(p, g, cc, job_pk[j], xj, xjs);
-                const unsigned m = __ballot_sync(full, ok);
-                if (lane == 0) jmask[j0 >> 5] = m;
-            }
-            __syncwarp();
-
-            // walk the marked cells, streaming their candidates from global memory (L1/L2)
+            // the stencil rows, each trimmed to the cells this primary can reach: the x range left
+            // by the row's distance across the other axes, split where it wraps (at most one wrap,
+            // since a row spans at most the grid)
             int nbuf = 0;  // warp-uniform: staged pairs of the current batch
-            const int nwords = (njobs + 31) >> 5;
-            for (int jw = 0; jw < nwords; ++jw) {
-                unsigned mword = jmask[jw];
-                while (mword) {
-                    const int j = (jw << 5) + __ffs(mword) - 1;
-                    mword &= mword - 1;
-                    const int seg_a = job_a[j];
-                    const int seg_n = job_pre[j + 1] - job_pre[j];
-                    const int packed = job_pk[j];
-                    T xjs[DP];
+            T side0, box0;
+            if constexpr (kFP32) {
+                side0 = g.sidef[0];
+                box0 = g.boxf[0];
+            } else {
+                side0 = g.side[0];
+                box0 = g.box[0];
+            }
+            const int nc0 = g.nc[0];
+            for (int r = 0; r < nrows; ++r) {
+                const int base = job_a[r];
+                if (base < 0) continue;
+                const int rest = job_pk[r], lohi = job_pre[r];
+                T xjs[DP];
+                T a2 = T(0);
 #pragma unroll
-                    for (int d = 0; d < DP; ++d) {
-                        const int c = cc[d] + (int)(signed char)((packed >> (8 * d)) & 0xff);
-                        T box;
-                        if constexpr (kFP32) box = g.boxf[d];
-                        else box = g.box[d];
-                        xjs[d] = xj[d] - (c < 0 ? -box : (c >= g.nc[d] ? box : T(0)));
+                for (int d = 1; d < DP; ++d) {
+                    const int u = cc[d] + (int)(signed char)((rest >> (8 * (d - 1))) & 0xff);
+                    T side, box;
+                    if constexpr (kFP32) {
+                        side = g.sidef[d];
+                        box = g.boxf[d];
+                    } else {
+                        side = g.side[d];
+                        box = g.box[d];
                     }
+                    const T lo = T(u) * side, hi = lo + side;
+                    const T a = fmax(fmax(lo - xj[d], xj[d] - hi), T(0));
+                    a2 = fma(a, a, a2);
+                    xjs[d] = xj[d] - (u < 0 ? -box : (u >= g.nc[d] ? box : T(0)));
+                }
+                const T rx2 = T(p.rmax2f) - a2;
+                if (!(rx2 >= T(0))) continue;
+                const T rx = sqrt(rx2);
+                // cells whose x interval meets [x_j - rx, x_j + rx] (a margin of 1e-3 cells)
+                int ulo = (int)floor((xj[0] - rx) / side0 - T(1e-3));
+                int uhi = (int)floor((xj[0] + rx) / side0 + T(1e-3));
+                ulo = max(ulo, cc[0] + (int)(signed char)(lohi & 0xff));
+                uhi = min(uhi, cc[0] + (int)(signed char)((lohi >> 8) & 0xff));
+                if (!p.periodic) {
+                    ulo = max(ulo, 0);
+                    uhi = min(uhi, nc0 - 1);
+                }
+                for (int piece = 0; piece < 3; ++piece) {  // x < 0 (wrapped), inside, x >= nc (wrapped)
+                    const int qa = piece == 0 ? ulo : (piece == 1 ? max(ulo, 0) : max(ulo, nc0));
+                    const int qb = piece == 0 ? min(uhi, -1) : (piece == 1 ? min(uhi, nc0 - 1) : uhi);
+                    if (qa > qb) continue;
+                    const int wrap = piece == 0 ? nc0 : (piece == 2 ? -nc0 : 0);
+                    const int seg_a = p.cell_start[base + qa + wrap];
+                    const int seg_n = p.cell_start[base + qb + wrap + 1] - seg_a;
+                    if (seg_n <= 0) continue;
+                    // the run's image shift is that of its first cell (offset qa - cc[0] along x)
+                    const int packed = ((qa - cc[0]) & 0xff) | (rest << 8);
+                    xjs[0] = xj[0] - (piece == 0 ? -box0 : (piece == 2 ? box0 : T(0)));
                     ncand += seg_n;
                     nchunks += (unsigned)((seg_n + 31) >> 5);
                     // candidates in chunks of 32, two chunks per trip; each buffer is refilled two
                     // chunks ahead right after it is consumed (the record array is padded, so the
-                    // loads past the cell's end are harmless and masked)
+                    // loads past the run's end are harmless and masked)
                     const RP* src = rec + seg_a;
                     RP buf0 = ldg_rec(src, lane);
                     RP buf1 = ldg_rec(src, 32 + lane);

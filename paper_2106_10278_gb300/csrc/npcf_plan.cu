@@ -208,12 +208,13 @@ struct npcf_plan_s {
     DevBuf b_geo, b_cells, b_offsets, b_first, b_count, b_scales, b_stencil;
     std::vector<int64_t> b_key_off;
     std::vector<double> b_key_box;
-    int b_ncat = 0, b_ncells = 0, b_nstencil = 0;
+    int b_ncat = 0, b_ncells = 0, b_nstencil = 0, b_nrows = 0;
     // cached cell grid
     int grid_c = -1;
     int nc[4] = {1, 1, 1, 1};
     int ncells = 0;
     int nstencil = 0;
+    int nrows = 0;  // stencil rows (after the cells in d_stencil)
     int64_t grid_n = -1;
     // device facts
     int device = -1, nsm = 0, smem_optin = 0;
@@ -448,6 +449,42 @@ std::vector<int> make_stencil(int D, int c, const double* side, double reach)
     return out;
 }
 
+// The stencil's rows for the pair kernel: the cells that differ only in their axis-0 offset form a
+// run of consecutive cell indices (axis 0 has stride 1), so of sorted records.  A row is (offsets
+// along axes 1..3, 8 bits each from the lowest; x range lo | hi << 8), in a fixed pseudo-random
+// order.  They follow the cell list, which is padded to an even length (the rows are read as int2);
+// *nrows receives their count.
+std::vector<int> stencil_with_rows(const std::vector<int>& cells, int* nrows)
+{
+    std::vector<int> keys;
+    std::vector<int2> rows;
+    for (int pk : cells) {
+        const int dx = (int)(signed char)(pk & 0xff);
+        const int rest = (int)((unsigned)pk >> 8);
+        size_t i = 0;
+        while (i < keys.size() && keys[i] != rest) ++i;
+        if (i == keys.size()) {
+            keys.push_back(rest);
+            rows.push_back(make_int2(dx, dx));
+        } else {
+            rows[i].x = std::min(rows[i].x, dx);
+            rows[i].y = std::max(rows[i].y, dx);
+        }
+    }
+    std::vector<int> order(keys.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::mt19937 rng(0x5eed4321u);
+    std::shuffle(order.begin(), order.end(), rng);
+    std::vector<int> out(cells);
+    if (out.size() & 1) out.push_back(0);
+    for (int i : order) {
+        out.push_back(keys[i]);
+        out.push_back((rows[i].x & 0xff) | ((rows[i].y & 0xff) << 8));
+    }
+    *nrows = (int)keys.size();
+    return out;
+}
+
 GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
 {
     // Preferred: the cheapest grid with >= 4 particles per cell on average;
@@ -476,7 +513,10 @@ GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
         const double npc = (double)std::max<int64_t>(n, 1) / (double)ncells;
         g.stencil = make_stencil(P->Dp, c, side, reach);
         if ((int)g.stencil.size() > kMaxJobs) continue;  // the pair kernel lists an item's cells in smem
-        const double cost = g.stencil.size() * (npc + 24.0);
+        // candidates examined, plus a fixed cost per stencil row (the pair kernel walks rows)
+        int nrows = 0;
+        stencil_with_rows(g.stencil, &nrows);
+        const double cost = g.stencil.size() * npc + 40.0 * nrows;
         if (cost < any_cost) {
             any_cost = cost;
             any = g;
@@ -1057,7 +1097,7 @@ npcf_status prepare_grid(npcf_plan_s* P, int64_t n)
     for (int d = 0; d < 4; ++d) P->nc[d] = g.nc[d];
     P->ncells = g.ncells;
     P->nstencil = (int)g.stencil.size();
-    CUDA_TRY(upload(P->d_stencil, g.stencil));
+    CUDA_TRY(upload(P->d_stencil, stencil_with_rows(g.stencil, &P->nrows)));
     CUDA_TRY(upload(P->d_geo, std::vector<CatGeom>{make_geom(P->Dp, g.nc, P->box, 0, 0)}));
     P->grid_n = n;
     return NPCF_OK;
@@ -1097,8 +1137,9 @@ struct GridView {
     const CatGeom* geo = nullptr;      // device, ncat
     const int64_t* offsets = nullptr;  // device, ncat + 1 (ncat > 1)
     const int* cat_cells = nullptr;    // device, ncat + 1 (ncat > 1)
-    const int* stencil = nullptr;      // device
+    const int* stencil = nullptr;      // device (cells, then rows)
     int nstencil = 0;
+    int nrows = 0;
 };
 
 GridView single_view(const npcf_plan_s* P)
@@ -1108,6 +1149,7 @@ GridView single_view(const npcf_plan_s* P)
     v.geo = P->d_geo.as<CatGeom>();
     v.stencil = P->d_stencil.as<int>();
     v.nstencil = P->nstencil;
+    v.nrows = P->nrows;
     return v;
 }
 
@@ -1260,6 +1302,8 @@ npcf_status run_pairs(npcf_plan_s* P, const GridView& gv, const void* pos, const
     pp.geo = gv.geo;
     pp.nstencil = gv.nstencil;
     pp.stencil = gv.stencil;
+    pp.nrows = gv.nrows;
+    pp.rows = reinterpret_cast<const int2*>(gv.stencil + ((gv.nstencil + 1) & ~1));
     pp.rec = P->w_rec.p;
     pp.cell_start = cell_start;
     pp.items = ib.items;
@@ -1485,7 +1529,7 @@ npcf_status prepare_batch(npcf_plan_s* P, const int64_t* offsets, const double* 
     CUDA_TRY(upload(P->b_first, first));
     CUDA_TRY(upload(P->b_count, count));
     CUDA_TRY(upload(P->b_scales, scales));
-    CUDA_TRY(upload(P->b_stencil, best_stencil));
+    CUDA_TRY(upload(P->b_stencil, stencil_with_rows(best_stencil, &P->b_nrows)));
     P->b_ncells = base;
     P->b_nstencil = (int)best_stencil.size();
     P->b_key_off = off;
@@ -1538,6 +1582,7 @@ npcf_status run_batched(npcf_plan_s* P, const void* pos, const void* w, const in
     gv.cat_cells = P->b_cells.as<int>();
     gv.stencil = P->b_stencil.as<int>();
     gv.nstencil = P->b_nstencil;
+    gv.nrows = P->b_nrows;
     PairStage ps;
     if ((st = run_pairs(P, gv, pos, w, n, 0, n, s, &ps)) != NPCF_OK) return st;
     CoupleParams kp = couple_params(P, P->w_a.p, P->w_wprim.p, ps.ib.nprim, chunk, P->w_partial.as<double>());
@@ -2356,7 +2401,9 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
 
     Carve cv{base};
     CatGeom* geo = static_cast<CatGeom*>(cv.take(sizeof(CatGeom)));
-    int* stencil = static_cast<int*>(cv.take(sizeof(int) * g.stencil.size()));
+    int nrows = 0;
+    const std::vector<int> stencil_rows = stencil_with_rows(g.stencil, &nrows);
+    int* stencil = static_cast<int*>(cv.take(sizeof(int) * stencil_rows.size()));
     int* cid = static_cast<int*>(cv.take(sizeof(int) * (n + 1)));
     int* perm = static_cast<int*>(cv.take(sizeof(int) * (n + 1)));
     void* rec = cv.take((size_t)rb * (n + 1 + kRecPad));
@@ -2393,7 +2440,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
                         (cv.need + 255) & ~size_t(255), (long long)n, kNoallocBytes);
     }
 
-    CUDA_TRY(cudaMemcpyAsync(stencil, g.stencil.data(), sizeof(int) * g.stencil.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(stencil, stencil_rows.data(), sizeof(int) * stencil_rows.size(), cudaMemcpyHostToDevice, s));
     const CatGeom hgeo = make_geom(P->D, g.nc, P->box, 0, 0);
     CUDA_TRY(cudaMemcpyAsync(geo, &hgeo, sizeof(CatGeom), cudaMemcpyHostToDevice, s));
     int* cell_count = cells;
@@ -2441,6 +2488,8 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     pp.geo = geo;
     pp.nstencil = (int)g.stencil.size();
     pp.stencil = stencil;
+    pp.nrows = nrows;
+    pp.rows = reinterpret_cast<const int2*>(stencil + ((pp.nstencil + 1) & ~1));
     pp.rec = rec;
     pp.cell_start = cell_start;
     pp.items = ib.items;
