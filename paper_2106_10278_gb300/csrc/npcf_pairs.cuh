@@ -668,11 +668,27 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                             const bool flg = kFP32 ? (code & 64) != 0 : code != 63;
                             if (__any_sync(full, flg)) {
                                 if (flg) {
-                                    const int b = bin_refine_sph<T>(p, jorig, seg_a + c0 + lane, e1, e2, &rd0, &rd1);
-                                    bin = b < 0 ? 63 : b;
-                                    refined = true;
                                     ++nflag;
-                                    ++nexact;
+                                    // FP32 plans: the squared chord against the edges' (2 - 2 c_e); only a
+                                    // pair within tol of one (above the FP32 error of both) goes to FP64
+                                    bool nearE = !kFP32;
+                                    int bb = 0;
+                                    if constexpr (kFP32) {
+                                        for (int e = 0; e <= nbins; ++e) {
+                                            const float se = 2.f - 2.f * s_edge[e];
+                                            bb += se >= (float)r2 ? 1 : 0;
+                                            nearE = nearE || fabsf((float)r2 - se) < p.tol;
+                                        }
+                                    }
+                                    if (nearE) {
+                                        const int b = bin_refine_sph<T>(p, jorig, seg_a + c0 + lane, e1, e2, &rd0,
+                                                                        &rd1);
+                                        bin = b < 0 ? 63 : b;
+                                        refined = true;
+                                        ++nexact;
+                                    } else {
+                                        bin = (bb >= 1 && bb <= nbins) ? bb - 1 : 63;
+                                    }
                                 }
                             }
                         } else if constexpr (kFP32) {
