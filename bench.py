@@ -574,6 +574,16 @@ def run_ours(args, rank, world):
                                       "(null when that summary was taken on other sources)", "peak_note": note,
                     "flops_per_pair": fpp, "pairs_per_launch": pairs_per_step,
                     "pair_kernel_ms": float(np.mean(pair_ms))}
+    elif wl.N == 5:
+        # the factored 5PCF coupling: its algorithmic work is the contraction over (primary, m12) of
+        # X(row) Z(column) for every key, a complex multiply-add (8 flops) per key and m12 value
+        k = plan.keys()
+        macs = int(sum(2 * int(row[4 + 2]) + 1 for row in k))
+        achieved = 8 * macs * nprim / ck_s / 1e12
+        roofline = {"bound": "alu", "kernel": "k_d3n5_contract (factored 5PCF)", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_note": note,
+                    "flops_per_primary": 8 * macs, "flops_note": "8 per key and m12 (complex multiply-add)",
+                    "couple_kernel_ms": float(np.mean(couple_ms))}
     else:
         fpt = COUPLING_FLOPS_PER_TERM[wl.N]
         achieved = fpt * terms * nprim / ck_s / 1e12

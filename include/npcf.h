@@ -310,8 +310,9 @@ NPCF_API npcf_status npcf_last_counters(npcf_plan_t plan, int64_t* counters, int
 
 /*
  * Autotuning of the launch shapes (no counterpart in the paper): times candidate shapes on a
- * bounded sample of this input's primaries (about n/50, at least several waves of pair-kernel
- * work items) and keeps the fastest in the plan for every later call (npcf_compute,
+ * bounded sample of this input's primaries (all of them up to n = 500,000, else max(500,000,
+ * n/10) in four ranges spread over the input; a shape replaces the built-in one only when it is
+ * faster by more than 3%) and keeps the fastest in the plan for every later call (npcf_compute,
  * npcf_compute_batched, npcf_backward, npcf_compute_noalloc).  Searched: the pair kernel's warps
  * per CTA and pairs per warp batch; then, timed alone on the a-array of a quarter of the
  * primaries, the coupling's CTAs per SM (CUDA-core kernels), its FP32 span in chunks (tensor-core

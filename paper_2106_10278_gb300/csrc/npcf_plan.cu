@@ -211,6 +211,7 @@ struct npcf_plan_s {
     int b_ncat = 0, b_ncells = 0, b_nstencil = 0, b_nrows = 0;
     // cached cell grid
     int grid_c = -1;
+    int grid_adj = 0;  // the cached grid was chosen for the adjoint (cells capped at kMaxJobs)
     int nc[4] = {1, 1, 1, 1};
     int ncells = 0;
     int nstencil = 0;
@@ -485,10 +486,13 @@ std::vector<int> stencil_with_rows(const std::vector<int>& cells, int* nrows)
     return out;
 }
 
-GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
+GridChoice choose_grid(const npcf_plan_s* P, int64_t n, bool adjoint)
 {
     // Preferred: the cheapest grid with >= 4 particles per cell on average;
-    // otherwise (very sparse inputs) the cheapest valid grid of any density.
+    // otherwise (very sparse inputs) the cheapest valid grid of any density.  Cells of side
+    // r_max / c, c <= 4: finer cells (c up to 8, 20% fewer candidates at the D=3 4PCF workload)
+    // made the forward pair kernel 1.9x slower -- many short runs, each starting with a wait for
+    // its first records.  The adjoint pair kernel lists an item's cells, at most kMaxJobs.
     GridChoice best, any;
     double best_cost = 1e300, any_cost = 1e300;
     const double rmax = P->rcut;
@@ -512,10 +516,11 @@ GridChoice choose_grid(const npcf_plan_s* P, int64_t n)
         g.ncells = (int)ncells;
         const double npc = (double)std::max<int64_t>(n, 1) / (double)ncells;
         g.stencil = make_stencil(P->Dp, c, side, reach);
-        if ((int)g.stencil.size() > kMaxJobs) continue;  // the pair kernel lists an item's cells in smem
+        if (adjoint && (int)g.stencil.size() > kMaxJobs) continue;  // the adjoint lists an item's cells in smem
         // candidates examined, plus a fixed cost per stencil row (the pair kernel walks rows)
         int nrows = 0;
         stencil_with_rows(g.stencil, &nrows);
+        if (nrows > kMaxJobs) continue;  // the pair kernel tabulates an item's rows in smem
         const double cost = g.stencil.size() * npc + 40.0 * nrows;
         if (cost < any_cost) {
             any_cost = cost;
@@ -1086,10 +1091,10 @@ npcf_status setup_tables(npcf_plan_s* P)
     return NPCF_OK;
 }
 
-npcf_status prepare_grid(npcf_plan_s* P, int64_t n)
+npcf_status prepare_grid(npcf_plan_s* P, int64_t n, bool adjoint = false)
 {
-    if (P->grid_n == n && P->grid_c > 0) return NPCF_OK;
-    GridChoice g = choose_grid(P, n);
+    if (P->grid_n == n && P->grid_c > 0 && P->grid_adj == (int)adjoint) return NPCF_OK;
+    GridChoice g = choose_grid(P, n, adjoint);
     if (g.c == 0)
         return fail(NPCF_ERR_UNSUPPORTED, "no cell grid fits r_max=%g in the box (need r_max < box/2.25)",
                     P->edges[P->nbins]);
@@ -1100,6 +1105,7 @@ npcf_status prepare_grid(npcf_plan_s* P, int64_t n)
     CUDA_TRY(upload(P->d_stencil, stencil_with_rows(g.stencil, &P->nrows)));
     CUDA_TRY(upload(P->d_geo, std::vector<CatGeom>{make_geom(P->Dp, g.nc, P->box, 0, 0)}));
     P->grid_n = n;
+    P->grid_adj = (int)adjoint;
     return NPCF_OK;
 }
 
@@ -1403,7 +1409,7 @@ npcf_status run_backward(npcf_plan_s* P, const void* pos, const void* w, int64_t
 {
     npcf_status st;
     if ((st = ensure_device(P)) != NPCF_OK) return st;
-    if ((st = prepare_grid(P, n)) != NPCF_OK) return st;
+    if ((st = prepare_grid(P, n, true)) != NPCF_OK) return st;
     const int La = adjoint_compiled_lmax(P->D, P->lmax);
     if (La < 0) return fail(NPCF_ERR_UNSUPPORTED, "the adjoint is not compiled for D=%d lmax=%d", P->D, P->lmax);
     const int asmem = adjoint_pair_smem(P->D, La, P->fp64, P->nbins);
@@ -1475,7 +1481,9 @@ npcf_status prepare_batch(npcf_plan_s* P, const int64_t* offsets, const double* 
     for (int c = 1; c <= 4; ++c) {
         double side[4] = {rmax / c, rmax / c, rmax / c, rmax / c};
         std::vector<int> st = make_stencil(D, c, side, reach);
-        if ((int)st.size() > kMaxJobs) continue;
+        int nrows = 0;
+        stencil_with_rows(st, &nrows);
+        if (nrows > kMaxJobs) continue;
         bool ok = true;
         double cost = 0.0;
         int64_t total = 0;
@@ -1490,7 +1498,7 @@ npcf_status prepare_batch(npcf_plan_s* P, const int64_t* offsets, const double* 
             }
             total += cells;
             const double ni = (double)(off[i + 1] - off[i]);
-            cost += ni * st.size() * (ni / cells + 24.0);
+            cost += ni * (st.size() * ni / cells + 40.0 * nrows);
         }
         if (!ok || total >= (int64_t(1) << 26)) continue;
         if (cost < best_cost) {
@@ -1818,14 +1826,25 @@ void apply_shape(npcf_plan_s* P, const TuneShape& t)
 }
 
 // stage times (ms) of one run of the plan on primaries [0, pe): pair kernel, coupling
-npcf_status time_stages(npcf_plan_s* P, const void* pos, const void* w, int64_t n, int64_t pe, double* coeffs,
+// Stage times of one pass over m primaries, taken as four ranges of m/4 spread over the input
+// (inputs are often ordered -- e.g. data before randoms, or clustered points last -- so a single
+// leading range would tune for one part of the catalogue only).
+npcf_status time_stages(npcf_plan_s* P, const void* pos, const void* w, int64_t n, int64_t m, double* coeffs,
                         cudaStream_t s, float* pair_ms, float* couple_ms)
 {
-    npcf_status st = run(P, pos, w, n, coeffs, 0, pe, s);
-    if (st != NPCF_OK) return st;
-    CUDA_TRY(cudaEventSynchronize(P->ev[4]));
-    CUDA_TRY(cudaEventElapsedTime(pair_ms, P->ev[1], P->ev[2]));
-    CUDA_TRY(cudaEventElapsedTime(couple_ms, P->ev[2], P->ev[3]));
+    *pair_ms = *couple_ms = 0.f;
+    const int parts = (m < n && m >= 4 * 32) ? 4 : 1;  // the whole input: one pass, as the real call
+    for (int k = 0; k < parts; ++k) {
+        const int64_t pb = parts == 1 ? 0 : k * (n / parts), pe = pb + m / parts;
+        npcf_status st = run(P, pos, w, n, coeffs, pb, std::min(pe, n), s);
+        if (st != NPCF_OK) return st;
+        float a = 0.f, b = 0.f;
+        CUDA_TRY(cudaEventSynchronize(P->ev[4]));
+        CUDA_TRY(cudaEventElapsedTime(&a, P->ev[1], P->ev[2]));
+        CUDA_TRY(cudaEventElapsedTime(&b, P->ev[2], P->ev[3]));
+        *pair_ms += a;
+        *couple_ms += b;
+    }
     return NPCF_OK;
 }
 
@@ -1872,13 +1891,15 @@ npcf_status autotune(npcf_plan_s* P, const void* pos, const void* w, int64_t n, 
         return fail(NPCF_ERR_WORKSPACE, "device allocation of the tuning output failed");
     double* out = P->w_hout.as<double>();
     // the sample: enough primaries for several waves of pair-kernel items, at most all of them
-    const int64_t pe = std::min<int64_t>(n, std::max<int64_t>((int64_t)P->nsm * P->max_warps * 8, n / 50));
+    // (inputs up to 500k particles whole; larger ones a tenth: with smaller samples the short
+    // runs' tail and cache behaviour favoured shapes that were slower over the whole input)
+    const int64_t pe = n <= 500000 ? n : std::max<int64_t>(500000, n / 10);
     const npcf_opts saved = P->opts;
     P->opts.timing = 1;
     auto restore = [&]() { P->opts = saved; };
     // 1. the pair kernel: warps per CTA x batch size
     const int b0 = pair_batch(rec_bytes(P->D, P->fp64));
-    const int batches[4] = {b0 / 2, b0 * 3 / 4, b0, b0 * 3 / 2};
+    const int batches[4] = {b0, b0 / 2, b0 * 3 / 4, b0 * 3 / 2};  // the built-in one first
     const int mw = P->max_warps;
     const int warps[3] = {mw, std::max(1, mw * 3 / 4), std::max(1, mw / 2)};
     float bestp = 1e30f;
@@ -1892,7 +1913,9 @@ npcf_status autotune(npcf_plan_s* P, const void* pos, const void* w, int64_t n, 
                     restore();
                     return st;
                 }
-            if (pm < bestp) {
+            // the built-in shape (all warps, the default batch) is timed first and kept unless
+            // another is faster by more than 3% (timing noise)
+            if (best.pair_warps == 0 || pm < 0.97f * bestp) {
                 bestp = pm;
                 best.pair_warps = P->warps;
                 best.pair_batch = P->batch;
@@ -1906,12 +1929,9 @@ npcf_status autotune(npcf_plan_s* P, const void* pos, const void* w, int64_t n, 
     // 2. the coupling's launch shape, timed alone on the a-array of a larger sample (a quarter of the
     // primaries): its grid is sized by the primary count, so a small sample misjudges it
     const int64_t pe2 = std::min<int64_t>(n, std::max<int64_t>(pe, n / 4));
-    {
-        float pm = 0.f, cm = 0.f;
-        if ((st = time_stages(P, pos, w, n, pe2, out, s, &pm, &cm)) != NPCF_OK) {
-            restore();
-            return st;
-        }
+    if ((st = run(P, pos, w, n, out, 0, pe2, s)) != NPCF_OK) {  // the a-array of primaries [0, pe2)
+        restore();
+        return st;
     }
     float bestc = 1e30f;
     int cand[4];
@@ -2392,7 +2412,7 @@ npcf_status run_noalloc(npcf_plan_s* P, const void* pos, const void* w, int64_t 
     npcf_status st = noalloc_scratch(dev, &base);
     if (st != NPCF_OK) return st;
 
-    GridChoice g = choose_grid(P, n);
+    GridChoice g = choose_grid(P, n, false);
     if (g.c == 0) return fail(NPCF_ERR_UNSUPPORTED, "no cell grid fits r_max in the box");
     const int nc = g.ncells;
     const int64_t nprim_max = pe - pb;
