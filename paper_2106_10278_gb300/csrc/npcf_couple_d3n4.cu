@@ -4,16 +4,18 @@
 // (eq. NPCF-estimator-discrete with the coupling of eq. Coupling-C; the two CGs
 // of eq. CG-examples, the second coupling to zero, collapse to the signed 3j).
 //
-// Layout of the work: a CTA holds 8 primaries' a^b (all signed m) in shared
-// memory and walks the (l1, l2) label pairs in lockstep -- every warp runs the
-// same, fully unrolled body at a time, which keeps the instruction working set
-// small.  A lane owns (bin pair b1 < b2, primary): it forms
+// Layout of the work: a CTA holds 16 primaries' a^b (all signed m) in shared
+// memory and walks the (l1, l2) label pairs with a fully unrolled body.  A lane
+// owns (bin pair b1 < b2, primary); a warp task is two bin pairs x 16 primaries.
+// The lane forms
 //     P(l3, m3) = sum_{m1} c u_{m1} v_{-m1-m3},  m3 >= 0,
 // (the m3 < 0 half is (-1)^{l1+l2+l3} times the conjugate), contracts P with
-// a^{b3}_{l3 m3} for every b3 > b2, and the 8 primaries' terms of one output
-// are summed with three shuffles before one lane adds them to the CTA's FP32
-// shared accumulator.  Every 128 primaries the accumulators go into the CTA's
-// FP64 row of the partial buffer.
+// a^{b3}_{l3 m3} for every b3 > b2, and the 16 primaries' terms of one output
+// are summed with four shuffles before one lane adds them to the CTA's FP32
+// shared accumulator.  Tasks are ordered by b2 (long b3 loops first) and dealt
+// to the warps in snake order (w, 2W - 1 - w, 2W + w, ...), so every warp gets
+// long and short tasks alike before the group's barrier.  Every 128 primaries
+// the accumulators go into the CTA's FP64 row of the partial buffer.
 #include <cuda_runtime.h>
 
 #include "npcf_device.cuh"
@@ -23,7 +25,7 @@ namespace npcf {
 
 namespace {
 
-constexpr int kGP = 8;  // primaries held at once (lanes per bin pair)
+constexpr int kGP = 16;  // primaries held at once (lanes per bin pair)
 
 template <typename T>
 struct Cx {
@@ -98,6 +100,7 @@ __device__ __forceinline__ void couple_item(const Cx<T>* Ap, int b1, int b2, int
                 s += __shfl_xor_sync(0xffffffffu, s, 1);
                 s += __shfl_xor_sync(0xffffffffu, s, 2);
                 s += __shfl_xor_sync(0xffffffffu, s, 4);
+                s += __shfl_xor_sync(0xffffffffu, s, 8);
                 if (on && prim == 0) acc[key0 + (b3 - b2 - 1) * NLAM + lam] += s;
             });
         }
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(320, 2) k_couple_d3n4(const CoupleParams p)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int prim = lane & (kGP - 1);
     const int npair = blk.y - blk.x;
-    const int ntask = (npair + 3) / 4;
+    const int ntask = (npair + 1) / 2;
 
     // catalogue blockIdx.z: its primaries' rows of the a-array and its own partial rows
     const int cat = blockIdx.z;
@@ -168,8 +171,11 @@ __global__ void __launch_bounds__(320, 2) k_couple_d3n4(const CoupleParams p)
             __syncthreads();
             const T w = wsm[prim];
             const Cx<T>* Ap = A + prim * astride;
-            for (int t = warp; t < ntask; t += nwarps) {
-                const int pi = t * 4 + (lane >> 3);
+            for (int k = 0;; ++k) {
+                const int t = (k & 1) ? (k + 1) * nwarps - 1 - warp : k * nwarps + warp;  // snake order
+                if (k * nwarps >= ntask) break;
+                if (t >= ntask) continue;
+                const int pi = t * 2 + (lane >> 4);
                 const bool valid = pi < npair;
                 const int pr = p.task_pairs[blk.x + (valid ? pi : 0)];
                 const int2 bb = p.pairs[pr];
@@ -216,9 +222,11 @@ int couple_d3n4_smem(const CoupleParams& p, int fp64)
 
 int couple_d3n4_threads(int max_block_pairs)
 {
-    const int ntask = (max_block_pairs + 3) / 4;
-    // at most 10 warps: with __launch_bounds__(320, 2) two CTAs share an SM (warps loop over the tasks)
-    return 32 * (ntask < 10 ? (ntask < 1 ? 1 : ntask) : 10);
+    const int ntask = (max_block_pairs + 1) / 2;
+    // about two tasks per warp (snake order balances a long and a short one), at most 10 warps:
+    // with __launch_bounds__(320, 2) two CTAs share an SM
+    const int nw = (ntask + 1) / 2;
+    return 32 * (nw < 10 ? (nw < 1 ? 1 : nw) : 10);
 }
 
 cudaError_t launch_couple_d3n4(const CoupleParams& p, int fp64, int grid, int threads, int smem, cudaStream_t s)
