@@ -133,6 +133,50 @@ __device__ __forceinline__ void accum_d3(T* acc, T x, T y, T z, T w)
     });
 }
 
+// D=3 in FP32 with the complex columns as packed pairs (sm_100 FP32x2 arithmetic: one
+// instruction for the real and imaginary part): the same terms as accum_d3, the m = 0 column in
+// accR[l] and the (l, m >= 1) components in accC[l (l - 1) / 2 + m - 1] as (Re, Im).
+__host__ __device__ constexpr int d3_cidx(int l, int m) { return l * (l - 1) / 2 + m - 1; }
+
+template <int LMAX>
+__device__ __forceinline__ void accum_d3_x2(float* accR, float2* accC, float x, float y, float z, float w)
+{
+    // m = 0: w Qs_l^0(z)
+    accR[0] += w;
+    if constexpr (LMAX >= 1) {
+        float t2 = w, t1 = z * w;
+        accR[1] += t1;
+        static_for<2, LMAX + 1>([&](auto L) {
+            constexpr int l = decltype(L)::value;
+            const float nr = fmaf(float(cx::leg_A(l, 0)) * z, t1, -t2);
+            accR[l] += nr;
+            t2 = t1;
+            t1 = nr;
+        });
+    }
+    // m >= 1: P_m = w (x - i y)^m, then the column Qs_l^m(z) P_m
+    float2 P = make_float2(w, 0.f);
+    const float2 xx = make_float2(x, x), yy = make_float2(y, -y), zz = make_float2(z, z);
+    static_for<1, LMAX + 1>([&](auto M) {
+        constexpr int m = decltype(M)::value;
+        // (pr, pi) (x - i y) = (pr x + pi y, pi x - pr y)
+        P = __ffma2_rn(make_float2(P.y, P.x), yy, __fmul2_rn(P, xx));
+        accC[d3_cidx(m, m)] = __fadd2_rn(accC[d3_cidx(m, m)], P);
+        if constexpr (m + 1 <= LMAX) {
+            float2 t2 = P, t1 = __fmul2_rn(zz, P);
+            accC[d3_cidx(m + 1, m)] = __fadd2_rn(accC[d3_cidx(m + 1, m)], t1);
+            static_for<m + 2, LMAX + 1>([&](auto L) {
+                constexpr int l = decltype(L)::value;
+                const float az = float(cx::leg_A(l, m)) * z;
+                const float2 n = __ffma2_rn(make_float2(az, az), t1, make_float2(-t2.x, -t2.y));
+                accC[d3_cidx(l, m)] = __fadd2_rn(accC[d3_cidx(l, m)], n);
+                t2 = t1;
+                t1 = n;
+            });
+        }
+    });
+}
+
 // D=4: w Rs_{l2}^{l1}(u1, u2, u3) Cs^{(l2+1)}_{l3-l2}(u4), l1 <= l2 <= l3 <= LMAX
 template <int LMAX, typename T>
 __device__ __forceinline__ void accum_d4(T* acc, T u1, T u2, T u3, T u4, T w)

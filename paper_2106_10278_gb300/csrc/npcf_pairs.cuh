@@ -313,7 +313,7 @@ __device__ __forceinline__ Rec<D, T> ldg_rec(const Rec<D, T>* src, int i)
 template <int D, int LMAX, typename T>
 __device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned char* bins, unsigned short* idx,
                                                  T* acc_s, T* w2_s, int* hist, int* cursor, int* seg, int nbuf,
-                                                 int nbins, T* acc, unsigned& nrounds)
+                                                 int nbins, unsigned& nrounds)
 {
     constexpr int NQ = PairCfg<D, LMAX, T>::NQ;
     const unsigned full = 0xffffffffu;
@@ -389,32 +389,64 @@ __device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned
     // 5. every lane accumulates the pairs of its bin, lanes of one bin taking every my_nl-th
     // (the next record is loaded before the current one is accumulated; the index is clamped into
     // the batch, so the extra load at the end is harmless)
+    // 6 (first half). The lanes' sums go through the record space (32 x (NQ + 1) scratch), so each
+    // lane's accumulators live only inside this function.
     T w2 = T(0);
-    if (my_rank < my_nl && my_rank < my_cnt) {
-        const int last = nbuf - 1;
-        Rec<D, T> e = recs[idx[my_start + my_rank]];
-        for (int k = my_rank; k < my_cnt; k += my_nl) {
-            const Rec<D, T> en = recs[idx[min(my_start + k + my_nl, last)]];
-            if constexpr (D == 2) accum_d2<LMAX, T>(acc, e.x(0), e.x(1), e.w());
-            else if constexpr (D == 3) accum_d3<LMAX, T>(acc, e.x(0), e.x(1), e.x(2), e.w());
-            else accum_d4<LMAX, T>(acc, e.x(0), e.x(1), e.x(2), e.x(3), e.w());
-            w2 = fma(e.w(), e.w(), w2);
-            e = en;
-        }
-    }
-    __syncwarp();
-    // 6. merge: the lanes' sums through the record space into acc_s (segments in lane order).
-    // Components 0..31 go lane = component over the bins in turn (the segment length is the same
-    // for the whole warp); the last NQ - 32 components and the w^2 sums are shared out over
-    // (bin, component).
     T* scr = reinterpret_cast<T*>(recs);
+    if constexpr (D == 3 && sizeof(T) == 4) {
+        // FP32 D = 3: the complex columns accumulated as packed pairs
+        constexpr int NC = LMAX * (LMAX + 1) / 2;
+        float accR[LMAX + 1];
+        float2 accC[NC > 0 ? NC : 1];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        scr[lane * (NQ + 1) + q] = acc[q];
-        acc[q] = T(0);
+        for (int l = 0; l <= LMAX; ++l) accR[l] = 0.f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) accC[c] = make_float2(0.f, 0.f);
+        if (my_rank < my_nl && my_rank < my_cnt) {
+            const int last = nbuf - 1;
+            Rec<D, T> e = recs[idx[my_start + my_rank]];
+            for (int k = my_rank; k < my_cnt; k += my_nl) {
+                const Rec<D, T> en = recs[idx[min(my_start + k + my_nl, last)]];
+                accum_d3_x2<LMAX>(accR, accC, e.x(0), e.x(1), e.x(2), e.w());
+                w2 = fma(e.w(), e.w(), w2);
+                e = en;
+            }
+        }
+        __syncwarp();
+        static_for<0, LMAX + 1>([&](auto L) {
+            constexpr int l = decltype(L)::value;
+            scr[lane * (NQ + 1) + q_index_d3(l, 0)] = accR[l];
+            static_for<1, l + 1>([&](auto M) {
+                constexpr int m = decltype(M)::value;
+                scr[lane * (NQ + 1) + q_index_d3(l, m)] = accC[d3_cidx(l, m)].x;
+                scr[lane * (NQ + 1) + q_index_d3(l, m) + 1] = accC[d3_cidx(l, m)].y;
+            });
+        });
+    } else {
+        T acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = T(0);
+        if (my_rank < my_nl && my_rank < my_cnt) {
+            const int last = nbuf - 1;
+            Rec<D, T> e = recs[idx[my_start + my_rank]];
+            for (int k = my_rank; k < my_cnt; k += my_nl) {
+                const Rec<D, T> en = recs[idx[min(my_start + k + my_nl, last)]];
+                if constexpr (D == 2) accum_d2<LMAX, T>(acc, e.x(0), e.x(1), e.w());
+                else if constexpr (D == 3) accum_d3<LMAX, T>(acc, e.x(0), e.x(1), e.x(2), e.w());
+                else accum_d4<LMAX, T>(acc, e.x(0), e.x(1), e.x(2), e.x(3), e.w());
+                w2 = fma(e.w(), e.w(), w2);
+                e = en;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) scr[lane * (NQ + 1) + q] = acc[q];
     }
     scr[lane * (NQ + 1) + NQ] = w2;
     __syncwarp();
+    // 6 (second half). Merge into acc_s (segments in lane order): components 0..31 go lane =
+    // component over the bins in turn (the segment length is the same for the whole warp); the
+    // last NQ - 32 components and the w^2 sums are shared out over (bin, component).
     constexpr int QA = NQ < 32 ? NQ : 32;  // components merged lane-parallel
     constexpr int QB = NQ + 1 - QA;         // the rest (w^2 last)
     unsigned bm = E;                        // bins with a segment
@@ -573,9 +605,6 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                 e2[2] = uj[0] * e1[1] - uj[1] * e1[0];
             }
 
-            T acc[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) acc[q] = T(0);
             for (int i = lane; i < nbins * NQ; i += 32) acc_s[i] = T(0);
             w2_s[lane] = T(0);
 
@@ -751,7 +780,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
                         if (nbuf > kB - 64) {  // room for the trip's two chunks
                             __syncwarp();
                             pair_batch_flush<D, LMAX, T>(recs, bins, idx, acc_s, w2_s, hist, cursor, seg, nbuf,
-                                                         nbins, acc, nrounds);
+                                                         nbins, nrounds);
                             nbuf = 0;
                             ++nbatch;
                         }
@@ -766,7 +795,7 @@ __global__ void __launch_bounds__(PairCfg<D, LMAX, T>::kThreads, 1) k_pairs(cons
             }
             if (nbuf > 0) {
                 __syncwarp();
-                pair_batch_flush<D, LMAX, T>(recs, bins, idx, acc_s, w2_s, hist, cursor, seg, nbuf, nbins, acc,
+                pair_batch_flush<D, LMAX, T>(recs, bins, idx, acc_s, w2_s, hist, cursor, seg, nbuf, nbins,
                                              nrounds);
                 ++nbatch;
             }
