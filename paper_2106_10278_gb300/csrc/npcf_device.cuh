@@ -94,6 +94,21 @@ __device__ __forceinline__ void accum_d2(T* acc, T x, T y, T w)
     });
 }
 
+// D=2 in FP32 with packed pairs: acc0 the l = 0 term, accC[l - 1] = (Re, Im) of w (x - i y)^l.
+template <int LMAX>
+__device__ __forceinline__ void accum_d2_x2(float& acc0, float2* accC, float x, float y, float w)
+{
+    acc0 += w;
+    float2 P = make_float2(w, 0.f);
+    const float2 xx = make_float2(x, x), yy = make_float2(y, -y);
+    static_for<1, LMAX + 1>([&](auto L) {
+        constexpr int l = decltype(L)::value;
+        // (pr, pi) (x - i y) = (pr x + pi y, pi x - pr y)
+        P = __ffma2_rn(make_float2(P.y, P.x), yy, __fmul2_rn(P, xx));
+        accC[l - 1] = __fadd2_rn(accC[l - 1], P);
+    });
+}
+
 // D=3: w Qs_l^m(z) (x - i y)^m for l <= LMAX, 0 <= m <= l
 template <int LMAX, typename T>
 __device__ __forceinline__ void accum_d3(T* acc, T x, T y, T z, T w)

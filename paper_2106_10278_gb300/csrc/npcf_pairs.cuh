@@ -393,7 +393,30 @@ __device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned
     // lane's accumulators live only inside this function.
     T w2 = T(0);
     T* scr = reinterpret_cast<T*>(recs);
-    if constexpr (D == 3 && sizeof(T) == 4) {
+    if constexpr (D == 2 && sizeof(T) == 4) {
+        // FP32 D = 2: the complex powers accumulated as packed pairs
+        float acc0 = 0.f;
+        float2 accC[LMAX > 0 ? LMAX : 1];
+#pragma unroll
+        for (int c = 0; c < LMAX; ++c) accC[c] = make_float2(0.f, 0.f);
+        if (my_rank < my_nl && my_rank < my_cnt) {
+            const int last = nbuf - 1;
+            Rec<D, T> e = recs[idx[my_start + my_rank]];
+            for (int k = my_rank; k < my_cnt; k += my_nl) {
+                const Rec<D, T> en = recs[idx[min(my_start + k + my_nl, last)]];
+                accum_d2_x2<LMAX>(acc0, accC, e.x(0), e.x(1), e.w());
+                w2 = fma(e.w(), e.w(), w2);
+                e = en;
+            }
+        }
+        __syncwarp();
+        scr[lane * (NQ + 1)] = acc0;
+#pragma unroll
+        for (int l = 1; l <= LMAX; ++l) {
+            scr[lane * (NQ + 1) + q_index_d2(l)] = accC[l - 1].x;
+            scr[lane * (NQ + 1) + q_index_d2(l) + 1] = accC[l - 1].y;
+        }
+    } else if constexpr (D == 3 && sizeof(T) == 4) {
         // FP32 D = 3: the complex columns accumulated as packed pairs
         constexpr int NC = LMAX * (LMAX + 1) / 2;
         float accR[LMAX + 1];
