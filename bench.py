@@ -580,10 +580,12 @@ def run_ours(args, rank, world):
         k = plan.keys()
         macs = int(sum(2 * int(row[4 + 2]) + 1 for row in k))
         achieved = 8 * macs * nprim / ck_s / 1e12
-        roofline = {"bound": "alu", "kernel": "k_d3n5_contract (factored 5PCF)", "achieved": achieved,
+        roofline = {"bound": "alu", "kernel": "k_d3n5_form + k_d3n5_contract (factored 5PCF)", "achieved": achieved,
                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_note": note,
                     "flops_per_primary": 8 * macs, "flops_note": "8 per key and m12 (complex multiply-add)",
                     "couple_kernel_ms": float(np.mean(couple_ms))}
+        if prec == "mixed_bf16x3":
+            roofline.update(d3n5_tensor_roofline(wl, ck_s))
     else:
         fpt = COUPLING_FLOPS_PER_TERM[wl.N]
         achieved = fpt * terms * nprim / ck_s / 1e12
@@ -631,7 +633,10 @@ def run_ours(args, rank, world):
         # the D=3 4PCF has no tensor-core coupling (its contraction over primaries would need a
         # per-primary operand of 58,320 complex products, as costly as its CUDA-core kernel); the
         # metric's mixed-vs-FP32 comparison is measured on the D=2 4PCF, whose coupling runs there
-        line["mixed_vs_fp32"] = mixed_arm(dev)
+        line["mixed_vs_fp32"] = mixed_arm(dev, "d2n4")
+        line["mixed_vs_fp32_5pcf"] = mixed_arm(dev, "d3n5", oracle_prims=24)
+    if rank == 0 and args.workload == "d3n5" and not args.no_mixed_arm and prec != "mixed_bf16x3":
+        line["mixed_vs_fp32"] = mixed_arm(dev, "d3n5", oracle_prims=24)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def gpu_range(a, b):  # the GPU's coefficients of primaries [a, b), for the per-result error
             z = plan.compute(pos, w, primaries=(a, b)).cpu().numpy()
@@ -645,26 +650,67 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
-def mixed_arm(dev, steps=5, oracle_prims=100):
+def d3n5_tc_k1_sum(lmax, nbins):
+    """Sum over the tiles of the tensor-core 5PCF contraction of K per primary (2 l12 + 1): the
+    tiles are 128 rows x 64 columns of one parity, rows (b1 < b2, l1, l2) in (parity, b2, b1) order
+    and columns (b3 < b4, l3, l4) in (parity, b3, b4) order, kept when some row's b2 is below some
+    column's b3 (the plan's own tiling, restated)."""
+    p12 = [(b1, b2) for b2 in range(1, nbins - 2) for b1 in range(b2)]
+    p34 = [(b3, b4) for b3 in range(2, nbins - 1) for b4 in range(b3 + 1, nbins)]
+    total = 0
+    for l12 in range(2 * lmax + 1):
+        lx = [(a, b) for a in range(lmax + 1) for b in range(lmax + 1) if abs(a - b) <= l12 <= a + b]
+        lz = [(a, b) for a in range(lmax + 1) for b in range(lmax + 1) if abs(l12 - a) <= b <= l12 + a]
+        for par in (0, 1):
+            rows = sorted((p[1], p[0], i) for p in p12 for i, (a, b) in enumerate(lx) if (a + b) % 2 == par)
+            cols = sorted((p[0], p[1], i) for p in p34 for i, (a, b) in enumerate(lz) if (a + b) % 2 == par)
+            for r0 in range(0, len(rows), 128):
+                for c0 in range(0, len(cols), 64):
+                    if rows[r0][0] < cols[min(len(cols), c0 + 64) - 1][0]:
+                        total += 2 * l12 + 1
+    return total
+
+
+def d3n5_tensor_roofline(wl, couple_s):
+    """Tensor-pipe rate of the BF16x3 5PCF contraction: MMA flops issued (6 MMAs of 128 x 128 per
+    16 K elements: 2 x 128 x 128 x 6 flops per K element and tile, padding included) over the
+    coupling stage (formation + contraction)."""
+    mma = 6 * 2 * 128 * 128 * d3n5_tc_k1_sum(wl.lmax, len(wl.edges) - 1) * wl.n
+    bf = _peaks().get("bf16_tflops")
+    out = {"tensor_bound": "tensor", "tensor_kernel": "k_d3n5_contract_tc (bf16x3)",
+           "tensor_achieved": mma / couple_s / 1e12, "tensor_peak": bf, "tensor_unit": "TFLOP/s",
+           "tensor_peak_note": "MEASURED_PEAKS.json bf16_tflops (of measured)",
+           "tensor_flops_note": "MMA flops issued per launch over the coupling stage (formation included)"}
+    if bf:
+        out["tensor_frac"] = out["tensor_achieved"] / bf
+    return out
+
+
+def mixed_arm(dev, name="d2n4", steps=5, oracle_prims=100):
     """The split-precision tensor-core coupling against the FP32 CUDA-core coupling, on the D=2 4PCF
-    workload (200k points, 16 bins, lmax 10): coupling-stage times (CUDA events, median of `steps`
-    after a warm-up), the speed-up, the error of each split against the FP32 result (every primary)
-    and against the FP64 oracle (primaries [0, oracle_prims)), and the tensor pipe's rate."""
+    workload (200k points, 16 bins, lmax 10) or the paper's 5PCF example (10^4 points, 10 bins,
+    lmax 4): coupling-stage times (CUDA events, median of `steps` after a warm-up), the speed-up,
+    the error of each split against the FP32 result (every primary) and against the FP64 oracle
+    (primaries [0, oracle_prims)), and the tensor pipe's rate."""
     import torch
 
     from paper_2106_10278_gb300 import catalogs
     from paper_2106_10278_gb300.npcf import Plan
     import oracle
 
-    wl = catalogs.workload("d2n4")
+    wl = catalogs.workload(name)
     pos = torch.tensor(wl.pos, dtype=torch.float32, device=dev)
     w = torch.tensor(wl.w, dtype=torch.float32, device=dev)
     keys, ref = oracle.estimate(wl.D, wl.N, wl.lmax, wl.edges, wl.box, wl.pos, wl.w, primaries=(0, oracle_prims))
     index = {tuple(int(x) for x in k): i for i, k in enumerate(keys)}
-    out = {"workload": "d2n4: D=2 4PCF, 200k points (100k uniform + 100k in 400 Gaussian blobs), 16 bins over "
-                       "[0.002,0.05], lmax 10", "couple_ms": {}, "rel_err_vs_fp32": {}, "rel_err_vs_oracle": {}}
+    desc = {"d2n4": "d2n4: D=2 4PCF, 200k points (100k uniform + 100k in 400 Gaussian blobs), 16 bins over "
+                    "[0.002,0.05], lmax 10",
+            "d3n5": "d3n5: D=3 5PCF, 10^4 uniform points in the periodic unit cube, 10 bins over [0.1,0.4], lmax 4"}
+    out = {"workload": desc[name], "couple_ms": {}, "rel_err_vs_fp32": {}, "rel_err_vs_oracle": {},
+           "oracle_primaries": oracle_prims}
     z32 = None
-    for prec in ("fp32", "mixed_bf16x3", "mixed_tf32x3"):
+    precs = ("fp32", "mixed_bf16x3", "mixed_tf32x3") if name == "d2n4" else ("fp32", "mixed_bf16x3")
+    for prec in precs:
         plan = Plan(wl.D, wl.N, wl.lmax, wl.edges, wl.box, precision=prec, sync_check=False, timing=True)
         plan.autotune(pos, w)
         z = plan.compute(pos, w).cpu().numpy()
@@ -684,6 +730,9 @@ def mixed_arm(dev, steps=5, oracle_prims=100):
             out["tuned_bf16x3"] = plan.tuned_config()
     t32 = out["couple_ms"]["fp32"]
     out["speedup_vs_fp32"] = {k: t32 / v for k, v in out["couple_ms"].items() if k != "fp32"}
+    if name == "d3n5":
+        out["tensor_roofline"] = d3n5_tensor_roofline(wl, out["couple_ms"]["mixed_bf16x3"] * 1e-3)
+        return out
     # tensor-pipe rate of the BF16x3 kernel: MMA flops issued (3 split products over M=128 rows x N=32
     # columns x K=2 per primary and label set, padding included) over its time
     nprim, nlam = wl.n, 176

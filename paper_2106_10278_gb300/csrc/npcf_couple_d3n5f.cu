@@ -16,6 +16,7 @@
 // ty + 16 a, columns tx + 16 b),
 // K staged through shared memory, FP32 (or FP64) sums over the CTA's primaries added into its
 // FP64 partial row.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,34 +33,61 @@ struct C5 {
     T r, i;
 };
 
-constexpr int kFormThreads = 256;
+constexpr int kFormWarps = 8;
 constexpr int kTile = 64;   // rows and columns of a contraction tile
 constexpr int kKc = 16;     // K entries per shared-memory stage
 constexpr int kConThreads = 256;
 
-// One primary per CTA: its a^b for all signed m in shared memory, then every X and Z entry.
-template <typename T>
-__global__ void __launch_bounds__(kFormThreads) k_d3n5_form(const D3n5Params q, int chunk0, int nchunk_prim)
+// Where one X (or Z) entry of primary jj of the chunk goes.  Within the block of label l12 the
+// rows are K = npc (2 l12 + 1) long and K is ordered (m12, primary), so the lanes of a warp
+// (consecutive primaries) write consecutive elements.  MODE 0: complex T; MODE 1: four BF16
+// planes (Re hi, Re lo, Im hi, Im lo) of the split-precision tensor-core contraction, where
+// v = hi + lo with hi = v rounded to BF16 and lo the rounded remainder.
+template <typename T, int MODE>
+__device__ __forceinline__ void d5_store(void* base, size_t block, size_t plane, size_t at, T re, T im)
+{
+    if constexpr (MODE == 0) {
+        static_cast<C5<T>*>(base)[block + at] = C5<T>{re, im};
+    } else {
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(base) + 4 * block + at;
+        const float r = (float)re, i = (float)im;
+        const __nv_bfloat16 rh = __float2bfloat16_rn(r), ih = __float2bfloat16_rn(i);
+        o[0] = rh;
+        o[plane] = __float2bfloat16_rn(r - __bfloat162float(rh));
+        o[2 * plane] = ih;
+        o[3 * plane] = __float2bfloat16_rn(i - __bfloat162float(ih));
+    }
+}
+
+// X and Z of PL primaries per CTA (blockIdx.x), primary = lane % PL: their a^b for all signed m
+// in shared memory ([bin, state][PL], so the lanes of one term read consecutive words), then the
+// CTA's slice (blockIdx.y of gridDim.y) of the X and Z entries, one entry per group of PL lanes,
+// its CG terms walked together by those lanes.
+template <typename T, int MODE, int PL>
+__global__ void __launch_bounds__(kFormWarps * 32) k_d3n5_form(const D3n5Params q, int chunk0, int nchunk_prim)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NSUB = 32 / PL;
     const int nb = q.nbins, S = (q.lmax + 1) * (q.lmax + 1);
-    C5<T>* A = reinterpret_cast<C5<T>*>(smem);  // [nb][S]
-    const int jj = blockIdx.x;
-    const int cat = blockIdx.y;
+    C5<T>* A = reinterpret_cast<C5<T>*>(smem);  // [nb * S][PL]
+    const int cat = blockIdx.z;
     const int nprim = q.cat_count ? q.cat_count[cat] : *q.nprim;
     const size_t first = q.cat_first ? (size_t)q.cat_first[cat] : 0;
-    const int j = chunk0 + jj;
-    const bool live = jj < nchunk_prim && j < nprim;
-    const T* ap = static_cast<const T*>(q.a) + (first + (live ? j : 0)) * (size_t)nb * q.nq;
-    const T w = live ? static_cast<const T*>(q.wprim)[first + j] : T(0);
-    for (int i = threadIdx.x; i < nb * S; i += blockDim.x) {
-        const int b = i / S, s = i - b * S;
-        int l = 0;
-        while ((l + 1) * (l + 1) <= s) ++l;
-        const int m = s - l * l - l, am = m < 0 ? -m : m;
+    const int jj0 = blockIdx.x * PL;
+    const int nx = q.ngx * q.np12, nz = q.ngz * q.np34;
+    const int per = (nx + nz + gridDim.y - 1) / gridDim.y;
+    const int e0 = blockIdx.y * per, e1 = min(nx + nz, e0 + per);  // entries: X then Z
+    const T* abase = static_cast<const T*>(q.a);
+    for (int i = threadIdx.x; i < nb * S * PL; i += blockDim.x) {
+        const int pj = i % PL, bs = i / PL;
+        const int b = bs / S, s = bs - b * S;
+        const int jj = jj0 + pj, j = chunk0 + jj;
         T re = T(0), im = T(0);
-        if (live) {
-            const T* x = ap + b * q.nq + q_index_d3(l, am);
+        if (jj < nchunk_prim && j < nprim) {
+            int l = 0;
+            while ((l + 1) * (l + 1) <= s) ++l;
+            const int m = s - l * l - l, am = m < 0 ? -m : m;
+            const T* x = abase + (first + j) * (size_t)nb * q.nq + b * q.nq + q_index_d3(l, am);
             re = x[0];
             im = am > 0 ? x[1] : T(0);
             if (m < 0) {  // a_{l,-m} = (-1)^m conj(a_{l m})
@@ -72,55 +100,66 @@ __global__ void __launch_bounds__(kFormThreads) k_d3n5_form(const D3n5Params q, 
         }
         A[i] = C5<T>{re, im};
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pj = lane % PL, sub = lane / PL;
+    const int jj = jj0 + pj, j = chunk0 + jj;
+    const bool live = jj < nchunk_prim && j < nprim;
+    const bool mine = jj < q.npc;  // a column of the scratch (the chunk's last CTA may overhang it)
+    const T w = live ? static_cast<const T*>(q.wprim)[first + j] : T(0);
     __syncthreads();
-    C5<T>* X = static_cast<C5<T>*>(q.xs) + (size_t)cat * q.xs_cat;
-    C5<T>* Z = static_cast<C5<T>*>(q.zs) + (size_t)cat * q.zs_cat;
     const T* coef = static_cast<const T*>(q.coef);
+    const size_t npc = (size_t)q.npc;
+    void* X = MODE == 0 ? (void*)(static_cast<C5<T>*>(q.xs) + (size_t)cat * q.xs_cat)
+                        : (void*)(static_cast<__nv_bfloat16*>(q.xs) + (size_t)cat * 4 * q.xs_cat);
+    void* Z = MODE == 0 ? (void*)(static_cast<C5<T>*>(q.zs) + (size_t)cat * q.zs_cat)
+                        : (void*)(static_cast<__nv_bfloat16*>(q.zs) + (size_t)cat * 4 * q.zs_cat);
     // X entries: (group, bin pair); group = (l12, (l1, l2), m12) with its term list
-    const int nx = q.ngx * q.np12;
-    for (int e = threadIdx.x; e < nx; e += blockDim.x) {
+    for (int e = e0 + warp * NSUB + sub; e < min(e1, nx); e += kFormWarps * NSUB) {
         const int g = e / q.np12, pr = e - g * q.np12;
         const int4 G = q.gx[g];  // term begin, term end, l12, row-in-pair (ix) | m12 index << 16
         const int2 bb = q.p12[pr];
-        const C5<T>* u = A + bb.x * S;
-        const C5<T>* v = A + bb.y * S;
+        const C5<T>* u = A + bb.x * S * PL + pj;
+        const C5<T>* v = A + bb.y * S * PL + pj;
         T sr = T(0), si = T(0);
         for (int t = G.x; t < G.y; ++t) {
             const int st = q.terms[t];
-            const C5<T> x = u[st & 0xff], y = v[(st >> 8) & 0xff];
+            const C5<T> x = u[(st & 0xff) * PL], y = v[((st >> 8) & 0xff) * PL];
             const T pr_ = x.r * y.r - x.i * y.i, pi_ = x.r * y.i + x.i * y.r;
             sr = fma(coef[t], pr_, sr);
             si = fma(coef[t], pi_, si);
         }
         const int l12 = G.z, ix = G.w & 0xffff, mi = G.w >> 16, K = 2 * l12 + 1;
         const int row = q.xrow[q.row0[l12] + pr * q.nlx[l12] + ix];  // position in the (parity, b2) order
-        X[(size_t)q.xoff[l12] * q.npc + ((size_t)row * q.npc + jj) * K + mi] = C5<T>{w * sr, w * si};
+        if (mine)
+            d5_store<T, MODE>(X, (size_t)q.xoff[l12] * npc, (size_t)q.np12 * q.nlx[l12] * K * npc,
+                              ((size_t)row * K + mi) * npc + jj, w * sr, w * si);
     }
-    const int nz = q.ngz * q.np34;
-    for (int e = threadIdx.x; e < nz; e += blockDim.x) {
+    for (int e = max(e0, nx) - nx + warp * NSUB + sub; e < e1 - nx; e += kFormWarps * NSUB) {
         const int g = e / q.np34, pr = e - g * q.np34;
         const int4 G = q.gz[g];
         const int2 bb = q.p34[pr];
-        const C5<T>* u = A + bb.x * S;
-        const C5<T>* v = A + bb.y * S;
+        const C5<T>* u = A + bb.x * S * PL + pj;
+        const C5<T>* v = A + bb.y * S * PL + pj;
         T sr = T(0), si = T(0);
         for (int t = G.x; t < G.y; ++t) {
             const int st = q.terms[t];
-            const C5<T> x = u[st & 0xff], y = v[(st >> 8) & 0xff];
+            const C5<T> x = u[(st & 0xff) * PL], y = v[((st >> 8) & 0xff) * PL];
             const T pr_ = x.r * y.r - x.i * y.i, pi_ = x.r * y.i + x.i * y.r;
             sr = fma(coef[t], pr_, sr);
             si = fma(coef[t], pi_, si);
         }
         const int l12 = G.z, iz = G.w & 0xffff, mi = G.w >> 16, K = 2 * l12 + 1;
         const int col = q.zcol[q.col0[l12] + pr * q.nlz[l12] + iz];  // position in the (parity, b3) order
-        Z[(size_t)q.zoff[l12] * q.npc + ((size_t)col * q.npc + jj) * K + mi] = C5<T>{sr, si};
+        if (mine)
+            d5_store<T, MODE>(Z, (size_t)q.zoff[l12] * npc, (size_t)q.np34 * q.nlz[l12] * K * npc,
+                              ((size_t)col * K + mi) * npc + jj, sr, si);
     }
 }
 
 // One tile (l12, 64 rows, 64 columns) per blockIdx.x, one slice of the chunk's primaries per
 // blockIdx.y (its own partial row), catalogue blockIdx.z.
 template <typename T>
-__global__ void __launch_bounds__(kConThreads) k_d3n5_contract(const D3n5Params q, int nchunk_prim)
+__global__ void __launch_bounds__(kConThreads) k_d3n5_contract(const D3n5Params q)
 {
     __shared__ C5<T> Xs[kKc][kTile + 1];
     __shared__ C5<T> Zs[kKc][kTile + 1];
@@ -133,10 +172,10 @@ __global__ void __launch_bounds__(kConThreads) k_d3n5_contract(const D3n5Params 
     const int cat = blockIdx.z;
     const C5<T>* X = static_cast<const C5<T>*>(q.xs) + (size_t)cat * q.xs_cat + (size_t)q.xoff[l12] * q.npc;
     const C5<T>* Z = static_cast<const C5<T>*>(q.zs) + (size_t)cat * q.zs_cat + (size_t)q.zoff[l12] * q.npc;
-    // this CTA's primaries of the chunk
-    const int per = (nchunk_prim + gridDim.y - 1) / gridDim.y;
-    const int j0 = blockIdx.y * per, j1 = min(nchunk_prim, j0 + per);
-    const int k0 = j0 * K1, k1 = max(k0, j1 * K1);
+    // this CTA's slice of K = (m12, primary of the chunk)
+    const int Kr = q.npc * K1;
+    const int per = (Kr + gridDim.y - 1) / gridDim.y;
+    const int k0 = min(Kr, (int)blockIdx.y * per), k1 = min(Kr, k0 + per);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     T ar[4][4], ai[4][4];
 #pragma unroll
@@ -194,25 +233,66 @@ __global__ void __launch_bounds__(kConThreads) k_d3n5_contract(const D3n5Params 
 
 }  // namespace
 
-int d3n5f_form_smem(int nbins, int lmax, int fp64)
+// Primaries per CTA of the formation kernel (32, 16 or 8: the most whose a-values fit in shared
+// memory), or 0 when even 8 do not fit.
+int d3n5f_form_lanes(int nbins, int lmax, int fp64, int smem_optin)
 {
-    return nbins * (lmax + 1) * (lmax + 1) * 2 * (fp64 ? 8 : 4);
+    for (int pl = 32; pl >= 8; pl /= 2)
+        if (d3n5f_form_smem(nbins, lmax, fp64, pl) <= smem_optin) return pl;
+    return 0;
 }
 
-cudaError_t launch_d3n5f(const D3n5Params& q, int fp64, int nchunk_prim, int chunk0, int ksplit, int ncat,
+int d3n5f_form_smem(int nbins, int lmax, int fp64, int lanes)
+{
+    return nbins * (lmax + 1) * (lmax + 1) * lanes * 2 * (fp64 ? 8 : 4);
+}
+
+namespace {
+
+template <typename T, int MODE, int PL>
+cudaError_t launch_form(const D3n5Params& q, int nchunk_prim, int chunk0, int ncat, cudaStream_t s)
+{
+    auto kern = k_d3n5_form<T, MODE, PL>;
+    const int fs = d3n5f_form_smem(q.nbins, q.lmax, sizeof(T) == 8, PL);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
+    if (e != cudaSuccess) return e;
+    // entry slices: about four CTAs per SM over the chunk's groups of PL primaries
+    const int ngrp = (q.npc + PL - 1) / PL;
+    const int nent = q.ngx * q.np12 + q.ngz * q.np34;
+    const int slices = std::max(1, std::min((4 * q.nsm + ngrp - 1) / ngrp, (nent + 255) / 256));
+    kern<<<dim3(ngrp, slices, ncat > 1 ? ncat : 1), kFormWarps * 32, fs, s>>>(q, chunk0, nchunk_prim);
+    ++launch_counter();
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_form_pl(const D3n5Params& q, int nchunk_prim, int chunk0, int ncat, cudaStream_t s)
+{
+    switch (q.form_lanes) {
+        case 32: return launch_form<T, MODE, 32>(q, nchunk_prim, chunk0, ncat, s);
+        case 16: return launch_form<T, MODE, 16>(q, nchunk_prim, chunk0, ncat, s);
+        case 8: return launch_form<T, MODE, 8>(q, nchunk_prim, chunk0, ncat, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+// mode 0: FP32, 1: FP64 (CUDA-core contraction); 2: split BF16 (tensor-core contraction, FP32 inputs)
+cudaError_t launch_d3n5f(const D3n5Params& q, int mode, int nchunk_prim, int chunk0, int ksplit, int ncat,
                          cudaStream_t s)
 {
-    const int fs = d3n5f_form_smem(q.nbins, q.lmax, fp64);
-    const dim3 fgrid(q.npc, ncat > 1 ? ncat : 1);
+    cudaError_t e;
     const dim3 cgrid(q.ntiles, ksplit, ncat > 1 ? ncat : 1);
-    if (fp64) {
-        k_d3n5_form<double><<<fgrid, kFormThreads, fs, s>>>(q, chunk0, nchunk_prim);
-        ++launch_counter();
-        k_d3n5_contract<double><<<cgrid, kConThreads, 0, s>>>(q, nchunk_prim);
+    if (mode == 1) {
+        if ((e = launch_form_pl<double, 0>(q, nchunk_prim, chunk0, ncat, s)) != cudaSuccess) return e;
+        k_d3n5_contract<double><<<cgrid, kConThreads, 0, s>>>(q);
+    } else if (mode == 0) {
+        if ((e = launch_form_pl<float, 0>(q, nchunk_prim, chunk0, ncat, s)) != cudaSuccess) return e;
+        k_d3n5_contract<float><<<cgrid, kConThreads, 0, s>>>(q);
     } else {
-        k_d3n5_form<float><<<fgrid, kFormThreads, fs, s>>>(q, chunk0, nchunk_prim);
-        ++launch_counter();
-        k_d3n5_contract<float><<<cgrid, kConThreads, 0, s>>>(q, nchunk_prim);
+        if ((e = launch_form_pl<float, 1>(q, nchunk_prim, chunk0, ncat, s)) != cudaSuccess) return e;
+        return launch_d3n5_contract_tc(q, ksplit, ncat, s);
     }
     ++launch_counter();
     return cudaGetLastError();

@@ -178,15 +178,26 @@ struct D3n5Params {
     const int4* tiles;           // (l12, first row, first column, 0): the 64 x 64 blocks that hold keys
     const int* lamidx;           // [l1][l2][l12][l3][l4] -> label-set index (or -1)
     const int* trikey;           // [b1][b2][b3] -> first key of the bin triple
-    void* xs;                    // scratch: X of the chunk (complex T)
+    int ntc;
+    const int4* tc_tiles;        // (l12, first row, first column, rows | columns << 16): the 128-row x
+                                 //   64-column blocks of one parity that hold keys (tensor-core path)
+    int kpiece;                  // tensor-core path: K elements per CTA (a multiple of 64)
+    int form_lanes;              // primaries per CTA of the formation kernel (32, 16 or 8)
+    int nsm;                     // SMs of the device (launch shapes)
+    void* xs;                    // scratch: X of the chunk (complex T, or four BF16 planes)
     void* zs;                    // scratch: Z of the chunk
     size_t xs_cat, zs_cat;       // complex elements per catalogue
     double* partial;             // (catalogue, ksplit) rows x 2 ncoeff
+    int* err;                    // error word: bit 2 = a bounded wait on the tensor core ran out
 };
 
-int d3n5f_form_smem(int nbins, int lmax, int fp64);
-cudaError_t launch_d3n5f(const D3n5Params& q, int fp64, int nchunk_prim, int chunk0, int ksplit, int ncat,
+int d3n5f_form_smem(int nbins, int lmax, int fp64, int lanes);
+int d3n5f_form_lanes(int nbins, int lmax, int fp64, int smem_optin);
+// mode 0: FP32, 1: FP64, 2: split-BF16 tensor-core contraction (FP32 a-array)
+cudaError_t launch_d3n5f(const D3n5Params& q, int mode, int nchunk_prim, int chunk0, int ksplit, int ncat,
                          cudaStream_t s);
+cudaError_t launch_d3n5_contract_tc(const D3n5Params& q, int npieces, int ncat, cudaStream_t s);
+int d3n5_tc_smem();
 
 // ------------------------------------------------------------- launchers
 // Each returns cudaSuccess or the launch error, and adds the kernels it

@@ -185,7 +185,8 @@ struct npcf_plan_s {
     DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil, d_task;
     // N=5: the factored coupling's tables (npcf_couple_d3n5f.cu) and its per-chunk scratch
     DevBuf d5_p12, d5_p34, d5_gx, d5_gz, d5_terms, d5_coef, d5_nlx, d5_nlz, d5_row0, d5_col0, d5_xrow, d5_zcol;
-    DevBuf d5_rowinfo, d5_colinfo, d5_xoff, d5_zoff, d5_tiles, d5_lamidx, d5_trikey, w_x5, w_z5;
+    DevBuf d5_rowinfo, d5_colinfo, d5_xoff, d5_zoff, d5_tiles, d5_tctiles, d5_lamidx, d5_trikey, w_x5, w_z5;
+    std::vector<int> d5_tc_k1;  // K per primary (2 l12 + 1) of each tensor-core tile
     D3n5Params d5{};           // host copy with the device table pointers (scratch set per call)
     int64_t d5_unit_x = 0, d5_unit_z = 0;  // complex scratch elements per primary of a chunk
     DevBuf d_los_lam, d_los_terms, d_los_coef;  // line-of-sight basis: term lists per label set
@@ -695,7 +696,7 @@ npcf_status build_d3n5f_tables(npcf_plan_s* P)
     }
     // rows (columns) of each l12 in (parity, b2, b1, ix) ((parity, b3, b4, iz)) order
     std::vector<int> nlx(NL), nlz(NL), row0(NL + 1), col0(NL + 1), xrow, zcol;
-    std::vector<int4> rowinfo, colinfo, tiles;
+    std::vector<int4> rowinfo, colinfo, tiles, tc_tiles;
     std::vector<long long> xoff(NL), zoff(NL);
     long long ux = 0, uz = 0;
     for (int l12 = 0; l12 < NL; ++l12) {
@@ -752,7 +753,25 @@ npcf_status build_d3n5f_tables(npcf_plan_s* P)
                 }
                 if (minb2[0] < maxb3[0] || minb2[1] < maxb3[1]) tiles.push_back(make_int4(l12, r0, c0, 0));
             }
+        // the tensor-core path: 128-row x 64-column blocks within one parity (rows and columns of a
+        // parity are contiguous in this order) that hold a key
+        for (int par = 0; par < 2; ++par) {
+            int ra = 0, rb = 0, ca = 0, cb = 0;
+            while (ra < nr && rowinfo[row0[l12] + ra].z != par) ++ra;
+            for (rb = ra; rb < nr && rowinfo[row0[l12] + rb].z == par;) ++rb;
+            while (ca < nc && colinfo[col0[l12] + ca].z != par) ++ca;
+            for (cb = ca; cb < nc && colinfo[col0[l12] + cb].z == par;) ++cb;
+            for (int r0 = ra; r0 < rb; r0 += 128)
+                for (int c0 = ca; c0 < cb; c0 += 64) {
+                    const int tr = std::min(128, rb - r0), tcn = std::min(64, cb - c0);
+                    // rows ascend in b2 and columns in b3: a key iff the first row's b2 < the last column's b3
+                    if (rowinfo[row0[l12] + r0].y < colinfo[col0[l12] + c0 + tcn - 1].x)
+                        tc_tiles.push_back(make_int4(l12, r0, c0, tr | (tcn << 16)));
+                }
+        }
     }
+    // longest K first (the CTAs of one launch are dealt in tile order)
+    std::stable_sort(tc_tiles.begin(), tc_tiles.end(), [](const int4& a, const int4& b) { return a.x > b.x; });
     row0[NL] = (int)rowinfo.size();
     col0[NL] = (int)colinfo.size();
     const int L1 = L + 1;
@@ -781,6 +800,7 @@ npcf_status build_d3n5f_tables(npcf_plan_s* P)
     CUDA_TRY(upload(P->d5_xoff, xoff));
     CUDA_TRY(upload(P->d5_zoff, zoff));
     CUDA_TRY(upload(P->d5_tiles, tiles));
+    CUDA_TRY(upload(P->d5_tctiles, tc_tiles));
     CUDA_TRY(upload(P->d5_lamidx, lamidx));
     CUDA_TRY(upload(P->d5_trikey, trikey));
     D3n5Params& q = P->d5;
@@ -812,29 +832,67 @@ npcf_status build_d3n5f_tables(npcf_plan_s* P)
     q.zoff = P->d5_zoff.as<long long>();
     q.ntiles = (int)tiles.size();
     q.tiles = P->d5_tiles.as<int4>();
+    q.ntc = (int)tc_tiles.size();
+    q.tc_tiles = P->d5_tctiles.as<int4>();
+    P->d5_tc_k1.clear();
+    for (const int4& t : tc_tiles) P->d5_tc_k1.push_back(2 * t.x + 1);
+    q.form_lanes = d3n5f_form_lanes(nb, L, P->fp64, P->smem_optin);
+    q.nsm = P->nsm;
     q.lamidx = P->d5_lamidx.as<int>();
     q.trikey = P->d5_trikey.as<int>();
     P->d5_unit_x = ux;
     P->d5_unit_z = uz;
-    if (d3n5f_form_smem(nb, L, P->fp64) > P->smem_optin)
+    if (q.form_lanes == 0)
         return fail(NPCF_ERR_UNSUPPORTED, "the 5PCF coupling needs more shared memory than available");
+    if (P->mixed && d3n5_tc_smem() > P->smem_optin)
+        return fail(NPCF_ERR_UNSUPPORTED, "the tensor-core 5PCF contraction needs %d bytes of shared memory",
+                    d3n5_tc_smem());
     return NPCF_OK;
 }
 
 // Primaries per chunk of the factored 5PCF coupling: its X and Z scratch near 64 MB (it stays in
-// L2 between the two kernels), a multiple of 16 in [16, 512].
+// L2 between the two kernels), a multiple of 64 (whole 64-element K stages of the tensor-core
+// contraction) in [64, 512].
 int d3n5f_chunk(const npcf_plan_s* P, size_t budget = 0)
 {
     if (budget == 0 && P->d5_npc > 0) return P->d5_npc;  // the autotuner's choice
     if (budget == 0) budget = size_t(64) << 20;
     const size_t per = (size_t)(P->d5_unit_x + P->d5_unit_z) * 2 * (P->fp64 ? 8 : 4);
     const size_t c = budget / std::max<size_t>(per, 1);
-    return (int)std::max<size_t>(16, std::min<size_t>(512, c / 16 * 16));
+    return (int)std::max<size_t>(64, std::min<size_t>(512, c / 64 * 64));
 }
 
-// The partial rows (K slices) of the factored 5PCF coupling: about two CTAs per SM over its tiles.
+bool d5_tc(const npcf_plan_s* P) { return P->N == 5 && P->mixed == 1; }
+
+// Tensor-core 5PCF contraction: K elements per CTA (a multiple of 64).  One CTA fits an SM, so a
+// launch takes ceil(pieces / SMs) waves of at most kpiece K each; the choice minimises
+// waves x (kpiece + 128), the 128 standing for a CTA's fixed cost (its epilogue and pipeline fill).
+int d3n5f_kpiece(const npcf_plan_s* P, int npc)
+{
+    int kmax = 1;
+    for (int k1 : P->d5_tc_k1) kmax = std::max(kmax, k1);
+    const int64_t nsm = std::max(P->nsm, 1);
+    int best = 64;
+    int64_t best_cost = (int64_t)1 << 62;
+    for (int kp = 64; kp <= npc * kmax; kp += 64) {
+        int64_t pieces = 0;
+        for (int k1 : P->d5_tc_k1) pieces += ((int64_t)npc * k1 + kp - 1) / kp;
+        const int64_t cost = (pieces + nsm - 1) / nsm * (kp + 128);
+        if (cost < best_cost) best_cost = cost, best = kp;
+    }
+    return best;
+}
+
+// The partial rows (K slices) of the factored 5PCF coupling: about two CTAs per SM over its tiles
+// (CUDA cores); the most K pieces of a tile (tensor cores).
 int d3n5f_ksplit(const npcf_plan_s* P, int npc)
 {
+    if (d5_tc(P)) {
+        int kmax = 1;
+        for (int k1 : P->d5_tc_k1) kmax = std::max(kmax, k1);
+        const int kp = d3n5f_kpiece(P, npc);
+        return (int)(((int64_t)npc * kmax + kp - 1) / kp);
+    }
     return std::max(1, std::min(npc / 8, (2 * P->nsm + P->d5.ntiles - 1) / std::max(P->d5.ntiles, 1)));
 }
 
@@ -842,10 +900,13 @@ int d3n5f_ksplit(const npcf_plan_s* P, int npc)
 // primaries the formation and the contraction kernels; partial rows [cat][ksplit].
 npcf_status run_d3n5f(npcf_plan_s* P, const void* a, const void* wprim, const int* nprim_dev, int64_t nprim_max,
                       const int* cat_first, const int* cat_count, int ncat, void* xs, void* zs, int npc, int ksplit,
-                      double* partial, cudaStream_t s)
+                      double* partial, int* err, cudaStream_t s)
 {
     D3n5Params q = P->d5;
     q.npc = npc;
+    q.err = err;
+    q.kpiece = d3n5f_kpiece(P, npc);
+    const int mode = d5_tc(P) ? 2 : (P->fp64 ? 1 : 0);
     q.a = a;
     q.wprim = wprim;
     q.nprim = nprim_dev;
@@ -858,7 +919,7 @@ npcf_status run_d3n5f(npcf_plan_s* P, const void* a, const void* wprim, const in
     q.partial = partial;
     for (int64_t c0 = 0; c0 < std::max<int64_t>(nprim_max, 1); c0 += npc) {
         const int nc = (int)std::min<int64_t>(npc, std::max<int64_t>(nprim_max - c0, 0));
-        cudaError_t e = launch_d3n5f(q, P->fp64, nc, (int)c0, ksplit, ncat, s);
+        cudaError_t e = launch_d3n5f(q, mode, nc, (int)c0, ksplit, ncat, s);
         if (e != cudaSuccess) return fail(NPCF_ERR_CUDA, "5PCF coupling launch: %s", cudaGetErrorString(e));
     }
     return NPCF_OK;
@@ -1214,7 +1275,7 @@ npcf_status plan_coupling(npcf_plan_s* P, CoupleParams kp, int* err, int rows, i
     cudaError_t e;
     if (P->N == 5)
         return run_d3n5f(P, kp.a, kp.wprim, kp.nprim, nprim_max, kp.cat_first, kp.cat_count, kp.ncat, xs, zs, npc,
-                         rows, kp.partial, s);
+                         rows, kp.partial, err, s);
     if (tc_coupling(P))
         e = launch_couple_d2n4_tc(kp, P->mixed == 2, rows, tc_groups(P),
                                   couple_tc_smem(P->nbins, P->nq, P->mixed == 2), s);
@@ -1938,8 +1999,8 @@ npcf_status autotune(npcf_plan_s* P, const void* pos, const void* w, int64_t n, 
     int which;
     if (P->N == 5) {
         const int c0 = d3n5f_chunk(P, size_t(64) << 20);
-        cand[0] = std::max(16, c0 / 4 / 16 * 16);
-        cand[1] = std::max(16, c0 / 2 / 16 * 16);
+        cand[0] = std::max(64, c0 / 4 / 64 * 64);
+        cand[1] = std::max(64, c0 / 2 / 64 * 64);
         cand[2] = c0;
         cand[3] = std::min(1024, c0 * 2);
         which = 2;
@@ -2033,9 +2094,11 @@ npcf_status npcf_plan_create(npcf_plan_t* out, int D, int N, int lmax, const dou
         o.precision != NPCF_MIXED_TF32X3)
         return fail(NPCF_ERR_ARG, "bad precision");
     const bool mixed = o.precision == NPCF_MIXED_BF16X3 || o.precision == NPCF_MIXED_TF32X3;
-    if (mixed && !(D == 2 && N == 4))
-        return fail(NPCF_ERR_UNSUPPORTED, "the split-precision tensor-core coupling is provided for the D=2 4PCF");
-    if (mixed && (nbins - 1) * (nbins - 2) / 2 > 128)
+    if (mixed && !(D == 2 && N == 4) && !(D == 3 && N == 5 && o.precision == NPCF_MIXED_BF16X3))
+        return fail(NPCF_ERR_UNSUPPORTED,
+                    "the split-precision tensor-core coupling is provided for the D=2 4PCF (BF16x3, TF32x3) and the "
+                    "D=3 5PCF (BF16x3)");
+    if (mixed && N == 4 && (nbins - 1) * (nbins - 2) / 2 > 128)
         return fail(NPCF_ERR_UNSUPPORTED, "the tensor-core D=2 4PCF coupling takes at most 17 bins");
     if (o.bin_order != NPCF_BINS_LE && o.bin_order != NPCF_BINS_LT) return fail(NPCF_ERR_ARG, "bad bin_order");
     if (o.remove_self != 0 && o.remove_self != 1) return fail(NPCF_ERR_ARG, "remove_self must be 0 or 1");
@@ -2331,7 +2394,7 @@ void npcf_plan_destroy(npcf_plan_t P)
                       &P->b_offsets, &P->b_first, &P->b_count, &P->b_scales, &P->b_stencil,
                       &P->d5_p12,  &P->d5_p34, &P->d5_gx,  &P->d5_gz, &P->d5_terms, &P->d5_coef, &P->d5_nlx,
                       &P->d5_nlz,  &P->d5_row0, &P->d5_col0, &P->d5_xrow, &P->d5_zcol, &P->d5_rowinfo,
-                      &P->d5_colinfo, &P->d5_xoff, &P->d5_zoff, &P->d5_tiles, &P->d5_lamidx, &P->d5_trikey,
+                      &P->d5_colinfo, &P->d5_xoff, &P->d5_zoff, &P->d5_tiles, &P->d5_tctiles, &P->d5_lamidx, &P->d5_trikey,
                       &P->w_x5,    &P->w_z5,
                       &P->d_colmap,  &P->d_selfc, &P->w_self, &P->d_los_lam, &P->d_los_terms, &P->d_los_coef,
                       &P->g_khat,  &P->g_xhat, &P->g_work, &P->g_cstate, &P->g_small};

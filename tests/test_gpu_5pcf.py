@@ -93,3 +93,73 @@ def test_5pcf_batched_matches_oracle():
         index = {tuple(int(x) for x in k): j for j, k in enumerate(keys)}
         ref = ref[np.array([index[tuple(int(x) for x in k)] for k in plan.keys()])]
         assert np.max(np.abs(got[i] - ref)) <= TOL64 * np.max(np.abs(ref))
+
+
+# ------------------------------------------------- split-precision tensor-core contraction
+MIX = "mixed_bf16x3"
+
+
+@pytest.mark.parametrize("lmax,nbins,n,prims", [(2, 5, 1000, (100, 260)), (3, 6, 1000, None), (4, 10, 1500, (0, 130)),
+                                                (1, 4, 300, (5, 9))])
+def test_5pcf_mixed_small_parity(lmax, nbins, n, prims):
+    """The BF16x3 contraction (X and Z written as hi + lo BF16 planes, three MMAs per product, FP32
+    accumulation in tensor memory) against the FP64 oracle at 1e-5 of the coefficient norm: several
+    chunks of 64 primaries with a partly filled last one, one chunk, and a catalogue of 4 bins (one
+    bin quadruple)."""
+    pos = np.concatenate([catalogs.uniform(n // 2, 3, 1.0, 71, fp32=True),
+                          catalogs.gaussian_blobs(n - n // 2, 3, 1.0, 6, 0.05, 72, fp32=True)])
+    w = catalogs.normal_weights(n, 1.0, 0.3, 73, fp32=True)
+    edges = np.linspace(0.05, 0.35, nbins + 1)
+    _compare(lmax, edges, np.ones(3), pos, w, MIX, primaries=prims)
+
+
+def test_5pcf_mixed_full_size_sampled():
+    """The paper's 5PCF example at full size (10^4 points, 10 bins, lmax 4), primaries [0, 40)."""
+    wl = catalogs.workload("d3n5")
+    _compare(wl.lmax, wl.edges, wl.box, wl.pos, wl.w, MIX, primaries=(0, 40))
+
+
+def test_5pcf_mixed_full_launch_matches_fp64():
+    """Every primary of the full-size example (the benchmark's launch): the BF16x3 tensor-core
+    contraction agrees with the FP64 GPU path (itself pinned to the oracle at 1e-10) to 1e-5 of the
+    coefficient norm, and so does the FP32 CUDA-core path; repeated calls are bitwise equal."""
+    wl = catalogs.workload("d3n5")
+    ref = _plan(wl.lmax, wl.edges, wl.box, "fp64").compute(torch.tensor(wl.pos, device="cuda"),
+                                                           torch.tensor(wl.w, device="cuda")).cpu().numpy()
+    pos = torch.tensor(wl.pos, dtype=torch.float32, device="cuda")
+    w = torch.tensor(wl.w, dtype=torch.float32, device="cuda")
+    for prec in ("fp32", MIX):
+        plan = _plan(wl.lmax, wl.edges, wl.box, prec)
+        z = plan.compute(pos, w).cpu().numpy()
+        assert np.linalg.norm(z - ref) <= TOL32 * np.linalg.norm(ref), prec
+        assert np.array_equal(z, plan.compute(pos, w).cpu().numpy()), prec
+
+
+def test_5pcf_mixed_batched_matches_oracle():
+    from paper_2106_10278_gb300.npcf import Plan
+
+    sizes = (400, 0, 700)
+    boxes = np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 1.0], [1.1, 0.9, 1.0]])
+    pos = np.concatenate([catalogs.uniform(n, 3, boxes[i], 80 + i, fp32=True) for i, n in enumerate(sizes)])
+    w = catalogs.normal_weights(len(pos), 1.0, 0.2, 85, fp32=True)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    edges = np.linspace(0.05, 0.35, 6)
+    plan = Plan(3, 5, 2, edges, np.ones(3), precision=MIX)
+    got = plan.compute_batched(torch.tensor(pos, dtype=torch.float32, device="cuda"),
+                               torch.tensor(w, dtype=torch.float32, device="cuda"), offsets, boxes).cpu().numpy()
+    for i in range(len(sizes)):
+        a, b = offsets[i], offsets[i + 1]
+        if a == b:
+            assert np.all(got[i] == 0)
+            continue
+        keys, ref = oracle.estimate(3, 5, 2, edges, boxes[i], pos[a:b], w[a:b])
+        index = {tuple(int(x) for x in k): j for j, k in enumerate(keys)}
+        ref = ref[np.array([index[tuple(int(x) for x in k)] for k in plan.keys()])]
+        assert np.linalg.norm(got[i] - ref) <= TOL32 * np.linalg.norm(ref)
+
+
+def test_5pcf_tf32_split_rejected():
+    from paper_2106_10278_gb300.npcf import NpcfError
+
+    with pytest.raises(NpcfError, match="UNSUPPORTED"):
+        _plan(2, np.linspace(0.05, 0.35, 6), np.ones(3), "mixed_tf32x3")
