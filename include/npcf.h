@@ -70,8 +70,10 @@ typedef enum {
  * the coupling (the contraction over primaries of eq. NPCF-estimator-discrete) on the
  * tensor cores: every FP32 operand x is split into hi + lo of BF16 (MIXED_BF16X3) or TF32
  * (MIXED_TF32X3) and a product is kept as hi*hi + hi*lo + lo*hi with FP32 accumulation over
- * spans of primaries and FP64 sums across spans.  Provided for the D=2 4PCF (at most 17
- * bins); other plans return NPCF_ERR_UNSUPPORTED for them. */
+ * spans of primaries and FP64 sums across spans.  Provided for the D=2 4PCF (both splits, at
+ * most 17 bins) and for the D=3 5PCF (MIXED_BF16X3: the contraction over (primary, m12) of
+ * the coupling factored through l12, FP32 accumulation over a piece of K of one chunk of
+ * primaries, FP64 across pieces and chunks); other plans return NPCF_ERR_UNSUPPORTED. */
 enum { NPCF_FP64 = 0, NPCF_FP32 = 1, NPCF_MIXED_BF16X3 = 2, NPCF_MIXED_TF32X3 = 3 };
 enum { NPCF_BINS_LE = 0, NPCF_BINS_LT = 1 };    /* npcf_opts.bin_order (N=3 only) */
 /* npcf_opts.parity: which components a plan returns, by their behaviour under r -> -r (the

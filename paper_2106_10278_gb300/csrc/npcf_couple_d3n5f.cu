@@ -78,27 +78,43 @@ __global__ void __launch_bounds__(kFormWarps * 32) k_d3n5_form(const D3n5Params 
     const int per = (nx + nz + gridDim.y - 1) / gridDim.y;
     const int e0 = blockIdx.y * per, e1 = min(nx + nz, e0 + per);  // entries: X then Z
     const T* abase = static_cast<const T*>(q.a);
-    for (int i = threadIdx.x; i < nb * S * PL; i += blockDim.x) {
-        const int pj = i % PL, bs = i / PL;
-        const int b = bs / S, s = bs - b * S;
-        const int jj = jj0 + pj, j = chunk0 + jj;
-        T re = T(0), im = T(0);
-        if (jj < nchunk_prim && j < nprim) {
-            int l = 0;
-            while ((l + 1) * (l + 1) <= s) ++l;
-            const int m = s - l * l - l, am = m < 0 ? -m : m;
-            const T* x = abase + (first + j) * (size_t)nb * q.nq + b * q.nq + q_index_d3(l, am);
-            re = x[0];
-            im = am > 0 ? x[1] : T(0);
-            if (m < 0) {  // a_{l,-m} = (-1)^m conj(a_{l m})
-                im = -im;
-                if (am & 1) {
-                    re = -re;
-                    im = -im;
-                }
+    // state s = l^2 + l + m -> its stored component q (m >= 0) and the signs of a_{l,-m} =
+    // (-1)^m conj(a_{l m}): bit 16 m != 0, bit 17 the real part flips, bit 18 the imaginary part
+    __shared__ int s_state[128];
+    for (int st = threadIdx.x; st < S; st += blockDim.x) {
+        int l = 0;
+        while ((l + 1) * (l + 1) <= st) ++l;
+        const int m = st - l * l - l, am = m < 0 ? -m : m;
+        const bool flip_re = m < 0 && (am & 1), flip_im = m < 0 && !(am & 1);
+        s_state[st] = q_index_d3(l, am) | (am > 0 ? 1 << 16 : 0) | (flip_re ? 1 << 17 : 0) | (flip_im ? 1 << 18 : 0);
+    }
+    __syncthreads();
+    // the a^b of the CTA's primaries, primary fastest (conflict-free stores); eight elements per
+    // thread and trip, their loads issued before any is used
+    constexpr int kU = 8;
+    const int ntot = nb * S * PL;
+    for (int i0 = threadIdx.x; i0 < ntot; i0 += kU * blockDim.x) {
+        T re[kU], im[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * blockDim.x;
+            re[u] = im[u] = T(0);
+            const int pj = i % PL, bs = i / PL;
+            const int jj = jj0 + pj, j = chunk0 + jj;
+            if (i < ntot && jj < nchunk_prim && j < nprim) {
+                const int b = bs / S, st = s_state[bs - b * S];
+                const T* x = abase + (first + j) * (size_t)nb * q.nq + b * q.nq + (st & 0xffff);
+                re[u] = x[0];
+                if (st & (1 << 16)) im[u] = x[1];
             }
         }
-        A[i] = C5<T>{re, im};
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= ntot) break;
+            const int bs = i / PL, st = s_state[bs % S];
+            A[i] = C5<T>{(st & (1 << 17)) ? -re[u] : re[u], (st & (1 << 18)) ? -im[u] : im[u]};
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pj = lane % PL, sub = lane / PL;

@@ -13,13 +13,14 @@
 // product.
 //
 // A CTA takes one tile (up to 128 rows x 64 columns of one parity that hold keys) and one piece of
-// its K (kpiece elements).  K goes through shared memory 64 elements at a time in the K-major
-// core-matrix layout (six 16 KB operand tiles per stage), copied with 16-byte cp.async from the
-// chunk's scratch in L2; two stages, the next one loading while the tensor core works on the
-// current.  One thread issues the 24 MMAs of a stage (M = 128, N = 128, K = 16 each) and commits
-// them to the stage's mbarrier; every wait on an mbarrier is bounded (error bit 2, then the CTA
-// waits for its MMAs in flight, frees its tensor memory and returns).  The epilogue reads D1 and
-// D2 back and adds the keys (b2 < b3) into the CTA's FP64 partial row (one row per K piece).
+// its K (kpiece elements).  K goes through shared memory 32 elements at a time in the K-major
+// core-matrix layout (six 8 KB operand tiles per stage), copied with 16-byte cp.async from the
+// chunk's scratch in L2; four stages, the loads running three stages ahead of the tensor core.
+// One thread issues the 12 MMAs of a stage (M = 128, N = 128, K = 16 each) and commits them to
+// the stage's mbarrier; every wait on an mbarrier is bounded (error bit 2, then the CTA waits for
+// its MMAs in flight, frees its tensor memory and returns).  The epilogue reads D1 and D2 back
+// and adds every (row, column) that is a key (b2 < b3; its index from the plan's table) into
+// the CTA's FP64 partial row (one row per K piece).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -31,11 +32,12 @@ namespace npcf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kKs = 64;                             // K elements per stage
-constexpr int kTileBytes = 128 * kKs * 2;           // one operand tile: 128 rows x 64 BF16
+constexpr int kKs = 32;                             // K elements per stage
+constexpr int kStages = 4;                          // stages in flight: loads run three ahead of the MMAs
+constexpr int kTileBytes = 128 * kKs * 2;           // one operand tile: 128 rows x 32 BF16
 constexpr int kStageBytes = 6 * kTileBytes;         // Re hi, Re lo, Im hi, Im lo of X; hi, lo of [Zr; Zi]
 constexpr int kHeader = 1024;
-constexpr int kSmem = kHeader + 2 * kStageBytes;
+constexpr int kSmem = kHeader + kStages * kStageBytes;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;    // 2 s
 constexpr int kErrTimeout = 4;
 
@@ -52,14 +54,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_d3n5_contract_tc(const D3n5Para
     const int k1 = min(Kr, k0 + q.kpiece);
     const int nst = (k1 - k0) / kKs;
 
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 16);
-    int* s_ok = reinterpret_cast<int*>(smem + 20);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);  // [kStages]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 64);
+    int* s_ok = reinterpret_cast<int*>(smem + 68);
     unsigned char* stage0 = smem + kHeader;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int i = 0; i < kStages; ++i) tc::mbar_init(&mbar[i], 1);
         tc::mbar_fence_init();
         *s_ok = 1;
     }
@@ -77,40 +78,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_d3n5_contract_tc(const D3n5Para
                              4 * (size_t)q.zoff[l12] * npc;
     const size_t xplane = (size_t)q.np12 * q.nlx[l12] * Kr, zplane = (size_t)q.np34 * q.nlz[l12] * Kr;
 
-    // 6 x 1024 16-byte pieces per stage: in each 32-piece group, 8 rows x 4 K chunks (the 8 rows
-    // of a core matrix fill all banks; the global side reads 64 contiguous bytes per row)
-    auto load = [&](int buf, int kk) {
-        unsigned char* st = stage0 + buf * kStageBytes;
-        for (int i = tid; i < 6 * 1024; i += kThreads) {
-            const int t = i >> 10, pc = i & 1023;
-            const int rest = pc >> 5;
-            const int row = (rest >> 1) * 8 + (pc & 7), ch = (rest & 1) * 4 + ((pc >> 3) & 3);
-            unsigned char* dst = st + t * kTileBytes + tc::tile_offset(row, ch * 16, kKs * 2);
-            const __nv_bfloat16* src;
-            bool valid;
-            if (t < 4) {  // X plane t, row r0 + row
-                valid = row < nr;
-                src = X + t * xplane + (size_t)(r0 + (valid ? row : 0)) * Kr + kk + ch * 8;
-            } else {      // [Zr; Zi] hi (t = 4) or lo (t = 5): operand row = part * 64 + column
-                const int part = row >> 6, col = row & 63;
-                valid = col < nc;
-                src = Z + (part * 2 + (t - 4)) * zplane + (size_t)(c0 + (valid ? col : 0)) * Kr + kk + ch * 8;
+    // one stage: 6 tiles x 512 16-byte pieces; in each 32-piece group 8 rows x 4 K chunks (the 8
+    // rows of a core matrix fill all banks; the global side reads 64 contiguous bytes per row).
+    // Every call commits one cp.async group, empty past the last stage, so that the group count
+    // stays in step with the stage count.
+    auto load = [&](int it) {
+        if (it < nst) {
+            unsigned char* st = stage0 + (it % kStages) * kStageBytes;
+            const int kk = k0 + it * kKs;
+            for (int i = tid; i < 6 * 512; i += kThreads) {
+                const int t = i >> 9, pc = i & 511;
+                const int row = (pc >> 5) * 8 + (pc & 7), ch = (pc >> 3) & 3;
+                unsigned char* dst = st + t * kTileBytes + tc::tile_offset(row, ch * 16, kKs * 2);
+                const __nv_bfloat16* src;
+                bool valid;
+                if (t < 4) {  // X plane t, row r0 + row
+                    valid = row < nr;
+                    src = X + t * xplane + (size_t)(r0 + (valid ? row : 0)) * Kr + kk + ch * 8;
+                } else {      // [Zr; Zi] hi (t = 4) or lo (t = 5): operand row = part * 64 + column
+                    const int part = row >> 6, col = row & 63;
+                    valid = col < nc;
+                    src = Z + (part * 2 + (t - 4)) * zplane + (size_t)(c0 + (valid ? col : 0)) * Kr + kk + ch * 8;
+                }
+                tc::cp_async16(dst, src, valid);
             }
-            tc::cp_async16(dst, src, valid);
         }
         tc::cp_async_commit();
     };
 
     const uint32_t id = tc::idesc(false, 128, 128);
     constexpr uint32_t sbo = (kKs * 2 / 16) * 128;
-    uint32_t committed[2] = {0u, 0u}, waited[2] = {0u, 0u};
+    int issued = 0, done = 0;  // MMA stages issued / known complete (thread 0)
     bool aborted = false;
-    load(0, k0);
+    for (int s = 0; s < kStages - 1; ++s) load(s);
     for (int it = 0; it < nst; ++it) {
-        const int b = it & 1;
-        tc::cp_async_wait<0>();
+        const int b = it % kStages;
+        tc::cp_async_wait<kStages - 2>();  // this thread's copies of stage `it` have landed
         tc::fence_smem_to_async();
-        __syncthreads();  // stage `it` is in shared memory
+        __syncthreads();                   // everyone's have
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t base = tc::smem_u32(stage0 + b * kStageBytes);
@@ -131,43 +136,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_d3n5_contract_tc(const D3n5Para
                 tc::mma<false>(tmem + 128, xil, bh, id, 1u);
             }
             tc::commit(&mbar[b]);
-            // the MMAs of the previous stage read the other buffer: done before it is refilled
-            if (waited[b ^ 1] < committed[b ^ 1]) {
-                if (tc::mbar_wait_bounded(&mbar[b ^ 1], waited[b ^ 1] & 1u, kWaitLimitNs)) waited[b ^ 1]++;
-                else *s_ok = 0;
+            issued = it + 1;
+            // the buffer the next load refills was read by the previous stage's MMAs
+            if (it >= 1) {
+                const int pv = it - 1;
+                if (tc::mbar_wait_bounded(&mbar[pv % kStages], (uint32_t)(pv / kStages) & 1u, kWaitLimitNs))
+                    done = it;
+                else
+                    *s_ok = 0;
             }
         }
-        committed[b]++;
         __syncthreads();
         if (!*s_ok) {
             aborted = true;
             break;
         }
-        if (it + 1 < nst) load(b ^ 1, k0 + (it + 1) * kKs);
+        load(it + kStages - 1);
     }
-    if (tid == 0) {  // every MMA done (after a timeout: bounded, then give up)
-        for (int s = 0; s < 2; ++s)
-            while (waited[s] < committed[s]) {
-                if (!tc::mbar_wait_bounded(&mbar[s], waited[s] & 1u, kWaitLimitNs)) {
-                    *s_ok = 0;
-                    break;
-                }
-                waited[s]++;
-            }
+    if (tid == 0 && issued > done) {  // the last stage's MMAs (in order: all before it too)
+        const int pv = issued - 1;
+        if (!tc::mbar_wait_bounded(&mbar[pv % kStages], (uint32_t)(pv / kStages) & 1u, kWaitLimitNs)) *s_ok = 0;
         if (!*s_ok) atomicOr(q.err, kErrTimeout);
     }
     tc::cp_async_wait<0>();
     __syncthreads();
     tc::fence_after_sync();
     if (!aborted && *s_ok) {
-        // warps w and w + 4 read TMEM lanes 32 (w % 4) ..: rows; columns 0..31 or 32..63 of the tile
+        // warps w and w + 4 read TMEM lanes 32 (w % 4) ..: rows; columns 0..31 or 32..63 of the tile;
+        // the key of every (row, column) comes from the plan's table (-1: b2 >= b3)
         const int wq = warp & 3, half = warp >> 2;
         const int r = 32 * wq + lane;
-        const bool rv = r < nr;
-        int4 R = make_int4(0, 0, 0, 0);
-        if (rv) R = q.rowinfo[q.row0[l12] + r0 + r];  // b1, b2, parity, l1 | l2 << 8
-        const int L1 = q.lmax + 1;
-        const int l1 = R.w & 0xff, l2 = R.w >> 8;
+        const int* tk = q.tc_keys + (size_t)blockIdx.x * 64 * 128 + r;
         double* prow = q.partial + ((size_t)cat * npieces + piece) * 2 * q.ncoeff;
         const uint32_t ta = tmem + ((uint32_t)(32 * wq) << 16);
         for (int cc = 0; cc < 2; ++cc) {
@@ -177,19 +176,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_d3n5_contract_tc(const D3n5Para
             tc::tmem_ld16(ta + 64 + cb, xrzi);
             tc::tmem_ld16(ta + 128 + cb, xizr);
             tc::tmem_ld16(ta + 192 + cb, xizi);
-            if (!rv) continue;
+            int key[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) key[i] = tk[(cb + i) * 128];  // coalesced over the rows
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const int c = cb + i;
-                if (c >= nc) break;
-                const int4 C = q.colinfo[q.col0[l12] + c0 + c];  // b3, b4, parity, l3 | l4 << 8
-                if (R.y >= C.x) continue;
-                const int l3 = C.w & 0xff, l4 = C.w >> 8;
-                const int lam = q.lamidx[(((l1 * L1 + l2) * (2 * L1 - 1) + l12) * L1 + l3) * L1 + l4];
-                const int key =
-                    q.trikey[(R.x * q.nbins + R.y) * q.nbins + C.x] + (C.y - C.x - 1) * q.nlam + lam;
-                prow[2 * key] += (double)(xrzr[i] - xizi[i]);
-                prow[2 * key + 1] += (double)(xrzi[i] + xizr[i]);
+                if (key[i] < 0) continue;
+                prow[2 * key[i]] += (double)(xrzr[i] - xizi[i]);
+                prow[2 * key[i] + 1] += (double)(xrzi[i] + xizr[i]);
             }
         }
     }

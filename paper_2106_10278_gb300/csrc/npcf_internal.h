@@ -181,6 +181,7 @@ struct D3n5Params {
     int ntc;
     const int4* tc_tiles;        // (l12, first row, first column, rows | columns << 16): the 128-row x
                                  //   64-column blocks of one parity that hold keys (tensor-core path)
+    const int* tc_keys;          // [tile][64 columns][128 rows]: the key of each entry, -1 if none
     int kpiece;                  // tensor-core path: K elements per CTA (a multiple of 64)
     int form_lanes;              // primaries per CTA of the formation kernel (32, 16 or 8)
     int nsm;                     // SMs of the device (launch shapes)

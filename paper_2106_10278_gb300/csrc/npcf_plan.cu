@@ -185,7 +185,7 @@ struct npcf_plan_s {
     DevBuf d_tab, d_qnorm, d_invvb, d_pairs, d_pair_key, d_kblocks, d_lam2, d_lamodd, d_pref, d_stencil, d_task;
     // N=5: the factored coupling's tables (npcf_couple_d3n5f.cu) and its per-chunk scratch
     DevBuf d5_p12, d5_p34, d5_gx, d5_gz, d5_terms, d5_coef, d5_nlx, d5_nlz, d5_row0, d5_col0, d5_xrow, d5_zcol;
-    DevBuf d5_rowinfo, d5_colinfo, d5_xoff, d5_zoff, d5_tiles, d5_tctiles, d5_lamidx, d5_trikey, w_x5, w_z5;
+    DevBuf d5_rowinfo, d5_colinfo, d5_xoff, d5_zoff, d5_tiles, d5_tctiles, d5_tckeys, d5_lamidx, d5_trikey, w_x5, w_z5;
     std::vector<int> d5_tc_k1;  // K per primary (2 l12 + 1) of each tensor-core tile
     D3n5Params d5{};           // host copy with the device table pointers (scratch set per call)
     int64_t d5_unit_x = 0, d5_unit_z = 0;  // complex scratch elements per primary of a chunk
@@ -782,6 +782,24 @@ npcf_status build_d3n5f_tables(npcf_plan_s* P)
     }
     std::vector<int> trikey((size_t)nb * nb * nb, -1);
     for (const int4& t : P->triples) trikey[((size_t)t.x * nb + t.y) * nb + t.z] = t.w;
+    // the key of every entry of every tensor-core tile, column-major ([tile][column][row]), -1 where
+    // b2 >= b3 or outside the tile
+    std::vector<int> tc_keys(tc_tiles.size() * 64 * 128, -1);
+    for (size_t t = 0; t < tc_tiles.size(); ++t) {
+        const int4 T = tc_tiles[t];
+        const int l12 = T.x, tr = T.w & 0xffff, tcn = T.w >> 16;
+        for (int c = 0; c < tcn; ++c)
+            for (int r = 0; r < tr; ++r) {
+                const int4 R = rowinfo[row0[l12] + T.y + r], C = colinfo[col0[l12] + T.z + c];
+                if (R.y >= C.x) continue;
+                const int lam = lamidx[((((size_t)(R.w & 0xff) * L1 + (R.w >> 8)) * NL + l12) * L1 + (C.w & 0xff)) * L1 +
+                                       (C.w >> 8)];
+                const int tk = trikey[((size_t)R.x * nb + R.y) * nb + C.x];
+                if (lam < 0 || tk < 0) return fail(NPCF_ERR_UNSUPPORTED, "5PCF key table: missing key");
+                tc_keys[(t * 64 + c) * 128 + r] = tk + (C.y - C.x - 1) * P->nlam + lam;
+            }
+    }
+    CUDA_TRY(upload(P->d5_tckeys, tc_keys));
     CUDA_TRY(upload(P->d5_p12, p12));
     CUDA_TRY(upload(P->d5_p34, p34));
     CUDA_TRY(upload(P->d5_gx, gx));
@@ -834,6 +852,7 @@ npcf_status build_d3n5f_tables(npcf_plan_s* P)
     q.tiles = P->d5_tiles.as<int4>();
     q.ntc = (int)tc_tiles.size();
     q.tc_tiles = P->d5_tctiles.as<int4>();
+    q.tc_keys = P->d5_tckeys.as<int>();
     P->d5_tc_k1.clear();
     for (const int4& t : tc_tiles) P->d5_tc_k1.push_back(2 * t.x + 1);
     q.form_lanes = d3n5f_form_lanes(nb, L, P->fp64, P->smem_optin);
@@ -2394,7 +2413,7 @@ void npcf_plan_destroy(npcf_plan_t P)
                       &P->b_offsets, &P->b_first, &P->b_count, &P->b_scales, &P->b_stencil,
                       &P->d5_p12,  &P->d5_p34, &P->d5_gx,  &P->d5_gz, &P->d5_terms, &P->d5_coef, &P->d5_nlx,
                       &P->d5_nlz,  &P->d5_row0, &P->d5_col0, &P->d5_xrow, &P->d5_zcol, &P->d5_rowinfo,
-                      &P->d5_colinfo, &P->d5_xoff, &P->d5_zoff, &P->d5_tiles, &P->d5_tctiles, &P->d5_lamidx, &P->d5_trikey,
+                      &P->d5_colinfo, &P->d5_xoff, &P->d5_zoff, &P->d5_tiles, &P->d5_tctiles, &P->d5_tckeys, &P->d5_lamidx, &P->d5_trikey,
                       &P->w_x5,    &P->w_z5,
                       &P->d_colmap,  &P->d_selfc, &P->w_self, &P->d_los_lam, &P->d_los_terms, &P->d_los_coef,
                       &P->g_khat,  &P->g_xhat, &P->g_work, &P->g_cstate, &P->g_small};
