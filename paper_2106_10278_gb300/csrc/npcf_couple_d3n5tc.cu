@@ -13,10 +13,12 @@
 // product.
 //
 // A CTA takes one tile (up to 128 rows x 64 columns of one parity that hold keys) and one piece of
-// its K (kpiece elements).  K goes through shared memory 32 elements at a time in the K-major
-// core-matrix layout (six 8 KB operand tiles per stage), copied with 16-byte cp.async from the
-// chunk's scratch in L2; four stages, the loads running three stages ahead of the tensor core.
-// One thread issues the 12 MMAs of a stage (M = 128, N = 128, K = 16 each) and commits them to
+// its K (kpiece elements).  K goes through shared memory 16 elements at a time in the K-major
+// core-matrix layout (six 4 KB operand tiles per stage), copied with 16-byte cp.async from the
+// chunk's scratch in L2; four stages, the loads running three stages ahead of the tensor core,
+// 97 KB of shared memory and 256 TMEM columns, so two CTAs share an SM (one's loads and
+// epilogue overlap the other's MMAs).
+// One thread issues the 6 MMAs of a stage (M = 128, N = 128, K = 16 each) and commits them to
 // the stage's mbarrier; every wait on an mbarrier is bounded (error bit 2, then the CTA waits for
 // its MMAs in flight, frees its tensor memory and returns).  The epilogue reads D1 and D2 back
 // and adds every (row, column) that is a key (b2 < b3; its index from the plan's table) into
@@ -32,16 +34,16 @@ namespace npcf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kKs = 32;                             // K elements per stage
+constexpr int kKs = 16;                             // K elements per stage (one MMA K step)
 constexpr int kStages = 4;                          // stages in flight: loads run three ahead of the MMAs
-constexpr int kTileBytes = 128 * kKs * 2;           // one operand tile: 128 rows x 32 BF16
+constexpr int kTileBytes = 128 * kKs * 2;           // one operand tile: 128 rows x 16 BF16
 constexpr int kStageBytes = 6 * kTileBytes;         // Re hi, Re lo, Im hi, Im lo of X; hi, lo of [Zr; Zi]
 constexpr int kHeader = 1024;
 constexpr int kSmem = kHeader + kStages * kStageBytes;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;    // 2 s
 constexpr int kErrTimeout = 4;
 
-__global__ void __launch_bounds__(kThreads, 1) k_d3n5_contract_tc(const D3n5Params q, int npieces)
+__global__ void __launch_bounds__(kThreads, 2) k_d3n5_contract_tc(const D3n5Params q, int npieces)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int4 tile = q.tc_tiles[blockIdx.x];
@@ -78,17 +80,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_d3n5_contract_tc(const D3n5Para
                              4 * (size_t)q.zoff[l12] * npc;
     const size_t xplane = (size_t)q.np12 * q.nlx[l12] * Kr, zplane = (size_t)q.np34 * q.nlz[l12] * Kr;
 
-    // one stage: 6 tiles x 512 16-byte pieces; in each 32-piece group 8 rows x 4 K chunks (the 8
-    // rows of a core matrix fill all banks; the global side reads 64 contiguous bytes per row).
+    // one stage: 6 tiles x 256 16-byte pieces; in each 32-piece group 2 x 8 rows x 2 K chunks (the
+    // 8 rows of a core matrix fill all banks; the global side reads 32 contiguous bytes per row).
     // Every call commits one cp.async group, empty past the last stage, so that the group count
     // stays in step with the stage count.
     auto load = [&](int it) {
         if (it < nst) {
             unsigned char* st = stage0 + (it % kStages) * kStageBytes;
             const int kk = k0 + it * kKs;
-            for (int i = tid; i < 6 * 512; i += kThreads) {
-                const int t = i >> 9, pc = i & 511;
-                const int row = (pc >> 5) * 8 + (pc & 7), ch = (pc >> 3) & 3;
+            for (int i = tid; i < 6 * 256; i += kThreads) {
+                const int t = i >> 8, pc = i & 255;
+                const int row = (pc >> 4) * 8 + (pc & 7), ch = (pc >> 3) & 1;
                 unsigned char* dst = st + t * kTileBytes + tc::tile_offset(row, ch * 16, kKs * 2);
                 const __nv_bfloat16* src;
                 bool valid;

@@ -883,14 +883,14 @@ int d3n5f_chunk(const npcf_plan_s* P, size_t budget = 0)
 
 bool d5_tc(const npcf_plan_s* P) { return P->N == 5 && P->mixed == 1; }
 
-// Tensor-core 5PCF contraction: K elements per CTA (a multiple of 64).  One CTA fits an SM, so a
-// launch takes ceil(pieces / SMs) waves of at most kpiece K each; the choice minimises
+// Tensor-core 5PCF contraction: K elements per CTA (a multiple of 64).  Two CTAs fit an SM, so a
+// launch takes ceil(pieces / (2 SMs)) waves of at most kpiece K each; the choice minimises
 // waves x (kpiece + 128), the 128 standing for a CTA's fixed cost (its epilogue and pipeline fill).
 int d3n5f_kpiece(const npcf_plan_s* P, int npc)
 {
     int kmax = 1;
     for (int k1 : P->d5_tc_k1) kmax = std::max(kmax, k1);
-    const int64_t nsm = std::max(P->nsm, 1);
+    const int64_t nsm = 2 * std::max(P->nsm, 1);  // CTA slots: two per SM
     int best = 64;
     int64_t best_cost = (int64_t)1 << 62;
     for (int kp = 64; kp <= npc * kmax; kp += 64) {
