@@ -6,16 +6,16 @@
 //     X_j = sum_{m1} <l1 m1 l2 m12-m1|l12 m12> a^{b1}_{l1 m1} a^{b2}_{l2, m12-m1},
 //     Z_j = sum_{m3} <l12 m12 l3 m3|l4 M><l4 M l4 -M|0 0> a^{b3}_{l3 m3} a^{b4}_{l4, -M}.
 // For one l12 the sum over (j, m12) is a matrix product: rows (b1 < b2, l1, l2), columns
-// (b3 < b4, l3, l4), K = (primary, m12).  Only blocks with b2 < b3 and l1 + l2 + l3 + l4 even
+// (b3 < b4, l3, l4), K = (m12, primary).  Only blocks with b2 < b3 and l1 + l2 + l3 + l4 even
 // are keys, so rows are ordered by (parity, b2) and columns by (parity, b3), and only tiles that
 // hold keys are computed.
 //
 // Per chunk of primaries: k_d3n5_form writes X (times w_j) and Z of each primary into a scratch
-// laid out K-contiguous per row (the chunk's X and Z stay in L2 for the contraction);
-// k_d3n5_contract runs the tiles, a 64 x 64 complex block per CTA with 4 x 4 per thread (rows
-// ty + 16 a, columns tx + 16 b),
-// K staged through shared memory, FP32 (or FP64) sums over the CTA's primaries added into its
-// FP64 partial row.
+// laid out K-contiguous per row (the chunk's X and Z stay in L2 for the contraction), as complex
+// T or, for the tensor-core contraction (npcf_couple_d3n5tc.cu), as four BF16 planes;
+// k_d3n5_contract runs the tiles on the CUDA cores, a 64 x 64 complex block of one parity per
+// CTA with 4 x 4 per thread (rows ty + 16 a, columns tx + 16 b), K staged through shared memory,
+// FP32 (or FP64) sums over the CTA's slice of K added into its FP64 partial row.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -179,12 +179,11 @@ __global__ void __launch_bounds__(kConThreads) k_d3n5_contract(const D3n5Params 
 {
     __shared__ C5<T> Xs[kKc][kTile + 1];
     __shared__ C5<T> Zs[kKc][kTile + 1];
-    const int4 tile = q.tiles[blockIdx.x];  // l12, first row, first column, -
+    const int4 tile = q.tiles[blockIdx.x];  // l12, first row, first column, rows | columns << 16
     const int l12 = tile.x, K1 = 2 * l12 + 1;
-    const int nrows = min(kTile, q.nlx[l12] * q.np12 - tile.y);
-    const int ncols = min(kTile, q.nlz[l12] * q.np34 - tile.z);
-    // rows and columns are in (parity, b2) and (parity, b3) order: row r and column c meet in a key
-    // when b2 < b3 and the parities agree
+    const int nrows = tile.w & 0xffff, ncols = tile.w >> 16;
+    // rows and columns of one parity, in (parity, b2) and (parity, b3) order: row r and column c
+    // meet in a key when b2 < b3
     const int cat = blockIdx.z;
     const C5<T>* X = static_cast<const C5<T>*>(q.xs) + (size_t)cat * q.xs_cat + (size_t)q.xoff[l12] * q.npc;
     const C5<T>* Z = static_cast<const C5<T>*>(q.zs) + (size_t)cat * q.zs_cat + (size_t)q.zoff[l12] * q.npc;
@@ -236,7 +235,7 @@ __global__ void __launch_bounds__(kConThreads) k_d3n5_contract(const D3n5Params 
             const int c = tx + 16 * b;
             if (c >= ncols) continue;
             const int4 C = q.colinfo[q.col0[l12] + tile.z + c];  // b3, b4, parity, l3 | l4 << 8
-            if (R.y >= C.x || R.z != C.z) continue;
+            if (R.y >= C.x) continue;
             const int L1 = q.lmax + 1;
             const int l1 = R.w & 0xff, l2 = R.w >> 8, l3 = C.w & 0xff, l4 = C.w >> 8;
             const int lam = q.lamidx[(((l1 * L1 + l2) * (2 * L1 - 1) + l12) * L1 + l3) * L1 + l4];

@@ -175,7 +175,8 @@ struct D3n5Params {
     const long long* xoff;       // per l12: first element of its X block in the scratch, per primary of a
     const long long* zoff;       //   chunk (complex elements; the block starts at xoff[l12] * npc)
     int ntiles;
-    const int4* tiles;           // (l12, first row, first column, 0): the 64 x 64 blocks that hold keys
+    const int4* tiles;           // (l12, first row, first column, rows | columns << 16): the 64 x 64
+                                 //   blocks of one parity that hold keys (CUDA-core contraction)
     const int* lamidx;           // [l1][l2][l12][l3][l4] -> label-set index (or -1)
     const int* trikey;           // [b1][b2][b3] -> first key of the bin triple
     int ntc;

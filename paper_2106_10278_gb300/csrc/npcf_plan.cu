@@ -739,28 +739,22 @@ npcf_status build_d3n5f_tables(npcf_plan_s* P)
         zoff[l12] = uz;
         ux += (long long)nr * (2 * l12 + 1);
         uz += (long long)nc * (2 * l12 + 1);
-        // 64 x 64 tiles that hold a key: some row and column of one parity with b2 < b3
-        for (int r0 = 0; r0 < nr; r0 += 64)
-            for (int c0 = 0; c0 < nc; c0 += 64) {
-                int minb2[2] = {1 << 30, 1 << 30}, maxb3[2] = {-1, -1};
-                for (int k = r0; k < std::min(nr, r0 + 64); ++k) {
-                    const int4 R = rowinfo[row0[l12] + k];
-                    minb2[R.z] = std::min(minb2[R.z], R.y);
-                }
-                for (int k = c0; k < std::min(nc, c0 + 64); ++k) {
-                    const int4 C = colinfo[col0[l12] + k];
-                    maxb3[C.z] = std::max(maxb3[C.z], C.x);
-                }
-                if (minb2[0] < maxb3[0] || minb2[1] < maxb3[1]) tiles.push_back(make_int4(l12, r0, c0, 0));
-            }
-        // the tensor-core path: 128-row x 64-column blocks within one parity (rows and columns of a
-        // parity are contiguous in this order) that hold a key
+        // blocks within one parity (rows and columns of a parity are contiguous in this order)
+        // that hold a key: 64 x 64 for the CUDA-core contraction, 128 rows x 64 columns for the
+        // tensor-core path
         for (int par = 0; par < 2; ++par) {
             int ra = 0, rb = 0, ca = 0, cb = 0;
             while (ra < nr && rowinfo[row0[l12] + ra].z != par) ++ra;
             for (rb = ra; rb < nr && rowinfo[row0[l12] + rb].z == par;) ++rb;
             while (ca < nc && colinfo[col0[l12] + ca].z != par) ++ca;
             for (cb = ca; cb < nc && colinfo[col0[l12] + cb].z == par;) ++cb;
+            for (int r0 = ra; r0 < rb; r0 += 64)
+                for (int c0 = ca; c0 < cb; c0 += 64) {
+                    const int tr = std::min(64, rb - r0), tcn = std::min(64, cb - c0);
+                    // rows ascend in b2 and columns in b3: a key iff the first row's b2 < the last column's b3
+                    if (rowinfo[row0[l12] + r0].y < colinfo[col0[l12] + c0 + tcn - 1].x)
+                        tiles.push_back(make_int4(l12, r0, c0, tr | (tcn << 16)));
+                }
             for (int r0 = ra; r0 < rb; r0 += 128)
                 for (int c0 = ca; c0 < cb; c0 += 64) {
                     const int tr = std::min(128, rb - r0), tcn = std::min(64, cb - c0);
