@@ -472,16 +472,28 @@ __device__ __forceinline__ void pair_batch_flush(Rec<D, T>* recs, const unsigned
     // last NQ - 32 components and the w^2 sums are shared out over (bin, component).
     constexpr int QA = NQ < 32 ? NQ : 32;  // components merged lane-parallel
     constexpr int QB = NQ + 1 - QA;         // the rest (w^2 last)
+    // two bins per step, so that their dependent shared-memory sums overlap (each bin's sum keeps
+    // its lane order)
     unsigned bm = E;                        // bins with a segment
     while (bm) {
-        const int b = __ffs(bm) - 1;
+        const int b0 = __ffs(bm) - 1;
         bm &= bm - 1;
-        const int f = __shfl_sync(full, first, b), n = __shfl_sync(full, nl, b);
+        const int b1 = bm ? __ffs(bm) - 1 : b0;
+        const bool two = bm != 0;
+        bm &= bm - 1;
+        const int f0 = __shfl_sync(full, first, b0), n0 = __shfl_sync(full, nl, b0);
+        const int f1 = __shfl_sync(full, first, b1), n1 = two ? __shfl_sync(full, nl, b1) : 0;
         if (lane < QA) {
-            const T* col = scr + f * (NQ + 1) + lane;
-            T sum = col[0];
-            for (int l = 1; l < n; ++l) sum += col[l * (NQ + 1)];
-            acc_s[b * NQ + lane] += sum;
+            const T* c0 = scr + f0 * (NQ + 1) + lane;
+            const T* c1 = scr + f1 * (NQ + 1) + lane;
+            T s0 = c0[0], s1 = c1[0];
+            const int nmax = n0 > n1 ? n0 : n1;
+            for (int l = 1; l < nmax; ++l) {
+                if (l < n0) s0 += c0[l * (NQ + 1)];
+                if (l < n1) s1 += c1[l * (NQ + 1)];
+            }
+            acc_s[b0 * NQ + lane] += s0;
+            if (two) acc_s[b1 * NQ + lane] += s1;
         }
     }
     for (int o = lane; o < nbins * QB; o += 32) {
