@@ -650,25 +650,32 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
-def d3n5_tc_k1_sum(lmax, nbins):
-    """Sum over the tiles of the tensor-core 5PCF contraction of K per primary (2 l12 + 1): the
-    tiles are 128 rows x 64 columns of one parity, rows (b1 < b2, l1, l2) in (parity, b2, b1) order
-    and columns (b3 < b4, l3, l4) in (parity, b3, b4) order, kept when some row's b2 is below some
-    column's b3 (the plan's own tiling, restated)."""
+def d3n5_tc_tiles(lmax, nbins):
+    """The tiles of the tensor-core 5PCF contraction, as (l12, rows, columns): 128 rows x 64
+    columns of one parity, rows (b2, b1, label pair) of the bin pairs b1 < b2 and label pairs
+    (l1, l2) that couple to l12, columns (b3, b4, label pair) likewise for (l3, l4), each in
+    ascending order; a tile is kept when its first row's b2 is below its last column's b3 (the
+    plan's own tiling, restated)."""
     p12 = [(b1, b2) for b2 in range(1, nbins - 2) for b1 in range(b2)]
     p34 = [(b3, b4) for b3 in range(2, nbins - 1) for b4 in range(b3 + 1, nbins)]
-    total = 0
+    tiles = []
     for l12 in range(2 * lmax + 1):
         lx = [(a, b) for a in range(lmax + 1) for b in range(lmax + 1) if abs(a - b) <= l12 <= a + b]
         lz = [(a, b) for a in range(lmax + 1) for b in range(lmax + 1) if abs(l12 - a) <= b <= l12 + a]
         for par in (0, 1):
-            rows = sorted((p[1], p[0], i) for p in p12 for i, (a, b) in enumerate(lx) if (a + b) % 2 == par)
-            cols = sorted((p[0], p[1], i) for p in p34 for i, (a, b) in enumerate(lz) if (a + b) % 2 == par)
+            rows = sorted((p[1], p[0], ab) for p in p12 for ab in lx if sum(ab) % 2 == par)
+            cols = sorted((p[0], p[1], ab) for p in p34 for ab in lz if sum(ab) % 2 == par)
             for r0 in range(0, len(rows), 128):
                 for c0 in range(0, len(cols), 64):
-                    if rows[r0][0] < cols[min(len(cols), c0 + 64) - 1][0]:
-                        total += 2 * l12 + 1
-    return total
+                    tr, tc = rows[r0:r0 + 128], cols[c0:c0 + 64]
+                    if tr[0][0] < tc[-1][0]:
+                        tiles.append((l12, tr, tc))
+    return tiles
+
+
+def d3n5_tc_k1_sum(lmax, nbins):
+    """Sum over the tensor-core tiles of K per primary (2 l12 + 1)."""
+    return sum(2 * l12 + 1 for l12, _, _ in d3n5_tc_tiles(lmax, nbins))
 
 
 def d3n5_tensor_roofline(wl, couple_s):
