@@ -31,6 +31,7 @@ int main(void)
 
     npcf_plan_t plan = NULL;
     const double edges[3] = {0.1, 0.2, 0.3};
+    const double edges5[6] = {0.05, 0.1, 0.15, 0.2, 0.25, 0.3};
     const double box[5] = {1.0, 1.0, 1.0, 1.0, 1.0};
     EXPECT(npcf_plan_create(&plan, 5, 3, 2, edges, 2, box, &o) == NPCF_ERR_UNSUPPORTED);
     EXPECT(plan == NULL);
@@ -47,8 +48,11 @@ int main(void)
     o.parity = NPCF_PARITY_ODD; /* N=3 has no odd-parity components */
     EXPECT(npcf_plan_create(&plan, 3, 3, 2, edges, 2, box, &o) == NPCF_ERR_UNSUPPORTED);
     npcf_default_opts(&o);
-    o.precision = NPCF_MIXED_TF32X3; /* the split-precision coupling exists for the D=2 4PCF */
+    o.precision = NPCF_MIXED_TF32X3; /* split precision: the D=2 4PCF (both) and the D=3 5PCF (BF16x3) */
     EXPECT(npcf_plan_create(&plan, 3, 3, 2, edges, 2, box, &o) == NPCF_ERR_UNSUPPORTED);
+    EXPECT(npcf_plan_create(&plan, 3, 5, 2, edges5, 5, box, &o) == NPCF_ERR_UNSUPPORTED);
+    o.precision = NPCF_MIXED_BF16X3;
+    EXPECT(npcf_plan_create(&plan, 3, 4, 2, edges5, 5, box, &o) == NPCF_ERR_UNSUPPORTED);
     EXPECT(plan == NULL);
     npcf_plan_destroy(NULL);
     printf("%d failures\n", fails);
